@@ -1,0 +1,208 @@
+"""Seeded synthetic inputs: directed graphs and per-edge weights.
+
+This module produces inputs only. It holds none of the influence-maximisation
+arithmetic (no coins, thresholds, RR sets, widths or estimators): both the CUDA
+path and the CPU oracle consume what it returns, and neither is imported here.
+
+Every graph is returned as an out-CSR of G with sources sorted ascending and, within
+one source, destinations sorted ascending; self-loops and duplicate edges removed:
+
+    rowptr : int64[n+1]   out-edge offsets of each source node
+    dst    : int32[m]     destination of each edge
+    weight : float32[m]   p(e) for IC, or the LT in-weight of e
+
+The shapes follow the paper's workloads (Section 6, Table 2): sparse directed
+social graphs with skewed degrees. R-MAT stands in for the benchmark graphs and a
+directed Chung-Lu power-law graph for the billion-edge Twitter crawl; the datasets
+themselves are not available. Randomness comes from numpy's Philox bit generator
+seeded by the caller.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+
+@dataclass
+class Graph:
+    n: int
+    rowptr: np.ndarray  # int64[n+1]
+    dst: np.ndarray  # int32[m]
+    name: str = ""
+
+    @property
+    def m(self) -> int:
+        return int(self.dst.shape[0])
+
+    def src(self) -> np.ndarray:
+        """Source node of every edge, int32[m] (edge order)."""
+        deg = np.diff(self.rowptr)
+        return np.repeat(np.arange(self.n, dtype=np.int32), deg)
+
+    def indeg(self) -> np.ndarray:
+        return np.bincount(self.dst, minlength=self.n).astype(np.int64)
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(seed))
+
+
+def csr_from_pairs(n: int, src: np.ndarray, dst: np.ndarray, name: str = "") -> Graph:
+    """Drop self-loops and duplicate pairs, sort by (src, dst), build an out-CSR."""
+    src = np.asarray(src, dtype=np.int64)
+    dst = np.asarray(dst, dtype=np.int64)
+    keep = src != dst
+    key = np.unique(src[keep] * np.int64(n) + dst[keep])
+    s = key // n
+    d = (key % n).astype(np.int32)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(s, minlength=n), out=rowptr[1:])
+    return Graph(n=n, rowptr=rowptr, dst=d, name=name)
+
+
+def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
+         c: float = 0.19, seed: int = 1) -> Graph:
+    """Directed R-MAT graph: 2**scale nodes, edge_factor * 2**scale edge draws.
+
+    Each draw descends `scale` levels of the adjacency matrix, picking the
+    (src-bit, dst-bit) quadrant (0,0) w.p. a, (0,1) w.p. b, (1,0) w.p. c and
+    (1,1) w.p. 1-a-b-c. No noise, no relabelling; self-loops and duplicates are
+    removed afterwards, so m is below the number of draws.
+    """
+    n = 1 << scale
+    draws = edge_factor * n
+    rng = _rng(seed)
+    src = np.zeros(draws, dtype=np.int64)
+    dst = np.zeros(draws, dtype=np.int64)
+    ab, abc = a + b, a + b + c
+    chunk = 1 << 22
+    for lo in range(0, draws, chunk):
+        hi = min(draws, lo + chunk)
+        s = np.zeros(hi - lo, dtype=np.int64)
+        d = np.zeros(hi - lo, dtype=np.int64)
+        for _ in range(scale):
+            u = rng.random(hi - lo)
+            sb = u >= ab
+            db = ((u >= a) & (u < ab)) | (u >= abc)
+            s = (s << 1) | sb
+            d = (d << 1) | db
+        src[lo:hi] = s
+        dst[lo:hi] = d
+    return csr_from_pairs(n, src, dst, name=f"rmat{scale}")
+
+
+def chung_lu(n: int, m_target: int, gamma: float = 2.1, seed: int = 1,
+             max_rounds: int = 64) -> Graph:
+    """Directed Chung-Lu power-law graph with about m_target distinct edges.
+
+    Node weights w_i ~ (i+1)^(-1/(gamma-1)); sources are drawn proportional to w
+    on the node ids, destinations proportional to w on a seeded permutation of the
+    ids. Self-loops and duplicates are dropped and draws repeat until m_target
+    distinct edges exist (or max_rounds is hit).
+    """
+    rng = _rng(seed)
+    w = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (gamma - 1.0))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    perm = rng.permutation(n)
+    have = np.zeros(0, dtype=np.int64)
+    for _ in range(max_rounds):
+        need = m_target - have.shape[0]
+        if need <= 0:
+            break
+        k = int(need * 1.1) + 16
+        s = np.searchsorted(cdf, rng.random(k), side="right")
+        d = perm[np.searchsorted(cdf, rng.random(k), side="right")]
+        s = np.minimum(s, n - 1)
+        d = np.minimum(d, n - 1)
+        keep = s != d
+        key = s[keep].astype(np.int64) * n + d[keep]
+        have = np.unique(np.concatenate([have, key]))
+    if have.shape[0] > m_target:
+        pick = np.sort(rng.choice(have.shape[0], size=m_target, replace=False))
+        have = have[pick]
+    s = have // n
+    d = have % n
+    return csr_from_pairs(n, s, d, name=f"chunglu{n}")
+
+
+def from_edges(n: int, edges, name: str = "") -> Graph:
+    """Graph from an explicit list of (u, v) pairs (u -> v)."""
+    if len(edges) == 0:
+        return Graph(n=n, rowptr=np.zeros(n + 1, dtype=np.int64),
+                     dst=np.zeros(0, dtype=np.int32), name=name)
+    e = np.asarray(edges, dtype=np.int64)
+    return csr_from_pairs(n, e[:, 0], e[:, 1], name=name)
+
+
+# ---------------------------------------------------------------- edge weights
+
+def weighted_cascade(g: Graph) -> np.ndarray:
+    """IC weighted cascade: p(u, v) = 1 / indeg(v), as float32 (Section 6)."""
+    indeg = g.indeg()
+    return (1.0 / indeg[g.dst].astype(np.float64)).astype(np.float32)
+
+
+def lt_inverse_indegree(g: Graph) -> np.ndarray:
+    """LT in-weights b(u, v) = 1 / indeg(v), as float32."""
+    return weighted_cascade(g)
+
+
+def lt_random_normalised(g: Graph, seed: int = 1) -> np.ndarray:
+    """LT in-weights drawn uniformly in [0, 1] per edge, then normalised so that
+    the in-weights of every node sum to one (Section 6, LT setting)."""
+    rng = _rng(seed)
+    r = rng.random(g.m)
+    tot = np.bincount(g.dst, weights=r, minlength=g.n)
+    return (r / tot[g.dst]).astype(np.float32)
+
+
+def trivalency(g: Graph, seed: int = 1) -> np.ndarray:
+    """IC trivalency: p(e) uniform over {0.1, 0.01, 0.001}, drawn per edge."""
+    rng = _rng(seed)
+    vals = np.array([0.1, 0.01, 0.001], dtype=np.float32)
+    return vals[rng.integers(0, 3, size=g.m)]
+
+
+def constant(g: Graph, p: float) -> np.ndarray:
+    return np.full(g.m, p, dtype=np.float32)
+
+
+def uniform_random(g: Graph, lo: float = 0.0, hi: float = 1.0, seed: int = 1) -> np.ndarray:
+    rng = _rng(seed)
+    return rng.uniform(lo, hi, size=g.m).astype(np.float32)
+
+
+# ------------------------------------------------------------ small hand graphs
+
+def star_in(n: int) -> Graph:
+    """Nodes 1..n-1 all point to node 0."""
+    return from_edges(n, [(i, 0) for i in range(1, n)], name=f"star{n}")
+
+
+def chain(n: int) -> Graph:
+    """0 -> 1 -> ... -> n-1."""
+    return from_edges(n, [(i, i + 1) for i in range(n - 1)], name=f"chain{n}")
+
+
+def cycle(n: int) -> Graph:
+    return from_edges(n, [(i, (i + 1) % n) for i in range(n)], name=f"cycle{n}")
+
+
+def complete(n: int) -> Graph:
+    return from_edges(n, [(i, j) for i in range(n) for j in range(n) if i != j],
+                      name=f"complete{n}")
+
+
+def random_small(n: int, m: int, seed: int) -> Graph:
+    """Uniform random directed graph with (at most) m distinct edges."""
+    rng = _rng(seed)
+    pairs = set()
+    tries = 0
+    while len(pairs) < m and tries < 50 * m + 100:
+        u, v = (int(x) for x in rng.integers(0, n, size=2))
+        tries += 1
+        if u != v:
+            pairs.add((u, v))
+    return from_edges(n, sorted(pairs), name=f"rand{n}_{m}_{seed}")

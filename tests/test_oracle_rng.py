@@ -1,0 +1,106 @@
+"""Pins for the oracle's random source (Philox4x32-10, Salmon et al. SC'11) and the
+keyed draws built on it. The paper fixes no generator; what it needs is independent
+uniform coins (Section 3.1) and a uniform root (Definition 2). These tests check
+those properties, and the key-schedule constants against their mathematical
+definitions."""
+import math
+import os
+import re
+from decimal import Decimal, getcontext
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+SRC = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle",
+                   "tim_oracle.c")
+
+
+def test_weyl_constants_are_golden_ratio_and_sqrt3():
+    text = open(SRC).read()
+    k0 = int(re.search(r"k\[0\] \+= (0x[0-9A-Fa-f]+)u", text).group(1), 16)
+    k1 = int(re.search(r"k\[1\] \+= (0x[0-9A-Fa-f]+)u", text).group(1), 16)
+    getcontext().prec = 60
+    phi_m1 = (Decimal(5).sqrt() - 1) / 2
+    s3_m1 = Decimal(3).sqrt() - 1
+    assert k0 == int(phi_m1 * (1 << 32))
+    assert k1 == int(s3_m1 * (1 << 32))
+
+
+def _words(count, key=(7, 0)):
+    out = np.zeros((count, 4), dtype=np.uint32)
+    for i in range(count):
+        out[i] = O.philox((i, 0, 0, 0), key)
+    return out
+
+
+def test_philox_uniform_bytes_chi_square():
+    w = _words(4096)
+    b = w.view(np.uint8).ravel()
+    hist = np.bincount(b, minlength=256)
+    exp = b.size / 256
+    chi2 = ((hist - exp) ** 2 / exp).sum()
+    # 255 dof: mean 255, sd ~22.6; a broken round (e.g. dropped xor) fails by far
+    assert 150 < chi2 < 380
+
+
+def test_philox_bit_balance_and_avalanche():
+    w = _words(2048)
+    bits = np.unpackbits(w.view(np.uint8).ravel())
+    assert abs(bits.mean() - 0.5) < 5 * 0.5 / math.sqrt(bits.size)
+    # flipping one counter bit changes about half of the 128 output bits
+    flips = []
+    for i in range(256):
+        a = O.philox((i, 3, 5, 9), (1, 2))
+        b = O.philox((i ^ (1 << (i % 32)), 3, 5, 9), (1, 2))
+        flips.append(int(np.unpackbits((a ^ b).view(np.uint8)).sum()))
+    assert 60 < np.mean(flips) < 68
+    assert min(flips) > 35
+
+
+def test_philox_key_and_counter_sensitivity():
+    a = O.philox((1, 2, 3, 4), (5, 6))
+    assert not np.array_equal(a, O.philox((1, 2, 3, 4), (5, 7)))
+    assert not np.array_equal(a, O.philox((1, 2, 3, 5), (5, 6)))
+    assert np.array_equal(a, O.philox((1, 2, 3, 4), (5, 6)))
+
+
+def test_root_is_uniform():
+    n = 10
+    cnt = np.bincount([O.root(1, O.make_sid(3, 0, j), n) for j in range(20000)], minlength=n)
+    exp = 2000
+    chi2 = ((cnt - exp) ** 2 / exp).sum()
+    assert chi2 < 40  # 9 dof
+    assert all(0 <= O.root(3, j, 1) == 0 for j in range(50))
+
+
+def test_root_formula_floor_x_n_over_2_64():
+    for j in range(200):
+        sid = O.make_sid(1, 2, j)
+        w = O.philox((sid & 0xFFFFFFFF, sid >> 32, 0, 0), (99, 0))
+        x = (int(w[1]) << 32) | int(w[0])
+        n = 1000003
+        assert O.root(99, sid, n) == (x * n) >> 64
+
+
+def test_set_id_layout():
+    assert O.make_sid(1, 2, 3) == (1 << 56) | (2 << 48) | 3
+    assert O.make_sid(3, 0, 0) == 3 << 56
+
+
+def test_ic_word_selects_lane_of_group():
+    seed, sid = 11, O.make_sid(1, 1, 17)
+    for j in range(0, 64):
+        w = O.philox((sid & 0xFFFFFFFF, sid >> 32, j >> 2, 1), (seed, 0))
+        assert O.ic_word(seed, sid, j) == int(w[j & 3])
+
+
+def test_coin_rate_matches_probability():
+    # live iff word < floor(p * 2^32): frequency p within 5 sigma
+    p = 0.3
+    thr = math.floor(p * 2 ** 32)
+    sid = O.make_sid(3, 0, 5)
+    xs = np.array([O.ic_word(5, sid, j) for j in range(40000)], dtype=np.uint64)
+    f = (xs < thr).mean()
+    assert abs(f - p) < 5 * math.sqrt(p * (1 - p) / xs.size)
