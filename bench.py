@@ -1,0 +1,407 @@
+"""Benchmark: end-to-end TIM+ on a directed R-MAT scale-20 graph, once under IC weighted
+cascade and once under LT with 1/indeg in-weights (k = 50, eps = 0.1, l = 1).
+
+One step = for each model: build G^T from the device-resident out-CSR
+(tim_load_graph_device) and run TIM+ (tim_run: Algorithm 2 -> Algorithm 3 -> theta ->
+Algorithm 1). The metric is RR sets generated per second over the whole step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0). Under torchrun every rank runs its own independent
+TIM+ step on its own GPU with a rank-specific seed (weak scaling, no data exchange).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1404_0900_gb300 import inputs  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--scale", type=int, default=20)
+    p.add_argument("--k", type=int, default=50)
+    p.add_argument("--eps", type=float, default=0.1)
+    p.add_argument("--ell", type=float, default=1.0)
+    p.add_argument("--seed", type=int, default=1)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=12.0,
+                   help="target CPU time of the oracle baseline sample")
+    return p.parse_args(argv)
+
+
+# ------------------------------------------------------------ distributed glue
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+    dist.init_process_group(backend=backend)
+    return dist
+
+
+def reduce_step_results(dist, device, seconds: float, sets: float):
+    """Max of the timed seconds and sum of the RR sets over ranks."""
+    if dist is None:
+        return seconds, sets
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    s = torch.tensor([sets], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(s, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(s.item())
+
+
+# ------------------------------------------------------------------ workload
+
+def workload(args):
+    g = inputs.rmat(args.scale, seed=1)
+    return g, inputs.weighted_cascade(g), inputs.lt_inverse_indegree(g)
+
+
+def config_dict(args, g, world):
+    return {"workload": f"TIM+ on directed R-MAT scale {args.scale} (a,b,c,d=.57,.19,.19,.05; "
+                        f"n={g.n}, m={g.m}), IC weighted cascade then LT 1/indeg, "
+                        f"k={args.k}, eps={args.eps}, l={args.ell}",
+            "n": g.n, "m": g.m, "k": args.k, "eps": args.eps, "ell": args.ell,
+            "models": ["IC", "LT"], "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(PEAKS_FILE))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        loaded = [x for x in sm if mx and x > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------- our arm
+
+def run_ours(args):
+    import torch
+
+    from paper_1404_0900_gb300 import tim
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    seed = args.seed + rank
+    g, w_ic, w_lt = workload(args)
+    stream = torch.cuda.Stream(device=device)
+    torch.cuda.set_stream(stream)
+    d_rowptr = torch.from_numpy(g.rowptr).to(device)
+    d_dst = torch.from_numpy(g.dst).to(device)
+    d_w = {tim.TIM_IC: torch.from_numpy(w_ic).to(device), tim.TIM_LT: torch.from_numpy(w_lt).to(device)}
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    engines = {m: tim.Engine(local, stream) for m in (tim.TIM_IC, tim.TIM_LT)}
+    seeds = np.zeros(args.k, dtype=np.int32)
+
+    def step():
+        out = {}
+        for m, eng in engines.items():
+            tim.tim_load_graph_device(eng.ctx, g.n, g.m, d_rowptr, d_dst, d_w[m], m)
+            _, frac, st = tim.tim_run(eng.ctx, args.k, args.eps, args.ell, seed, seeds_out=seeds)
+            out[m] = st
+        return out
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    for eng in engines.values():
+        tim.tim_get_profile(eng.ctx, reset=True)
+    launches0 = sum(tim.tim_launch_count(e.ctx) for e in engines.values())
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, total_sets, widths, per_model = 0.0, 0, 0, {}
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = step()
+        e1.record(stream)
+        e1.synchronize()
+        total_ms += e0.elapsed_time(e1)
+        for m, st in out.items():
+            total_sets += st["sets_total"]
+            widths += st["width_total"]
+            per_model.setdefault(m, []).append(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = sum(tim.tim_launch_count(e.ctx) for e in engines.values()) - launches0
+    prof_ic = tim.tim_get_profile(engines[tim.TIM_IC].ctx)
+    prof_lt = tim.tim_get_profile(engines[tim.TIM_LT].ctx)
+    sec, sets_all = reduce_step_results(dist, device, total_ms / 1e3, float(total_sets))
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        h_rowptr = torch.from_numpy(g.rowptr).pin_memory()
+        h_dst = torch.from_numpy(g.dst).pin_memory()
+        h_w = {m: torch.from_numpy(w).pin_memory() for m, w in ((tim.TIM_IC, w_ic), (tim.TIM_LT, w_lt))}
+        h_seeds = torch.zeros(args.k, dtype=torch.int32).pin_memory()
+
+        def step_host():
+            n_sets = 0
+            for m, eng in engines.items():
+                tim.lib().tim_load_graph(eng.ctx, g.n, g.m, tim._ptr(h_rowptr), tim._ptr(h_dst),
+                                         tim._ptr(h_w[m]), m)
+                _, _, st = tim.tim_run(eng.ctx, args.k, args.eps, args.ell, seed,
+                                       seeds_out=h_seeds.numpy())
+                n_sets += st["sets_total"]
+            return n_sets
+
+        step_host()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t_ms, e_sets = 0.0, 0
+        for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e_sets += step_host()
+            torch.cuda.synchronize()
+            t_ms += (time.perf_counter() - t0) * 1e3
+        esec, esets = reduce_step_results(dist, device, t_ms / 1e3, float(e_sets))
+        h2d = 2 * (h_rowptr.numel() * 8 + h_dst.numel() * 4 + g.m * 4)
+        e2e = {"value": esets / esec, "unit": "RR sets/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 2 * args.k * 4, "ms_per_step": t_ms / args.steps}
+
+    for eng in engines.values():
+        eng.close()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+
+    # roofline of the dominant kernel: the IC sampler pass with the most device time
+    p = prof_ic
+    dom = max((1, 2, 3), key=lambda i: p[f"pass{i}_ms"])
+    names = {1: "rr_warp_kernel<IC> tier 1 (shared-memory warp per set)",
+             2: "rr_warp_kernel<IC> tier 2 (global-memory warp per set)",
+             3: "bulk level-synchronous IC pass (tier 3)"}
+    alg_bytes = sampler_bytes(p, dom)
+    launches_dom = max(p[f"pass{dom}_launches"], 1)
+    per_launch_bytes = alg_bytes / launches_dom
+    per_launch_ms = p[f"pass{dom}_ms"] / launches_dom
+    peaks = measured_peaks()
+    if peaks and peaks.get("hbm_gbs"):
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, peak_src = FALLBACK_HBM_GBS, "fallback"
+    ms_dom = p[f"pass{dom}_ms"]
+    achieved = alg_bytes / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
+    ic = per_model[tim.TIM_IC][-1]
+    lt = per_model[tim.TIM_LT][-1]
+    line = {
+        "metric": "RR sets/s (TIM+ end to end: IC + LT)",
+        "value": sets_all / sec,
+        "unit": "RR sets/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32/int64 (FP64 for kappa and theta)",
+        "data": "synthetic (seeded R-MAT, no dataset)",
+        "config": config_dict(args, g, world),
+        "gteps_width": widths / (total_ms / 1e3) / 1e9,
+        "tim_plus_ms": {"IC": statistics.mean(s["ms_total"] for s in per_model[tim.TIM_IC]),
+                        "LT": statistics.mean(s["ms_total"] for s in per_model[tim.TIM_LT])},
+        "phases_ms_IC": {k: ic[k] for k in ("ms_kpt", "ms_refine", "ms_select_sample",
+                                             "ms_select_greedy")},
+        "phases_ms_LT": {k: lt[k] for k in ("ms_kpt", "ms_refine", "ms_select_sample",
+                                             "ms_select_greedy")},
+        "theta": {"IC": ic["theta"], "LT": lt["theta"]},
+        "kpt_plus": {"IC": ic["kpt_plus"], "LT": lt["kpt_plus"]},
+        "roofline": {"kernel": names[dom], "bound": "hbm",
+                     "achieved": achieved, "peak": peak, "peak_source": peak_src,
+                     "unit": "GB/s", "frac": achieved / peak,
+                     "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
+                     "traffic": None},
+        "sampler_profile": {"IC": prof_ic, "LT": prof_lt},
+        "clocks": clk,
+        "gpu_launches": launches,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, g, w_ic, w_lt,
+                                            n_ic=ic["sets_total"], n_lt=lt["sets_total"])
+    return line
+
+
+def sampler_bytes(p: dict, i: int) -> float:
+    """Algorithmic bytes of sampler pass i: 4 B threshold per examined in-edge, 4 B
+    source per live in-edge, 16 B of in-CSR offsets per member, 8 B emitted per member
+    (node and set id), 20 B of per-set records."""
+    return (4.0 * p[f"pass{i}_width"] + 4.0 * p[f"pass{i}_live"] + 24.0 * p[f"pass{i}_members"]
+            + 20.0 * p[f"pass{i}_sets"])
+
+
+# --------------------------------------------------------- the CPU oracle arm
+
+def oracle_rates(args, g, w_ic, w_lt, seconds: float, nthreads: int):
+    """RR sets/s of the oracle (Section 3.1 BFS, NodeSelection set ids) per model, on a
+    sample sized to take about `seconds` of wall time in total."""
+    from oracle import oracle as O
+    rates = {}
+    for name, model, w, probe in (("IC", O.IC, w_ic, 256), ("LT", O.LT, w_lt, 4096)):
+        og = O.load_graph(g.n, g.rowptr, g.dst, w, model)
+        t0 = time.perf_counter()
+        O.sample(og, args.seed, O.make_sid(3, 0, 0), probe, nthreads)
+        dt = max(time.perf_counter() - t0, 1e-6)
+        count = max(probe, int(probe * (seconds / 2) / dt))
+        t0 = time.perf_counter()
+        O.sample(og, args.seed, O.make_sid(3, 0, probe), count, nthreads)
+        dt = time.perf_counter() - t0
+        rates[name] = (count / dt, count, dt)
+    return rates
+
+
+def mix_rate(rates, n_ic, n_lt):
+    """Sets/s for a step with n_ic IC sets and n_lt LT sets."""
+    t = n_ic / rates["IC"][0] + n_lt / rates["LT"][0]
+    return (n_ic + n_lt) / t
+
+
+def cpu_baseline(args, g, w_ic, w_lt, n_ic, n_lt):
+    from oracle import oracle as O
+    nth = O.host_threads()
+    rates = oracle_rates(args, g, w_ic, w_lt, args.cpu_seconds, nth)
+    return {"value": mix_rate(rates, n_ic, n_lt), "unit": "RR sets/s", "cores": nth,
+            "kind": "oracle",
+            "sample": (f"oracle RR-set generation on the same graph: {rates['IC'][1]} IC sets in "
+                       f"{rates['IC'][2]:.1f} s and {rates['LT'][1]} LT sets in "
+                       f"{rates['LT'][2]:.1f} s ({nth} threads), rate weighted to one step's "
+                       f"mix of {n_ic} IC and {n_lt} LT sets")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return None
+    from oracle import oracle as O
+    g, w_ic, w_lt = workload(args)
+    nth = O.host_threads()
+    # one step = a bounded sample of the workload's RR sets (IC:LT in the GPU step's
+    # proportion, about 7:2), about two seconds of oracle time
+    per_step = max(1.0, 2.0)
+    for _ in range(args.warmup):
+        oracle_rates(args, g, w_ic, w_lt, per_step / 4, nth)
+    vals, secs = [], 0.0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        r = oracle_rates(args, g, w_ic, w_lt, per_step, nth)
+        secs += time.perf_counter() - t0
+        vals.append(mix_rate(r, 7, 2))
+    v = statistics.mean(vals)
+    return {"impl": "reference", "metric": "RR sets/s (TIM+ end to end: IC + LT)", "value": v,
+            "unit": "RR sets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32/int64 (FP64 for kappa)",
+            "data": "synthetic (seeded R-MAT, no dataset)",
+            "config": config_dict(args, g, world),
+            "cpu_baseline": {"value": v, "unit": "RR sets/s", "cores": nth, "kind": "oracle",
+                             "sample": "per step: oracle RR-set generation, IC and LT sets of "
+                                       "NodeSelection ids, about 1 s each, rate weighted 7:2"},
+            "e2e": {"value": v, "unit": "RR sets/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if line is not None:
+        print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

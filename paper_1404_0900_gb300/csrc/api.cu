@@ -1,0 +1,562 @@
+// api.cu -- the C ABI of libtim.so (declared in include/tim.h): context management,
+// graph loading, and the host-side drivers of Algorithm 2 (KptEstimation), Algorithm 3
+// (RefineKPT), Algorithm 1 (NodeSelection) and TIM / TIM+ (Sections 3.3 and 4.1).
+//
+// The drivers only do the scalar arithmetic the paper performs between phases (c_i of
+// Eq. 7, the stop test of Algorithm 2, eps', lambda', theta', lambda of Eq. 4, theta);
+// every per-set and per-node step runs in the kernels of sample.cu and select.cu.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <vector>
+
+#include "common.cuh"
+
+// ----------------------------------------------------------------- helpers
+
+int tim_fail(tim_ctx* ctx, int code, const std::string& msg) {
+    if (ctx) ctx->last_err = msg;
+    return code;
+}
+
+int tim_cuda_check(tim_ctx* ctx, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return TIM_OK;
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return tim_fail(ctx, TIM_ERR_OOM, msg);
+    }
+    return tim_fail(ctx, TIM_ERR_CUDA, msg);
+}
+
+void tim_free(DevBuf& b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+int tim_ensure(tim_ctx* ctx, DevBuf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return TIM_OK;
+    tim_free(b);
+    // Allocation is stream-ordered with respect to previous work only through the
+    // device-wide synchronisation of cudaMalloc/cudaFree.
+    void* p = nullptr;
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        char buf[128];
+        snprintf(buf, sizeof buf, "cudaMalloc of %zu bytes failed", bytes);
+        return tim_fail(ctx, TIM_ERR_OOM, buf);
+    }
+    b.p = p;
+    b.bytes = bytes;
+    return TIM_OK;
+}
+
+int tim_sync(tim_ctx* ctx) {
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return TIM_OK;
+}
+
+DevScalars* tim_dscal(tim_ctx* ctx) { return (DevScalars*)ctx->scal.p; }
+
+int tim_zero_scalars(tim_ctx* ctx) {
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->scal.p, 0, sizeof(DevScalars), ctx->stream));
+    return TIM_OK;
+}
+
+int tim_read_scalars(tim_ctx* ctx) {
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->h_scal, ctx->scal.p, sizeof(DevScalars),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return TIM_OK;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+static double elapsed_ms(tim_ctx* ctx, int a, int b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ctx->ev[a], ctx->ev[b]);
+    return (double)ms;
+}
+
+// ----------------------------------------------------------- scalar formulas
+
+// Number of rounds of Algorithm 2: floor(log2 n) - 1 (never negative).
+int tim_host_rounds(int64_t n) {
+    int fl = 0;
+    while (fl < 62 && ((int64_t)1 << (fl + 1)) <= n) fl++;
+    return std::max(fl - 1, 0);
+}
+
+// c_i of Eq. 7, rounded up.
+uint64_t tim_host_c_i(int64_t n, double ell, int i) {
+    const double ln_n = log((double)n);
+    const double c = (6.0 * ell * ln_n + 6.0 * log(log2((double)n))) * ldexp(1.0, i);
+    return (uint64_t)ceil(c);
+}
+
+// lambda of Eq. 4 with ln C(n, k) as a sum of k logarithms of ratios.
+double tim_host_lambda(int64_t n, int k, double eps, double ell) {
+    double lnb = 0.0;
+    for (int i = 0; i < k; i++) lnb += log((double)(n - i) / (double)(k - i));
+    const double ln_n = log((double)n);
+    return (8.0 + 2.0 * eps) * (double)n * (ell * ln_n + lnb + log(2.0)) / (eps * eps);
+}
+
+double tim_host_eps_prime(double eps, int k, double ell) {
+    return 5.0 * cbrt(ell * eps * eps / ((double)k + ell));
+}
+
+double tim_host_lambda_prime(int64_t n, double eps_p, double ell) {
+    return (2.0 + eps_p) * ell * (double)n * log((double)n) / (eps_p * eps_p);
+}
+
+static inline uint64_t make_sid(uint64_t phase, uint64_t round, uint64_t j) {
+    return (phase << 56) | (round << 48) | j;
+}
+
+// ------------------------------------------------------------------- the ABI
+
+extern "C" {
+
+const char* tim_strerror(int code) {
+    switch (code) {
+        case TIM_OK: return "ok";
+        case TIM_ERR_ARG: return "invalid argument";
+        case TIM_ERR_OOM: return "out of device memory";
+        case TIM_ERR_OVERFLOW: return "output buffer too small";
+        case TIM_ERR_TIMEOUT: return "bounded device wait timed out";
+        case TIM_ERR_CUDA: return "CUDA error";
+        case TIM_ERR_STATE: return "call out of order";
+        default: return "unknown status";
+    }
+}
+
+const char* tim_last_error_message(tim_ctx* ctx) { return ctx ? ctx->last_err.c_str() : ""; }
+
+int tim_create(tim_ctx** out, int device, void* cuda_stream) {
+    if (!out) return TIM_ERR_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return TIM_ERR_ARG;
+    }
+    DeviceGuard g(device);
+    tim_ctx* ctx = new tim_ctx();
+    ctx->device = device;
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+    if (cuda_stream) {
+        ctx->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return TIM_ERR_CUDA;
+        }
+        ctx->own_stream = true;
+    }
+    int rc = tim_ensure(ctx, ctx->scal, sizeof(DevScalars));
+    if (rc == TIM_OK && cudaMallocHost((void**)&ctx->h_scal, sizeof(DevScalars)) != cudaSuccess)
+        rc = TIM_ERR_OOM;
+    for (int i = 0; rc == TIM_OK && i < 8; i++)
+        if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) rc = TIM_ERR_CUDA;
+    for (int i = 0; rc == TIM_OK && i < 4; i++)
+        if (cudaEventCreate(&ctx->kev[i]) != cudaSuccess) rc = TIM_ERR_CUDA;
+    if (rc != TIM_OK) {
+        tim_destroy(ctx);
+        return rc;
+    }
+    memset(ctx->h_scal, 0, sizeof(DevScalars));
+    *out = ctx;
+    return TIM_OK;
+}
+
+int tim_destroy(tim_ctx* ctx) {
+    if (!ctx) return TIM_OK;
+    DeviceGuard g(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    DevBuf* bufs[] = {&ctx->rowptr,   &ctx->src,        &ctx->thr,       &ctx->pool,
+                      &ctx->pool_sid, &ctx->set_start,  &ctx->set_len,   &ctx->set_width,
+                      &ctx->counts,   &ctx->node_off,   &ctx->cursor,    &ctx->node_sets,
+                      &ctx->covered,  &ctx->chosen,     &ctx->best,      &ctx->seed_mark,
+                      &ctx->seeds_dev, &ctx->ovf_list,  &ctx->big_bitmap, &ctx->big_queue,
+                      &ctx->ovf_list2, &ctx->arena,
+                      &ctx->scratch_a, &ctx->scratch_b, &ctx->scratch_c, &ctx->scratch_d,
+                      &ctx->scratch_e, &ctx->scal,      &ctx->bulk_bitmap, &ctx->bulk_slot,
+                      &ctx->bulk_F,    &ctx->bulk_M,    &ctx->bulk_ng,   &ctx->bulk_gp,
+                      &ctx->bulk_scal};
+    for (DevBuf* b : bufs) tim_free(*b);
+    if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
+    for (int i = 0; i < 8; i++)
+        if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
+    for (int i = 0; i < 4; i++)
+        if (ctx->kev[i]) cudaEventDestroy(ctx->kev[i]);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return TIM_OK;
+}
+
+uint64_t tim_launch_count(tim_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int tim_set_width_budget(tim_ctx* ctx, uint64_t budget) {
+    if (!ctx) return TIM_ERR_ARG;
+    ctx->width_budget = budget;
+    return TIM_OK;
+}
+
+int tim_set_team_size(tim_ctx* ctx, int warps) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (warps != 0 && warps != 1 && warps != 2 && warps != 4 && warps != 8)
+        return tim_fail(ctx, TIM_ERR_ARG, "team size must be 0, 1, 2, 4 or 8");
+    ctx->team_size = warps;
+    return TIM_OK;
+}
+
+int tim_get_profile(tim_ctx* ctx, tim_profile* out, int reset) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (out) *out = ctx->prof;
+    if (reset) memset(&ctx->prof, 0, sizeof ctx->prof);
+    return TIM_OK;
+}
+
+int tim_load_graph_device(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_out_rowptr,
+                          const int32_t* d_out_dst, const float* d_edge_w, int model) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (!d_out_rowptr || (m > 0 && (!d_out_dst || !d_edge_w)))
+        return tim_fail(ctx, TIM_ERR_ARG, "null graph array");
+    DeviceGuard g(ctx->device);
+    int rc = tim_graph_build(ctx, n, m, d_out_rowptr, d_out_dst, d_edge_w, model);
+    // the radix-sort scratch is only needed while loading
+    tim_free(ctx->scratch_a);
+    tim_free(ctx->scratch_b);
+    tim_free(ctx->scratch_c);
+    tim_free(ctx->scratch_d);
+    return rc;
+}
+
+int tim_load_graph(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* out_rowptr,
+                   const int32_t* out_dst, const float* edge_w, int model) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (!out_rowptr || (m > 0 && (!out_dst || !edge_w)) || n < 2 || m < 0)
+        return tim_fail(ctx, TIM_ERR_ARG, "invalid graph arguments");
+    DeviceGuard g(ctx->device);
+    DevBuf r, d, w;
+    int rc = TIM_OK;
+    do {
+        if ((rc = tim_ensure(ctx, r, (size_t)(n + 1) * sizeof(int64_t)))) break;
+        if ((rc = tim_ensure(ctx, d, (size_t)(m + 1) * sizeof(int32_t)))) break;
+        if ((rc = tim_ensure(ctx, w, (size_t)(m + 1) * sizeof(float)))) break;
+        if ((rc = tim_cuda_check(ctx, cudaMemcpyAsync(r.p, out_rowptr, (size_t)(n + 1) * 8,
+                                                      cudaMemcpyHostToDevice, ctx->stream),
+                                 "copy rowptr")))
+            break;
+        if (m > 0) {
+            if ((rc = tim_cuda_check(ctx, cudaMemcpyAsync(d.p, out_dst, (size_t)m * 4,
+                                                          cudaMemcpyHostToDevice, ctx->stream),
+                                     "copy dst")))
+                break;
+            if ((rc = tim_cuda_check(ctx, cudaMemcpyAsync(w.p, edge_w, (size_t)m * 4,
+                                                          cudaMemcpyHostToDevice, ctx->stream),
+                                     "copy weights")))
+                break;
+        }
+        rc = tim_load_graph_device(ctx, n, m, (const int64_t*)r.p, (const int32_t*)d.p,
+                                   (const float*)w.p, model);
+    } while (0);
+    cudaStreamSynchronize(ctx->stream);
+    tim_free(r);
+    tim_free(d);
+    tim_free(w);
+    return rc;
+}
+
+int tim_sample_rr(tim_ctx* ctx, uint64_t theta, uint64_t seed, uint64_t first_set_id,
+                  uint64_t* total_members) {
+    if (!ctx) return TIM_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    SampleRequest req;
+    req.seed = seed;
+    req.sid0 = first_set_id;
+    req.count = theta;
+    req.flags = SAMPLE_EMIT;
+    SampleResult res;
+    TIM_TRY(tim_sample(ctx, req, &res));
+    ctx->have_kpt = false;
+    if (total_members) *total_members = res.members;
+    return TIM_OK;
+}
+
+int tim_rr_size(tim_ctx* ctx, uint64_t* n_sets, uint64_t* total_members) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (n_sets) *n_sets = ctx->n_sets;
+    if (total_members) *total_members = ctx->members;
+    return TIM_OK;
+}
+
+int tim_get_rr(tim_ctx* ctx, int64_t* off, int32_t* mem, uint64_t mem_cap, int64_t* widths) {
+    if (!ctx || !off) return TIM_ERR_ARG;
+    DeviceGuard g(ctx->device);
+    const uint64_t ns = ctx->n_sets, nm = ctx->members;
+    std::vector<uint64_t> start(ns);
+    std::vector<uint32_t> len(ns);
+    std::vector<uint64_t> wid(ns);
+    std::vector<uint32_t> pool(nm);
+    if (ns) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(start.data(), ctx->set_start.p, ns * 8, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(len.data(), ctx->set_len.p, ns * 4, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(wid.data(), ctx->set_width.p, ns * 8, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    }
+    if (nm)
+        CUDA_TRY(ctx, cudaMemcpyAsync(pool.data(), ctx->pool.p, nm * 4, cudaMemcpyDeviceToHost,
+                                      ctx->stream));
+    TIM_TRY(tim_sync(ctx));
+    off[0] = 0;
+    for (uint64_t j = 0; j < ns; j++) off[j + 1] = off[j] + len[j];
+    if (widths)
+        for (uint64_t j = 0; j < ns; j++) widths[j] = (int64_t)wid[j];
+    if ((uint64_t)off[ns] > mem_cap) return tim_fail(ctx, TIM_ERR_OVERFLOW, "mem_cap too small");
+    if (mem)
+        for (uint64_t j = 0; j < ns; j++)
+            memcpy(mem + off[j], pool.data() + start[j], (size_t)len[j] * 4);
+    return TIM_OK;
+}
+
+int tim_kappa_sum(tim_ctx* ctx, int k, uint64_t seed, uint64_t first_set_id, uint64_t count,
+                  uint64_t* sum_hi, uint64_t* sum_lo, uint64_t* width_sum) {
+    if (!ctx || k < 1) return tim_fail(ctx, TIM_ERR_ARG, "k must be >= 1");
+    DeviceGuard g(ctx->device);
+    SampleRequest req;
+    req.seed = seed;
+    req.sid0 = first_set_id;
+    req.count = count;
+    req.flags = SAMPLE_KAPPA;
+    req.k = k;
+    SampleResult res;
+    TIM_TRY(tim_sample(ctx, req, &res));
+    if (sum_hi) *sum_hi = (uint64_t)(res.ksum >> 64);
+    if (sum_lo) *sum_lo = (uint64_t)res.ksum;
+    if (width_sum) *width_sum = res.wsum;
+    return TIM_OK;
+}
+
+// Algorithm 2. Every round emits its sets too, so that the stopping round's sets are
+// R' of Algorithm 3 without regenerating them.
+int tim_kpt_estimate(tim_ctx* ctx, int k, double ell, uint64_t seed, double* kpt_star,
+                     int* round) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    if (k < 1 || k > ctx->n || !(ell > 0.0)) return tim_fail(ctx, TIM_ERR_ARG, "need 1 <= k <= n, l > 0");
+    DeviceGuard g(ctx->device);
+    const int rounds = tim_host_rounds(ctx->n);
+    ctx->have_kpt = false;
+    ctx->kpt_star = 1.0;
+    ctx->kpt_round = 0;
+    ctx->kpt_last_round = 0;
+    ctx->kpt_last_c = 0;
+    ctx->kpt_sets = 0;
+    ctx->kpt_width = 0;
+    ctx->n_sets = ctx->members = 0;
+    for (int i = 1; i <= rounds; i++) {
+        const uint64_t c = tim_host_c_i(ctx->n, ell, i);
+        SampleRequest req;
+        req.seed = seed;
+        req.sid0 = make_sid(1, (uint64_t)i, 0);
+        req.count = c;
+        req.flags = SAMPLE_EMIT | SAMPLE_KAPPA;
+        req.k = k;
+        SampleResult res;
+        TIM_TRY(tim_sample(ctx, req, &res));
+        ctx->kpt_last_round = i;
+        ctx->kpt_last_c = c;
+        ctx->kpt_sets += c;
+        ctx->kpt_width += res.wsum;
+        // sum/c_i > 2^-i  <=>  S > c_i * 2^(63 - i), S the 2^-63 fixed-point sum
+        const unsigned __int128 bound = (unsigned __int128)c << (63 - i);
+        if (res.ksum > bound) {
+            const double sum = ldexp((double)res.ksum, -63);
+            ctx->kpt_star = (double)ctx->n * sum / (2.0 * (double)c);
+            ctx->kpt_round = i;
+            break;
+        }
+    }
+    ctx->have_kpt = true;
+    ctx->kpt_k = k;
+    ctx->kpt_ell = ell;
+    ctx->kpt_seed = seed;
+    if (kpt_star) *kpt_star = ctx->kpt_star;
+    if (round) *round = ctx->kpt_round;
+    return TIM_OK;
+}
+
+int tim_refine_kpt(tim_ctx* ctx, int k, double ell, double eps, uint64_t seed, double* kpt_plus,
+                   double* eps_prime, uint64_t* theta_prime) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (!ctx->have_kpt) return tim_fail(ctx, TIM_ERR_STATE, "call tim_kpt_estimate first");
+    if (k < 1 || k > ctx->n || !(eps > 0.0) || !(ell > 0.0))
+        return tim_fail(ctx, TIM_ERR_ARG, "need 1 <= k <= n, eps > 0, l > 0");
+    DeviceGuard g(ctx->device);
+    // lines 1-6: greedy on R' (the store holds the last round of Algorithm 2)
+    TIM_TRY(tim_build_index(ctx));
+    TIM_TRY(tim_greedy(ctx, k, nullptr, nullptr));
+    TIM_TRY(tim_mark_seeds(ctx, (const int32_t*)ctx->seeds_dev.p, k));
+    // lines 7-8
+    const double ep = tim_host_eps_prime(eps, k, ell);
+    const double lp = tim_host_lambda_prime(ctx->n, ep, ell);
+    const uint64_t theta_p = (uint64_t)ceil(lp / ctx->kpt_star);
+    // lines 9-10
+    SampleRequest req;
+    req.seed = seed;
+    req.sid0 = make_sid(2, 0, 0);
+    req.count = theta_p;
+    req.flags = SAMPLE_COVER;
+    req.seed_mark = (const uint32_t*)ctx->seed_mark.p;
+    SampleResult res;
+    TIM_TRY(tim_sample(ctx, req, &res));
+    const double f = (double)res.covered / (double)theta_p;
+    // lines 11-12
+    ctx->ref_kpt_prime = f * (double)ctx->n / (1.0 + ep);
+    ctx->ref_kpt_plus = std::max(ctx->ref_kpt_prime, ctx->kpt_star);
+    ctx->ref_eps_prime = ep;
+    ctx->ref_theta_prime = theta_p;
+    ctx->ref_covered = res.covered;
+    ctx->ref_width = res.wsum;
+    if (kpt_plus) *kpt_plus = ctx->ref_kpt_plus;
+    if (eps_prime) *eps_prime = ep;
+    if (theta_prime) *theta_prime = theta_p;
+    return TIM_OK;
+}
+
+int tim_node_select(tim_ctx* ctx, int k, int32_t* seeds, double* covered_fraction,
+                    uint64_t* covered_count) {
+    if (!ctx || !seeds) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    DeviceGuard g(ctx->device);
+    TIM_TRY(tim_build_index(ctx));
+    uint64_t cov = 0;
+    TIM_TRY(tim_greedy(ctx, k, seeds, &cov));
+    if (covered_fraction) *covered_fraction = ctx->n_sets ? (double)cov / (double)ctx->n_sets : 0.0;
+    if (covered_count) *covered_count = cov;
+    return TIM_OK;
+}
+
+int tim_coverage_counts(tim_ctx* ctx, int32_t* counts) {
+    if (!ctx || !counts) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    DeviceGuard g(ctx->device);
+    TIM_TRY(tim_build_index(ctx));
+    CUDA_TRY(ctx, cudaMemcpyAsync(counts, ctx->counts.p, (size_t)ctx->n * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    return tim_sync(ctx);
+}
+
+int tim_covered_count(tim_ctx* ctx, const int32_t* seeds, int n_seeds, uint64_t seed,
+                      uint64_t first_set_id, uint64_t count, uint64_t* covered) {
+    if (!ctx || (n_seeds > 0 && !seeds) || n_seeds < 0) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    DeviceGuard g(ctx->device);
+    for (int i = 0; i < n_seeds; i++)
+        if (seeds[i] < 0 || seeds[i] >= ctx->n) return tim_fail(ctx, TIM_ERR_ARG, "seed out of range");
+    TIM_TRY(tim_ensure(ctx, ctx->seeds_dev, (size_t)std::max(n_seeds, 1) * sizeof(int32_t)));
+    if (n_seeds > 0)
+        CUDA_TRY(ctx, cudaMemcpyAsync(ctx->seeds_dev.p, seeds, (size_t)n_seeds * 4,
+                                      cudaMemcpyHostToDevice, ctx->stream));
+    TIM_TRY(tim_mark_seeds(ctx, (const int32_t*)ctx->seeds_dev.p, n_seeds));
+    SampleRequest req;
+    req.seed = seed;
+    req.sid0 = first_set_id;
+    req.count = count;
+    req.flags = SAMPLE_COVER;
+    req.seed_mark = (const uint32_t*)ctx->seed_mark.p;
+    SampleResult res;
+    TIM_TRY(tim_sample(ctx, req, &res));
+    if (covered) *covered = res.covered;
+    return TIM_OK;
+}
+
+static int run_common(tim_ctx* ctx, bool plus, int k, double eps, double ell, uint64_t seed,
+                      int32_t* seeds, double* covered_fraction, tim_stats* st,
+                      uint64_t theta_override) {
+    if (!ctx || !seeds) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    if (k < 1 || k > ctx->n || !(eps > 0.0) || !(ell > 0.0))
+        return tim_fail(ctx, TIM_ERR_ARG, "need 1 <= k <= n, eps > 0, l > 0");
+    DeviceGuard g(ctx->device);
+    tim_stats s;
+    memset(&s, 0, sizeof s);
+    cudaEventRecord(ctx->ev[0], ctx->stream);
+    TIM_TRY(tim_kpt_estimate(ctx, k, ell, seed, nullptr, nullptr));
+    cudaEventRecord(ctx->ev[1], ctx->stream);
+    double lower = ctx->kpt_star;
+    if (plus) {
+        TIM_TRY(tim_refine_kpt(ctx, k, ell, eps, seed, nullptr, nullptr, nullptr));
+        lower = ctx->ref_kpt_plus;
+    }
+    cudaEventRecord(ctx->ev[2], ctx->stream);
+    s.lambda = tim_host_lambda(ctx->n, k, eps, ell);
+    const uint64_t theta = theta_override ? theta_override : (uint64_t)ceil(s.lambda / lower);
+    SampleRequest req;
+    req.seed = seed;
+    req.sid0 = make_sid(3, 0, 0);
+    req.count = theta;
+    req.flags = SAMPLE_EMIT;
+    SampleResult res;
+    TIM_TRY(tim_sample(ctx, req, &res));
+    cudaEventRecord(ctx->ev[3], ctx->stream);
+    uint64_t cov = 0;
+    TIM_TRY(tim_build_index(ctx));
+    TIM_TRY(tim_greedy(ctx, k, seeds, &cov));
+    cudaEventRecord(ctx->ev[4], ctx->stream);
+    TIM_TRY(tim_sync(ctx));
+    s.kpt_round = ctx->kpt_round;
+    s.kpt_last_round = ctx->kpt_last_round;
+    s.kpt_star = ctx->kpt_star;
+    s.kpt_prime = plus ? ctx->ref_kpt_prime : 0.0;
+    s.kpt_plus = plus ? ctx->ref_kpt_plus : ctx->kpt_star;
+    s.eps_prime = plus ? ctx->ref_eps_prime : 0.0;
+    s.theta_prime = plus ? ctx->ref_theta_prime : 0;
+    s.covered_prime = plus ? ctx->ref_covered : 0;
+    s.theta = theta;
+    s.covered = cov;
+    s.sets_total = ctx->kpt_sets + s.theta_prime + theta;
+    s.members_select = res.members;
+    s.width_select = res.wsum;
+    s.width_total = ctx->kpt_width + (plus ? ctx->ref_width : 0) + res.wsum;
+    s.ms_kpt = elapsed_ms(ctx, 0, 1);
+    s.ms_refine = elapsed_ms(ctx, 1, 2);
+    s.ms_select_sample = elapsed_ms(ctx, 2, 3);
+    s.ms_select_greedy = elapsed_ms(ctx, 3, 4);
+    s.ms_total = elapsed_ms(ctx, 0, 4);
+    if (covered_fraction) *covered_fraction = theta ? (double)cov / (double)theta : 0.0;
+    if (st) *st = s;
+    return TIM_OK;
+}
+
+int tim_run(tim_ctx* ctx, int k, double eps, double ell, uint64_t seed, int32_t* seeds,
+            double* covered_fraction, tim_stats* stats, uint64_t theta_override) {
+    return run_common(ctx, true, k, eps, ell, seed, seeds, covered_fraction, stats, theta_override);
+}
+
+int tim_run_tim(tim_ctx* ctx, int k, double eps, double ell, uint64_t seed, int32_t* seeds,
+                double* covered_fraction, tim_stats* stats) {
+    return run_common(ctx, false, k, eps, ell, seed, seeds, covered_fraction, stats, 0);
+}
+
+}  // extern "C"

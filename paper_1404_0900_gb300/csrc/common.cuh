@@ -1,0 +1,288 @@
+// common.cuh -- context state, error handling and device helpers shared by the
+// translation units of libtim.so.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "tim.h"
+
+// ------------------------------------------------------------------ host side
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+// Scalars the kernels update; one block of device memory per context, mirrored in
+// pinned host memory for cheap read-back.
+struct DevScalars {
+    unsigned long long next_set;   // tier-1 work counter
+    unsigned long long pool_used;  // RR-set store fill (members)
+    unsigned long long ksum_lo;    // kappa fixed-point sum, low 64 bits
+    unsigned long long ksum_hi;    // high 64 bits
+    unsigned long long wsum;       // sum of widths, all tiers
+    unsigned long long covered;    // covered-set counter
+    unsigned long long next2;      // tier-2 work counter
+    unsigned long long next3;      // tier-3 work counter
+    unsigned int cnt1;             // sets tier 1 listed for tier 2
+    unsigned int cnt2;             // sets tier 2 listed for tier 3
+    int err;                       // device-side error bits (TIM_DEV_ERR_*)
+    int pad0;
+    unsigned long long width[3];   // sum of widths per tier
+    unsigned long long live[3];    // live in-edges followed per tier
+    unsigned long long memb[3];    // members per tier
+};
+
+enum : int {
+    TIM_DEV_ERR_POOL = 1,     // RR-set store too small (host grows it and re-runs)
+    TIM_DEV_ERR_OVF_LIST = 2, // second-pass list too small
+    TIM_DEV_ERR_GRAPH = 4,    // invalid graph (range, self-loop, duplicate)
+    TIM_DEV_ERR_WEIGHT = 8,   // invalid weight
+    TIM_DEV_ERR_BOUNDS = 16,  // an index check failed
+};
+
+struct tim_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int num_sms = 0;
+    std::string last_err;
+    unsigned long long launches = 0;
+
+    // graph: G^T as in-CSR
+    bool have_graph = false;
+    int64_t n = 0, m = 0;
+    int model = -1;
+    DevBuf rowptr;  // uint64[n+1]
+    DevBuf src;     // uint32[m + 4]
+    DevBuf thr;     // uint32[m + 4] IC thresholds or LT inclusive cumulative thresholds
+
+    // RR-set store
+    uint64_t n_sets = 0;
+    uint64_t members = 0;
+    DevBuf pool;       // uint32 members, grouped by set (sets in any order)
+    DevBuf pool_sid;   // uint32 set index of each member
+    DevBuf set_start;  // uint64[n_sets]
+    DevBuf set_len;    // uint32[n_sets]
+    DevBuf set_width;  // uint64[n_sets]
+
+    // greedy / index
+    DevBuf counts;     // int32[n]
+    DevBuf node_off;   // uint64[n+1]
+    DevBuf cursor;     // uint32[n]
+    DevBuf node_sets;  // uint32[members]
+    DevBuf covered;    // uint8[n_sets]
+    DevBuf chosen;     // uint8[n]
+    DevBuf best;       // uint64[k]
+    DevBuf seed_mark;  // uint32 bitmap[n/32 + 1]
+    DevBuf seeds_dev;  // int32[n]
+
+    // sets handed from tier 1 to tier 2 and from tier 2 to tier 3 of the sampler
+    DevBuf ovf_list;    // uint32 set index
+    DevBuf ovf_list2;   // uint32 set index
+    DevBuf arena;       // tier-2 per-warp hash + queue
+    bool arena_clean = false;
+    DevBuf big_bitmap;  // tier-3 LT: uint32[slots * words]
+    DevBuf big_queue;   // tier-3 LT: uint32[slots * n]
+    bool big_bitmap_clean = false;
+
+    // batched second pass for heavy IC sets (sample_bulk.cu)
+    DevBuf bulk_bitmap, bulk_slot, bulk_F, bulk_M, bulk_ng, bulk_gp, bulk_scal;
+    bool bulk_bitmap_clean = false;
+    uint64_t bulk_fcap = 0, bulk_mcap = 0;
+    // IC first pass: a warp gives a set to the second pass once its examined in-edges
+    // would exceed this many
+    unsigned long long width_budget = 16384;
+    // IC tier 2: warps per RR set (1, 2, 4 or 8); 0 = chosen from the number of sets
+    int team_size = 0;
+    int last_team = 1;
+
+    // generic scratch for scans and sorts
+    DevBuf scratch_a, scratch_b, scratch_c, scratch_d, scratch_e;
+
+    DevBuf scal;
+    DevScalars* h_scal = nullptr;  // pinned
+
+    cudaEvent_t ev[8] = {};
+    cudaEvent_t kev[4] = {};  // around the sampler's three tiers
+
+    // state of the last tim_kpt_estimate
+    bool have_kpt = false;
+    int kpt_round = 0, kpt_last_round = 0;
+    uint64_t kpt_last_c = 0;
+    double kpt_star = 1.0;
+    int kpt_k = 0;
+    double kpt_ell = 0.0;
+    uint64_t kpt_seed = 0;
+    uint64_t kpt_sets = 0, kpt_width = 0;
+
+    // kernel timing of the RR sampler (events around each launch)
+    tim_profile prof = {};
+
+    // state of the last tim_refine_kpt
+    double ref_kpt_prime = 0.0, ref_kpt_plus = 0.0, ref_eps_prime = 0.0;
+    uint64_t ref_theta_prime = 0, ref_covered = 0, ref_width = 0;
+};
+
+#define TIM_TRY(expr)                   \
+    do {                                \
+        int _rc = (expr);               \
+        if (_rc != TIM_OK) return _rc;  \
+    } while (0)
+
+int tim_fail(tim_ctx* ctx, int code, const std::string& msg);
+int tim_cuda_check(tim_ctx* ctx, cudaError_t e, const char* what);
+#define CUDA_TRY(ctx, call) TIM_TRY(tim_cuda_check((ctx), (call), #call))
+// After a kernel launch: count it and check the launch status.
+#define LAUNCH_CHECK(ctx, name)                                  \
+    do {                                                         \
+        (ctx)->launches++;                                       \
+        TIM_TRY(tim_cuda_check((ctx), cudaGetLastError(), name)); \
+    } while (0)
+
+int tim_ensure(tim_ctx* ctx, DevBuf& b, size_t bytes);
+void tim_free(DevBuf& b);
+int tim_sync(tim_ctx* ctx);
+int tim_read_scalars(tim_ctx* ctx);  // copy DevScalars to h_scal and synchronise
+int tim_zero_scalars(tim_ctx* ctx);
+DevScalars* tim_dscal(tim_ctx* ctx);
+
+// primitives (prims.cu)
+// Exclusive scan of uint32 counts into uint64 offsets out[0..count] (out[count] = total).
+int tim_scan_u32_to_u64(tim_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t count);
+// Stable LSD radix sort of (key, value) uint32 pairs by the low `bits` bits of key.
+// keys/vals are sorted in place (alternate buffers are taken from scratch).
+int tim_radix_sort_pairs(tim_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t count,
+                         int bits);
+
+// graph.cu
+int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
+                    const int32_t* d_dst, const float* d_w, int model);
+
+// sample.cu
+enum : int { SAMPLE_EMIT = 1, SAMPLE_KAPPA = 2, SAMPLE_COVER = 4 };
+struct SampleRequest {
+    uint64_t seed = 0;
+    uint64_t sid0 = 0;
+    uint64_t count = 0;
+    int flags = 0;
+    int k = 0;                         // kappa
+    const uint32_t* seed_mark = nullptr;  // cover: bitmap of the seed set
+};
+struct SampleResult {
+    unsigned __int128 ksum = 0;
+    uint64_t wsum = 0;
+    uint64_t live = 0;
+    uint64_t covered = 0;
+    uint64_t members = 0;
+    uint64_t big_sets = 0;
+};
+int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res);
+// Third tier for the heavy IC sets list[0 .. count) (sample_bulk.cu).
+int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, uint32_t count,
+                uint32_t* pool, uint32_t* pool_sid, uint64_t pool_cap, uint64_t* live_out);
+
+// select.cu
+int tim_build_index(tim_ctx* ctx);
+int tim_greedy(tim_ctx* ctx, int k, int32_t* host_seeds, uint64_t* covered);
+int tim_mark_seeds(tim_ctx* ctx, const int32_t* d_seeds, int k);
+
+// scalar formulas (api.cu)
+uint64_t tim_host_c_i(int64_t n, double ell, int i);
+int tim_host_rounds(int64_t n);
+double tim_host_lambda(int64_t n, int k, double eps, double ell);
+double tim_host_eps_prime(double eps, int k, double ell);
+double tim_host_lambda_prime(int64_t n, double eps_p, double ell);
+
+// ---------------------------------------------------------------- device side
+
+#define TIM_PHILOX_M0 0xD2511F53u
+#define TIM_PHILOX_M1 0xCD9E8D57u
+#define TIM_PHILOX_W0 0x9E3779B9u
+#define TIM_PHILOX_W1 0xBB67AE85u
+
+#define TIM_TAG_ROOT 0u
+#define TIM_TAG_IC 1u
+#define TIM_TAG_LT 2u
+
+// Philox round keys for one seed: key schedule k_r = k_0 + r * W, r = 0..9.
+struct PhiloxKeys {
+    uint32_t k0[10];
+    uint32_t k1[10];
+};
+
+static inline PhiloxKeys tim_philox_keys(uint64_t seed) {
+    PhiloxKeys K;
+    uint32_t a = (uint32_t)seed, b = (uint32_t)(seed >> 32);
+    for (int r = 0; r < 10; r++) {
+        K.k0[r] = a;
+        K.k1[r] = b;
+        a += TIM_PHILOX_W0;
+        b += TIM_PHILOX_W1;
+    }
+    return K;
+}
+
+#ifdef __CUDACC__
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// multiplies and xors with the precomputed round keys.
+__device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_t c2,
+                                               uint32_t c3, const PhiloxKeys& K) {
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        unsigned long long p0 = (unsigned long long)c0 * TIM_PHILOX_M0;
+        unsigned long long p1 = (unsigned long long)c2 * TIM_PHILOX_M1;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ K.k0[r];
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ K.k1[r];
+        c1 = (uint32_t)p1;
+        c3 = (uint32_t)p0;
+        c0 = n0;
+        c2 = n2;
+    }
+    return make_uint4(c0, c1, c2, c3);
+}
+
+// Uniform root: floor(x * n / 2^64) with x the first two words of the ROOT draw.
+__device__ __forceinline__ uint32_t rr_root(uint64_t sid, uint64_t n, const PhiloxKeys& K) {
+    uint4 w = philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32), 0u, TIM_TAG_ROOT, K);
+    unsigned long long x = ((unsigned long long)w.y << 32) | w.x;
+    return (uint32_t)__umul64hi(x, (unsigned long long)n);
+}
+
+// kappa(R) of Eq. 6 as (w/m) * sum_{i<k} q^i, q = 1 - w/m, built over the bits of k
+// (S_2j = S_j (1 + P_j), P_2j = P_j^2; set bit: S += P, P *= q). Every operation is
+// an explicitly rounded FP64 intrinsic so that nothing is contracted into an FMA.
+__device__ __forceinline__ double kappa_fp64(unsigned long long w, unsigned long long m, int k) {
+    if (m == 0 || w == 0 || k <= 0) return 0.0;
+    double x = __ddiv_rn((double)w, (double)m);
+    double q = __dsub_rn(1.0, x);
+    double S = 0.0, P = 1.0;
+    int top = 31 - __clz(k);
+    for (int b = top; b >= 0; b--) {
+        S = __dmul_rn(S, __dadd_rn(1.0, P));
+        P = __dmul_rn(P, P);
+        if ((k >> b) & 1) {
+            S = __dadd_rn(S, P);
+            P = __dmul_rn(P, q);
+        }
+    }
+    return __dmul_rn(x, S);
+}
+
+// kappa in 2^-63 fixed point, truncated toward zero.
+__device__ __forceinline__ unsigned long long kappa_fixed(double kappa) {
+    return __double2ull_rz(__dmul_rn(kappa, 9223372036854775808.0));
+}
+
+// Add a 128-bit (hi, lo) into a global 128-bit accumulator.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long* lo_p,
+                                                unsigned long long* hi_p,
+                                                unsigned long long lo, unsigned long long hi) {
+    unsigned long long old = atomicAdd(lo_p, lo);
+    unsigned long long carry = (old + lo < old) ? 1ull : 0ull;
+    if (hi + carry) atomicAdd(hi_p, hi + carry);
+}
+#endif

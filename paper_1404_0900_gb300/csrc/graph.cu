@@ -1,0 +1,213 @@
+// graph.cu -- G^T (Table 1 of the paper) on the device: the in-CSR of G with the
+// in-edges of every node ascending by source, and the per-edge thresholds of the
+// diffusion model.
+//
+// Build: a stable radix sort of (destination, edge id) pairs turns the out-CSR (sorted
+// by source) into in-lists sorted by source; sources come from a binary search of
+// the out-CSR offsets.
+//   IC (Section 2.1): thr = floor(p * 2^32) for p < 1, 0xFFFFFFFF (always live) for
+//                     p >= 1; an in-edge is live iff its coin word < thr.
+//   LT (Section 6):   thr = inclusive prefix over the in-list of floor(b * 2^32),
+//                     saturated at 2^32 - 1; the triggering in-edge of a node is the
+//                     first whose prefix exceeds the node's draw.
+#include "common.cuh"
+
+namespace {
+
+__global__ void check_rowptr_kernel(const int64_t* __restrict__ rowptr, int64_t n, int64_t m,
+                                    int* __restrict__ err) {
+    for (int64_t u = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; u < n;
+         u += (int64_t)gridDim.x * blockDim.x) {
+        int64_t a = rowptr[u], b = rowptr[u + 1];
+        if (b < a || a < 0 || b > m || (u == 0 && a != 0) || (u == n - 1 && b != m))
+            atomicOr(err, TIM_DEV_ERR_GRAPH);
+    }
+}
+
+__global__ void keys_iota_kernel(const int32_t* __restrict__ dst, int64_t m, int64_t n,
+                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
+                                 uint32_t* __restrict__ indeg, int* __restrict__ err) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int32_t v = dst[e];
+        if (v < 0 || v >= n) {
+            atomicOr(err, TIM_DEV_ERR_GRAPH);
+            v = 0;
+        }
+        keys[e] = (uint32_t)v;
+        vals[e] = (uint32_t)e;
+        atomicAdd(&indeg[v], 1u);
+    }
+}
+
+// Source of out-CSR edge e: the u with rowptr[u] <= e < rowptr[u+1].
+__device__ __forceinline__ uint32_t source_of(const int64_t* __restrict__ rowptr, int64_t n,
+                                              int64_t e) {
+    int64_t lo = 0, hi = n;  // answer in [lo, hi)
+    while (hi - lo > 1) {
+        int64_t mid = (lo + hi) >> 1;
+        if (rowptr[mid] <= e)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    return (uint32_t)lo;
+}
+
+__global__ void fill_in_edges_kernel(const int64_t* __restrict__ out_rowptr, int64_t n, int64_t m,
+                                     const uint32_t* __restrict__ sorted_dst,
+                                     const uint32_t* __restrict__ sorted_eid,
+                                     const float* __restrict__ w, int model,
+                                     uint32_t* __restrict__ src, uint32_t* __restrict__ thr,
+                                     unsigned long long* __restrict__ lt_t,
+                                     int* __restrict__ err) {
+    for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < m;
+         pos += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t e = sorted_eid[pos];
+        uint32_t v = sorted_dst[pos];
+        uint32_t u = source_of(out_rowptr, n, (int64_t)e);
+        if (u == v) atomicOr(err, TIM_DEV_ERR_GRAPH);
+        src[pos] = u;
+        float p = w[e];
+        if (!(p >= 0.0f && p <= 1.0f)) {
+            atomicOr(err, TIM_DEV_ERR_WEIGHT);
+            p = 0.0f;
+        }
+        double scaled = (double)p * 4294967296.0;  // exact: float -> double, times 2^32
+        if (model == TIM_IC) {
+            thr[pos] = p >= 1.0f ? 0xFFFFFFFFu : (uint32_t)scaled;  // truncation = floor
+        } else {
+            lt_t[pos] = (unsigned long long)scaled;
+        }
+    }
+}
+
+// Duplicate edges: equal neighbouring sources inside one in-list.
+__global__ void check_dups_kernel(const uint32_t* __restrict__ sorted_dst,
+                                  const uint32_t* __restrict__ src, int64_t m,
+                                  int* __restrict__ err) {
+    for (int64_t pos = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < m;
+         pos += (int64_t)gridDim.x * blockDim.x) {
+        if (sorted_dst[pos] == sorted_dst[pos - 1] && src[pos] <= src[pos - 1])
+            atomicOr(err, TIM_DEV_ERR_GRAPH);
+    }
+}
+
+// LT: per node (one warp), inclusive prefix of t over the in-list, saturated, and the
+// weight-sum check.
+__global__ void lt_prefix_kernel(const uint64_t* __restrict__ rowptr, int64_t n,
+                                 const unsigned long long* __restrict__ lt_t,
+                                 const uint32_t* __restrict__ sorted_eid,
+                                 const float* __restrict__ w, uint32_t* __restrict__ thr,
+                                 int* __restrict__ err) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        uint64_t a = rowptr[v], b = rowptr[v + 1];
+        unsigned long long carry = 0;
+        double wsum = 0.0;
+        for (uint64_t base = a; base < b; base += 32) {
+            uint64_t j = base + lane;
+            unsigned long long t = j < b ? lt_t[j] : 0ull;
+            double wj = j < b ? (double)w[sorted_eid[j]] : 0.0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= o) t += y;
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) wj += __shfl_xor_sync(0xffffffffu, wj, o);
+            wsum += wj;
+            unsigned long long inc = carry + t;
+            if (j < b) thr[j] = inc > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)inc;
+            carry += __shfl_sync(0xffffffffu, t, 31);
+        }
+        if (lane == 0 && wsum > 1.0 + 1e-5) atomicOr(err, TIM_DEV_ERR_WEIGHT);
+    }
+}
+
+}  // namespace
+
+int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
+                    const int32_t* d_dst, const float* d_w, int model) {
+    if (n < 2 || n > 0x7FFFFFFFll || m < 0 || m > 0xFFFFFFF0ll)
+        return tim_fail(ctx, TIM_ERR_ARG, "n must be in [2, 2^31) and m in [0, 2^32 - 16)");
+    if (model != TIM_IC && model != TIM_LT) return tim_fail(ctx, TIM_ERR_ARG, "unknown model");
+    ctx->have_graph = false;
+    ctx->have_kpt = false;
+    ctx->n_sets = ctx->members = 0;
+    TIM_TRY(tim_zero_scalars(ctx));
+    DevScalars* ds = tim_dscal(ctx);
+    const int T = 256;
+    const unsigned G = (unsigned)(ctx->num_sms * 8);
+
+    TIM_TRY(tim_ensure(ctx, ctx->rowptr, (size_t)(n + 1) * sizeof(uint64_t)));
+    TIM_TRY(tim_ensure(ctx, ctx->src, (size_t)(m + 4) * sizeof(uint32_t)));
+    TIM_TRY(tim_ensure(ctx, ctx->thr, (size_t)(m + 4) * sizeof(uint32_t)));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->src.p, 0, (size_t)(m + 4) * sizeof(uint32_t), ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->thr.p, 0, (size_t)(m + 4) * sizeof(uint32_t), ctx->stream));
+
+    DevBuf keys, vals, indeg, lt_t;
+    int rc = TIM_OK;
+    do {
+        if ((rc = tim_ensure(ctx, keys, (size_t)(m + 1) * sizeof(uint32_t)))) break;
+        if ((rc = tim_ensure(ctx, vals, (size_t)(m + 1) * sizeof(uint32_t)))) break;
+        if ((rc = tim_ensure(ctx, indeg, (size_t)(n + 1) * sizeof(uint32_t)))) break;
+        if (model == TIM_LT &&
+            (rc = tim_ensure(ctx, lt_t, (size_t)(m + 1) * sizeof(unsigned long long))))
+            break;
+        if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(indeg.p, 0, (size_t)(n + 1) * 4, ctx->stream),
+                                 "memset")))
+            break;
+        check_rowptr_kernel<<<G, T, 0, ctx->stream>>>(d_rowptr, n, m, &ds->err);
+        ctx->launches++;
+        if (m > 0) {
+            keys_iota_kernel<<<G, T, 0, ctx->stream>>>(d_dst, m, n, (uint32_t*)keys.p,
+                                                       (uint32_t*)vals.p, (uint32_t*)indeg.p,
+                                                       &ds->err);
+            ctx->launches++;
+            int bits = 0;
+            while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
+            if ((rc = tim_radix_sort_pairs(ctx, (uint32_t*)keys.p, (uint32_t*)vals.p, (uint64_t)m,
+                                           bits)))
+                break;
+        }
+        if ((rc = tim_scan_u32_to_u64(ctx, (const uint32_t*)indeg.p, (uint64_t*)ctx->rowptr.p,
+                                      (uint64_t)n)))
+            break;
+        if (m > 0) {
+            fill_in_edges_kernel<<<G, T, 0, ctx->stream>>>(
+                d_rowptr, n, m, (const uint32_t*)keys.p, (const uint32_t*)vals.p, d_w, model,
+                (uint32_t*)ctx->src.p, (uint32_t*)ctx->thr.p, (unsigned long long*)lt_t.p,
+                &ds->err);
+            ctx->launches++;
+            check_dups_kernel<<<G, T, 0, ctx->stream>>>((const uint32_t*)keys.p,
+                                                        (const uint32_t*)ctx->src.p, m, &ds->err);
+            ctx->launches++;
+            if (model == TIM_LT) {
+                lt_prefix_kernel<<<G, T, 0, ctx->stream>>>(
+                    (const uint64_t*)ctx->rowptr.p, n, (const unsigned long long*)lt_t.p,
+                    (const uint32_t*)vals.p, d_w, (uint32_t*)ctx->thr.p, &ds->err);
+                ctx->launches++;
+            }
+        }
+        if ((rc = tim_cuda_check(ctx, cudaGetLastError(), "graph kernels"))) break;
+        if ((rc = tim_read_scalars(ctx))) break;
+    } while (0);
+    tim_free(keys);
+    tim_free(vals);
+    tim_free(indeg);
+    tim_free(lt_t);
+    if (rc) return rc;
+    if (ctx->h_scal->err & TIM_DEV_ERR_WEIGHT)
+        return tim_fail(ctx, TIM_ERR_ARG, "invalid edge weights for the model");
+    if (ctx->h_scal->err & TIM_DEV_ERR_GRAPH)
+        return tim_fail(ctx, TIM_ERR_ARG,
+                        "invalid graph (offsets, node range, self-loop or duplicate edge)");
+    ctx->n = n;
+    ctx->m = m;
+    ctx->model = model;
+    ctx->have_graph = true;
+    return TIM_OK;
+}

@@ -1,0 +1,782 @@
+// sample.cu -- random RR sets on the GPU (Definitions 1-2; randomised BFS of Section
+// 3.1 "Implementation" for IC; the triggering-model BFS of Section 4.2 with the LT
+// triggering distribution of Section 6).
+//
+// Every coin is keyed on (seed, set id, in-CSR position) and every LT draw on (seed,
+// set id, node), so a set does not depend on which kernel expands it, in what order,
+// or on how many threads: the three tiers below give identical sets.
+//
+// Tier 1: a persistent kernel with one warp per RR set; the set's BFS queue (which is
+//   also its member list) and a visited hash live in shared memory. A frontier of up
+//   to 32 nodes is expanded at once: their in-lists are cut into 4-aligned groups of
+//   in-CSR positions, spread over the lanes, and each lane draws one Philox block (4
+//   coin words) and loads 4 thresholds with one 16-byte load. A set whose members
+//   outgrow the queue, or (IC) whose examined in-edges would pass a budget, is listed
+//   for tier 2. This keeps the kernel's tail short: light sets are most sets.
+// Tier 2: the same code with a 32x larger queue and hash in global memory (one arena
+//   slot per team) and no edge budget, run by teams of T warps per set: T = 1 when the
+//   listed sets are many (parallelism across sets fills the GPU), up to 8 when they are
+//   few (the team splits each in-list, so one heavy set does not leave the GPU idle).
+// In-lists of at least BIG_GROUPS groups (hubs) are streamed by the whole team one at
+// a time with two groups in flight per lane; the rest of a frontier is flattened.
+// Tier 3: sets beyond tier 2's queue: IC goes to the batched level-synchronous pass of
+//   sample_bulk.cu; LT (a chain) is walked by one warp per set with a visited bitmap.
+//
+// Per set the kernels can (flags): EMIT the members into the RR-set store, sum KAPPA
+// (Eq. 6) in 2^-63 fixed point, and test COVER (does the set meet a given seed set;
+// Algorithm 3 lines 9-10; the BFS stops at the first member in the seed set).
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace {
+
+constexpr uint32_t EMPTY = 0xFFFFFFFFu;
+constexpr int ST_OVERFLOW = 1;
+constexpr int ST_COVERED = 2;
+constexpr int WARPS = 8;          // warps per CTA (tiers 1 and 2)
+constexpr int CHUNK = 2;          // sets claimed per work-counter increment
+constexpr int BIG_THREADS = 256;  // tier 3 LT CTA size
+
+// Queue capacity Q and hash size 2^LOG2H (>= 2Q) of one warp's set.
+template <int QQ, int LG>
+struct Cap {
+    static constexpr int Q = QQ;
+    static constexpr int LOG2H = LG;
+    static constexpr int H = 1 << LG;
+    // hash[H] u32, queue[Q] u32, slot[Q] u16, ctl[4] int
+    static constexpr int WORDS = (1 << LG) + QQ + QQ / 2 + 4;
+};
+using Tier1 = Cap<256, 9>;
+using Tier2 = Cap<8192, 14>;
+
+struct SampleArgs {
+    const uint64_t* rowptr;
+    const uint32_t* src;
+    const uint32_t* thr;
+    uint64_t n, m;
+    PhiloxKeys K;
+    uint64_t sid0, count;
+    int flags, k;
+    const uint32_t* seed_mark;
+    uint32_t* pool;
+    uint32_t* pool_sid;
+    uint64_t pool_cap;
+    uint64_t* set_start;
+    uint32_t* set_len;
+    uint64_t* set_width;
+    DevScalars* ds;
+    uint32_t* list1;   // tier 1 -> tier 2
+    uint32_t* list2;   // tier 2 -> tier 3
+    uint32_t list_cap;
+    uint32_t* arena;   // tier 2 per-warp storage
+    uint32_t* big_bitmap;  // tier 3 LT
+    uint32_t* big_queue;
+    uint64_t big_words;
+    unsigned long long width_budget;  // tier 1 IC: in-edges one warp may examine per set
+};
+
+__device__ __forceinline__ uint4 draw(const SampleArgs& a, uint64_t sid, uint32_t elem,
+                                      uint32_t tag) {
+    return philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32), elem, tag, a.K);
+}
+
+__device__ __forceinline__ bool marked(const uint32_t* mark, uint32_t u) {
+    return (__ldg(mark + (u >> 5)) >> (u & 31)) & 1u;
+}
+
+__device__ __forceinline__ uint32_t pick(uint4 v, int c) {
+    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
+}
+
+__device__ __forceinline__ bool ic_live(uint32_t x, uint32_t thr) {
+    return thr == 0xFFFFFFFFu || x < thr;
+}
+
+__device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Visited set of one RR set: insert u. Returns INS_NEW, INS_OLD, or INS_FULL when the
+// queue or the hash is full (the set then moves to the next tier). Bounded probing.
+constexpr int INS_OLD = 0, INS_NEW = 1, INS_FULL = 2;
+
+template <class C>
+__device__ __forceinline__ int set_insert(uint32_t* hash, uint32_t* queue, uint16_t* slot,
+                                          int* ctl, uint32_t u) {
+    uint32_t h = (u * 0x9E3779B1u) >> (32 - C::LOG2H);
+    for (int probe = 0; probe < C::H; probe++) {
+        uint32_t old = atomicCAS(&hash[h], EMPTY, u);
+        if (old == EMPTY) {
+            int pos = atomicAdd(&ctl[0], 1);
+            if (pos < C::Q) {
+                queue[pos] = u;
+                slot[pos] = (uint16_t)h;
+                return INS_NEW;
+            }
+            atomicOr(&ctl[1], ST_OVERFLOW);
+            return INS_FULL;
+        }
+        if (old == u) return INS_OLD;
+        h = (h + 1) & (C::H - 1);
+    }
+    atomicOr(&ctl[1], ST_OVERFLOW);
+    return INS_FULL;
+}
+
+// First position j in [lo, hi) with thr[j] > x (thr non-decreasing), or hi.
+// 32-ary search by the whole warp.
+__device__ __forceinline__ uint64_t warp_lt_search(const uint32_t* __restrict__ thr, uint64_t lo,
+                                                   uint64_t hi, uint32_t x, int lane) {
+    for (int it = 0; it < 16 && hi - lo > 32; it++) {
+        uint64_t stride = (hi - lo + 31) >> 5;
+        uint64_t p = lo + (uint64_t)(lane + 1) * stride - 1;
+        bool valid = p < hi;
+        bool pred = valid && __ldg(thr + p) > x;
+        uint32_t b = __ballot_sync(0xffffffffu, pred);
+        if (b) {
+            int f = __ffs(b) - 1;
+            uint64_t nlo = lo + (uint64_t)f * stride;
+            hi = nlo + stride;
+            lo = nlo;
+        } else {
+            lo += (uint64_t)__popc(__ballot_sync(0xffffffffu, valid)) * stride;
+        }
+    }
+    uint64_t p = lo + lane;
+    bool pred = p < hi && __ldg(thr + p) > x;
+    uint32_t b = __ballot_sync(0xffffffffu, pred);
+    return b ? lo + (uint64_t)(__ffs(b) - 1) : hi;
+}
+
+// ------------------------------------------------------------ tiers 1 and 2
+
+// Barrier over the T warps of a team (T = 1: the warp itself). Named barrier ids
+// 1..8 are one per team of the block; 0 stays free for __syncthreads.
+template <int T>
+__device__ __forceinline__ void team_sync(int team) {
+    if (T == 1)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(T * 32) : "memory");
+}
+
+// Coins of the in-CSR positions [4g, 4g + 4) that lie in [beg, end): follow the live
+// in-edges. Returns bit 0 if the set overflowed, bit 1 if it met the seed set.
+template <class C>
+__device__ __forceinline__ int ic_group(const SampleArgs& a, uint64_t g, uint64_t beg,
+                                        uint64_t end, uint4 x, uint4 tv, uint32_t* hash,
+                                        uint32_t* queue, uint16_t* slot, int* ctl,
+                                        unsigned long long& live) {
+    int f = 0;
+    const uint64_t p0 = g << 2;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        const uint64_t p = p0 + c;
+        if (p >= beg && p < end && ic_live(pick(x, c), pick(tv, c))) {
+            const uint32_t u = __ldg(a.src + p);
+            live++;
+            const int r = set_insert<C>(hash, queue, slot, ctl, u);
+            if (r == INS_FULL) {
+                f |= 1;
+            } else if (r == INS_NEW && (a.flags & SAMPLE_COVER) && marked(a.seed_mark, u)) {
+                atomicOr(&ctl[1], ST_COVERED);
+                f |= 2;
+            }
+        }
+    }
+    return f;
+}
+
+// In-lists with at least this many 4-edge groups are expanded one at a time by the
+// whole team (no ownership search, two groups in flight per lane).
+constexpr uint32_t BIG_GROUPS = 32;
+
+// Expand one RR set with a team of T warps (wt = warp index in the team, team = team
+// index in the block). Returns the status bits; *width_out = w(R) (Eq. 1); *live_out
+// counts live in-edges followed (per lane).
+template <int MODEL, class C, int T>
+__device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32_t* hash,
+                                       uint32_t* queue, uint16_t* slot, int* ctl,
+                                       unsigned long long budget, int wt, int team,
+                                       unsigned long long* width_out,
+                                       unsigned long long* live_out) {
+    const int lane = threadIdx.x & 31;
+    volatile int* vctl = ctl;
+    const bool cover = a.flags & SAMPLE_COVER;
+    const uint32_t root = rr_root(sid, a.n, a.K);
+    if (wt == 0 && lane == 0) {
+        uint32_t h = (root * 0x9E3779B1u) >> (32 - C::LOG2H);
+        hash[h] = root;
+        queue[0] = root;
+        slot[0] = (uint16_t)h;
+        ctl[0] = 1;
+        ctl[1] = (cover && marked(a.seed_mark, root)) ? ST_COVERED : 0;
+    }
+    team_sync<T>(team);
+    unsigned long long width = 0, live = 0;
+    if (MODEL == TIM_IC) {
+        const PhiloxKeys& K = a.K;
+        const uint32_t s0 = (uint32_t)sid, s1 = (uint32_t)(sid >> 32);
+        const uint4* thr4 = reinterpret_cast<const uint4*>(a.thr);
+        int head = 0;
+        for (int guard = 0; guard < C::Q + 1; guard++) {
+            // a consistent snapshot of (tail, status) for the whole team
+            int tail, stat;
+            if (T == 1) {
+                tail = __shfl_sync(0xffffffffu, vctl[0], 0);
+                stat = __shfl_sync(0xffffffffu, vctl[1], 0);
+            } else {
+                tail = vctl[0];
+                stat = vctl[1];
+                team_sync<T>(team);
+            }
+            if (stat || head >= tail) break;
+            const int nb = min(32, tail - head);
+            uint64_t beg = 0, end = 0;
+            if (lane < nb) {
+                const uint32_t v = queue[head + lane];
+                beg = __ldg(a.rowptr + v);
+                end = __ldg(a.rowptr + v + 1);
+            }
+            const unsigned long long dw = warp_sum_u64(end - beg);
+            if (width + dw > budget) {
+                // too heavy for this tier: list the set for the next one
+                if (wt == 0 && lane == 0) ctl[1] |= ST_OVERFLOW;
+                break;
+            }
+            width += dw;
+            const uint32_t ng = end > beg ? (uint32_t)(((end - 1) >> 2) - (beg >> 2) + 1) : 0u;
+            const bool big = ng >= BIG_GROUPS;
+            int flags = 0;
+            // hubs first: the whole team strides over one in-list at a time
+            uint32_t bigmask = __ballot_sync(0xffffffffu, big);
+            while (bigmask && !(flags & 3)) {
+                const int b = __ffs(bigmask) - 1;
+                bigmask &= bigmask - 1;
+                const uint64_t bb = __shfl_sync(0xffffffffu, beg, b);
+                const uint64_t be = __shfl_sync(0xffffffffu, end, b);
+                const uint64_t g1 = ((be - 1) >> 2) + 1;
+                for (uint64_t g = (bb >> 2) + (uint64_t)(wt * 32 + lane);; g += 64 * T) {
+                    const bool v0 = g < g1, v1 = g + 32 * T < g1;
+                    if (!__any_sync(0xffffffffu, v0)) break;
+                    uint4 x0 = make_uint4(0, 0, 0, 0), t0 = x0, x1 = x0, t1 = x0;
+                    if (v0) {
+                        x0 = philox4x32_10(s0, s1, (uint32_t)g, TIM_TAG_IC, K);
+                        t0 = __ldg(thr4 + g);
+                    }
+                    if (v1) {
+                        x1 = philox4x32_10(s0, s1, (uint32_t)(g + 32 * T), TIM_TAG_IC, K);
+                        t1 = __ldg(thr4 + g + 32 * T);
+                    }
+                    if (v0) flags |= ic_group<C>(a, g, bb, be, x0, t0, hash, queue, slot, ctl, live);
+                    if (v1)
+                        flags |= ic_group<C>(a, g + 32 * T, bb, be, x1, t1, hash, queue, slot, ctl,
+                                             live);
+                    if (__any_sync(0xffffffffu, flags & 3)) break;
+                }
+                flags = __reduce_or_sync(0xffffffffu, flags);
+            }
+            // the rest, flattened over the lanes: lane -> (owner node, group)
+            const uint32_t ngs = big ? 0u : ng;
+            uint32_t incl = ngs;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t excl = incl - ngs;
+            for (uint32_t base = wt * 32; base < total && !(flags & 3); base += 32 * T) {
+                const uint32_t t = base + lane;
+                int own = 0;  // number of lanes whose inclusive count is <= t
+#pragma unroll
+                for (int sft = 16; sft > 0; sft >>= 1) {
+                    const uint32_t ic = __shfl_sync(0xffffffffu, incl, own + sft - 1);
+                    if (ic <= t) own += sft;
+                }
+                const uint64_t o_beg = __shfl_sync(0xffffffffu, beg, own);
+                const uint64_t o_end = __shfl_sync(0xffffffffu, end, own);
+                const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own);
+                if (t < total) {
+                    const uint64_t g = (o_beg >> 2) + (t - o_excl);
+                    const uint4 x = philox4x32_10(s0, s1, (uint32_t)g, TIM_TAG_IC, K);
+                    const uint4 tv = __ldg(thr4 + g);
+                    flags |= ic_group<C>(a, g, o_beg, o_end, x, tv, hash, queue, slot, ctl, live);
+                }
+                flags = __reduce_or_sync(0xffffffffu, flags);
+            }
+            team_sync<T>(team);
+            head += nb;
+        }
+    } else {
+        uint32_t v = root;
+        for (int guard = 0; guard < C::Q + 1; guard++) {
+            if (__shfl_sync(0xffffffffu, vctl[1], 0)) break;
+            const uint64_t beg = __ldg(a.rowptr + v), end = __ldg(a.rowptr + v + 1);
+            width += end - beg;
+            if (beg == end) break;
+            const uint32_t x = draw(a, sid, v, TIM_TAG_LT).x;
+            const uint64_t j = warp_lt_search(a.thr, beg, end, x, lane);
+            if (j >= end) break;
+            const uint32_t u = __ldg(a.src + j);
+            int fresh = 0;
+            if (lane == 0) {
+                live++;
+                fresh = set_insert<C>(hash, queue, slot, ctl, u) == INS_NEW ? 1 : 0;
+                if (fresh && cover && marked(a.seed_mark, u)) atomicOr(&ctl[1], ST_COVERED);
+            }
+            fresh = __shfl_sync(0xffffffffu, fresh, 0);
+            __syncwarp();
+            if (!fresh) break;
+            v = u;
+        }
+    }
+    team_sync<T>(team);
+    *width_out = width;
+    *live_out += live;
+    return T == 1 ? __shfl_sync(0xffffffffu, vctl[1], 0) : vctl[1];
+}
+
+// TIER 1: teams of one warp, storage in shared memory, every set index of [0, count),
+// in-edge budget (IC); listed sets go to list1. TIER 2: teams of T warps, storage in
+// the global arena, the sets of list1, no budget; listed sets go to list2.
+template <int MODEL, class C, int TIER, int T>
+__global__ void __launch_bounds__(WARPS * 32, 4) rr_team_kernel(SampleArgs a) {
+    extern __shared__ uint32_t smem[];
+    __shared__ unsigned long long s_claim[WARPS];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int wt = wid % T, team = wid / T;
+    const int tl = wt * 32 + lane;  // thread index inside the team
+    uint32_t* hash;
+    if (TIER == 1) {
+        hash = smem + team * C::WORDS;
+        for (int i = tl; i < C::H; i += 32 * T) hash[i] = EMPTY;
+    } else {
+        // the arena's hash regions are all EMPTY between sets
+        const uint64_t slot_id = (uint64_t)blockIdx.x * (WARPS / T) + team;
+        hash = a.arena + slot_id * C::WORDS;
+    }
+    team_sync<T>(team);
+    uint32_t* queue = hash + C::H;
+    uint16_t* slot = reinterpret_cast<uint16_t*>(queue + C::Q);
+    int* ctl = reinterpret_cast<int*>(queue + C::Q + C::Q / 2);
+    const unsigned long long budget =
+        (TIER == 1 && MODEL == TIM_IC) ? a.width_budget : ~0ull;
+    unsigned long long* counter = TIER == 1 ? &a.ds->next_set : &a.ds->next2;
+    const uint64_t items =
+        TIER == 1 ? a.count : (uint64_t)min(((volatile unsigned*)&a.ds->cnt1)[0], a.list_cap);
+    uint32_t* out_list = TIER == 1 ? a.list1 : a.list2;
+    unsigned* out_cnt = TIER == 1 ? &a.ds->cnt1 : &a.ds->cnt2;
+    unsigned long long k_lo = 0, k_hi = 0, wsum = 0, cov = 0, live = 0, memb = 0;
+    const bool emit = a.flags & SAMPLE_EMIT, kap = a.flags & SAMPLE_KAPPA;
+    const bool leader = wt == 0 && lane == 0;
+    for (;;) {
+        unsigned long long i0 = 0;
+        if (leader) i0 = atomicAdd(counter, (unsigned long long)CHUNK);
+        if (T == 1) {
+            i0 = __shfl_sync(0xffffffffu, i0, 0);
+        } else {
+            if (leader) s_claim[team] = i0;
+            team_sync<T>(team);
+            i0 = s_claim[team];
+            team_sync<T>(team);
+        }
+        if (i0 >= items) break;
+        const unsigned long long i1 = min(i0 + CHUNK, (unsigned long long)items);
+        for (unsigned long long it = i0; it < i1; it++) {
+            const uint64_t j = TIER == 1 ? it : a.list1[it];
+            unsigned long long width;
+            const int st = team_rr<MODEL, C, T>(a, a.sid0 + j, hash, queue, slot, ctl, budget, wt,
+                                                team, &width, &live);
+            const int tail = min(T == 1 ? __shfl_sync(0xffffffffu, ((volatile int*)ctl)[0], 0)
+                                        : ((volatile int*)ctl)[0],
+                                 C::Q);
+            team_sync<T>(team);
+            if (st & ST_OVERFLOW) {
+                if (leader) {
+                    unsigned idx = atomicAdd(out_cnt, 1u);
+                    if (idx < a.list_cap)
+                        out_list[idx] = (uint32_t)j;
+                    else
+                        atomicOr(&a.ds->err, TIM_DEV_ERR_OVF_LIST);
+                }
+                for (int i = tl; i < C::H; i += 32 * T) hash[i] = EMPTY;
+                team_sync<T>(team);
+                continue;
+            }
+            if (leader) {
+                wsum += width;
+                memb += tail;
+                if (st & ST_COVERED) cov++;
+                if (kap) {
+                    unsigned long long kf = kappa_fixed(kappa_fp64(width, a.m, a.k));
+                    k_lo += kf;
+                    if (k_lo < kf) k_hi++;
+                }
+            }
+            if (emit) {
+                unsigned long long base = 0;
+                if (leader) base = atomicAdd(&a.ds->pool_used, (unsigned long long)tail);
+                if (T == 1) {
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                } else {
+                    if (leader) s_claim[team] = base;
+                    team_sync<T>(team);
+                    base = s_claim[team];
+                }
+                if (base + tail <= a.pool_cap) {
+                    for (int i = tl; i < tail; i += 32 * T) {
+                        a.pool[base + i] = queue[i];
+                        a.pool_sid[base + i] = (uint32_t)j;
+                    }
+                    if (leader) {
+                        a.set_start[j] = base;
+                        a.set_len[j] = (uint32_t)tail;
+                        a.set_width[j] = width;
+                    }
+                } else if (leader) {
+                    atomicOr(&a.ds->err, TIM_DEV_ERR_POOL);
+                }
+            }
+            for (int i = tl; i < tail; i += 32 * T) hash[slot[i]] = EMPTY;
+            team_sync<T>(team);
+        }
+    }
+    live = warp_sum_u64(live);
+    if (lane == 0 && live) atomicAdd(&a.ds->live[TIER - 1], live);
+    if (leader) {
+        if (kap) atomic_add_u128(&a.ds->ksum_lo, &a.ds->ksum_hi, k_lo, k_hi);
+        if (wsum) {
+            atomicAdd(&a.ds->wsum, wsum);
+            atomicAdd(&a.ds->width[TIER - 1], wsum);
+        }
+        if (cov) atomicAdd(&a.ds->covered, cov);
+        if (memb) atomicAdd(&a.ds->memb[TIER - 1], memb);
+    }
+}
+
+// ---------------------------------------------------------- tier 3 (LT chains)
+
+// One CTA per listed set; warp 0 walks the chain with a visited bitmap and a queue of
+// up to n members in global memory.
+__global__ void __launch_bounds__(BIG_THREADS) rr_lt_chain_kernel(SampleArgs a) {
+    __shared__ unsigned long long s_j;
+    __shared__ int s_tail, s_status;
+    __shared__ unsigned long long s_width, s_base;
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint32_t* bitmap = a.big_bitmap + (uint64_t)blockIdx.x * a.big_words;
+    uint32_t* queue = a.big_queue + (uint64_t)blockIdx.x * a.n;
+    const bool emit = a.flags & SAMPLE_EMIT, kap = a.flags & SAMPLE_KAPPA,
+               cover = a.flags & SAMPLE_COVER;
+    unsigned long long k_lo = 0, k_hi = 0, wsum = 0, cov = 0, live = 0, memb = 0;
+    const unsigned nlist = min(((volatile unsigned*)&a.ds->cnt2)[0], a.list_cap);
+    for (;;) {
+        if (tid == 0) s_j = atomicAdd(&a.ds->next3, 1ull);
+        __syncthreads();
+        unsigned long long idx = s_j;
+        if (idx >= nlist) break;
+        uint64_t j = a.list2[idx];
+        uint64_t sid = a.sid0 + j;
+        uint32_t root = rr_root(sid, a.n, a.K);
+        if (tid == 0) {
+            atomicOr(&bitmap[root >> 5], 1u << (root & 31));
+            queue[0] = root;
+            s_tail = 1;
+            s_status = (cover && marked(a.seed_mark, root)) ? ST_COVERED : 0;
+            s_width = 0;
+        }
+        __syncthreads();
+        if (tid < 32) {
+            uint32_t v = root;
+            unsigned long long width = 0;
+            int tail = 1;
+            int status = s_status;
+            for (uint64_t guard = 0; guard <= a.n && !status; guard++) {
+                uint64_t beg = __ldg(a.rowptr + v), end = __ldg(a.rowptr + v + 1);
+                width += end - beg;
+                if (beg == end) break;
+                uint32_t x = draw(a, sid, v, TIM_TAG_LT).x;
+                uint64_t jj = warp_lt_search(a.thr, beg, end, x, lane);
+                if (jj >= end) break;
+                uint32_t u = __ldg(a.src + jj);
+                int fresh = 0;
+                if (lane == 0) {
+                    live++;
+                    uint32_t bit = 1u << (u & 31);
+                    uint32_t old = atomicOr(&bitmap[u >> 5], bit);
+                    fresh = !(old & bit);
+                    if (fresh) queue[tail] = u;
+                }
+                fresh = __shfl_sync(0xffffffffu, fresh, 0);
+                if (!fresh) break;
+                tail++;
+                if (cover && marked(a.seed_mark, u)) status |= ST_COVERED;
+                v = u;
+            }
+            __syncwarp();
+            if (lane == 0) {
+                s_width = width;
+                s_tail = tail;
+                s_status = status;
+            }
+        }
+        __syncthreads();
+        const int tail = s_tail;
+        const unsigned long long width = s_width;
+        if (tid == 0) {
+            wsum += width;
+            memb += tail;
+            if (s_status & ST_COVERED) cov++;
+            if (kap) {
+                unsigned long long kf = kappa_fixed(kappa_fp64(width, a.m, a.k));
+                k_lo += kf;
+                if (k_lo < kf) k_hi++;
+            }
+            if (emit) s_base = atomicAdd(&a.ds->pool_used, (unsigned long long)tail);
+        }
+        __syncthreads();
+        if (emit) {
+            unsigned long long base = s_base;
+            if (base + tail <= a.pool_cap) {
+                for (int i = tid; i < tail; i += BIG_THREADS) {
+                    a.pool[base + i] = queue[i];
+                    a.pool_sid[base + i] = (uint32_t)j;
+                }
+                if (tid == 0) {
+                    a.set_start[j] = base;
+                    a.set_len[j] = (uint32_t)tail;
+                    a.set_width[j] = width;
+                }
+            } else if (tid == 0) {
+                atomicOr(&a.ds->err, TIM_DEV_ERR_POOL);
+            }
+        }
+        for (int i = tid; i < tail; i += BIG_THREADS) {
+            uint32_t u = queue[i];
+            atomicAnd(&bitmap[u >> 5], ~(1u << (u & 31)));
+        }
+        __syncthreads();
+    }
+    if (tid == 0) {
+        if (kap && (k_lo || k_hi)) atomic_add_u128(&a.ds->ksum_lo, &a.ds->ksum_hi, k_lo, k_hi);
+        if (wsum) {
+            atomicAdd(&a.ds->wsum, wsum);
+            atomicAdd(&a.ds->width[2], wsum);
+        }
+        if (cov) atomicAdd(&a.ds->covered, cov);
+        if (memb) atomicAdd(&a.ds->memb[2], memb);
+        if (live) atomicAdd(&a.ds->live[2], live);
+    }
+}
+
+template <int MODEL, class C, int TIER, int T>
+int occupancy(size_t smem) {
+    int nb = 0;
+    auto k = rr_team_kernel<MODEL, C, TIER, T>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, WARPS * 32, smem) != cudaSuccess ||
+        nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
+}
+
+int launch_tier1(tim_ctx* ctx, const SampleArgs& a, unsigned grid, size_t smem) {
+    if (ctx->model == TIM_IC)
+        rr_team_kernel<TIM_IC, Tier1, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
+    else
+        rr_team_kernel<TIM_LT, Tier1, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
+    LAUNCH_CHECK(ctx, "rr_team_kernel (tier 1)");
+    return TIM_OK;
+}
+
+int launch_tier2(tim_ctx* ctx, const SampleArgs& a, unsigned grid, int T) {
+    if (ctx->model == TIM_LT || T == 1) {
+        if (ctx->model == TIM_IC)
+            rr_team_kernel<TIM_IC, Tier2, 2, 1><<<grid, WARPS * 32, 0, ctx->stream>>>(a);
+        else
+            rr_team_kernel<TIM_LT, Tier2, 2, 1><<<grid, WARPS * 32, 0, ctx->stream>>>(a);
+    } else if (T == 2) {
+        rr_team_kernel<TIM_IC, Tier2, 2, 2><<<grid, WARPS * 32, 0, ctx->stream>>>(a);
+    } else if (T == 4) {
+        rr_team_kernel<TIM_IC, Tier2, 2, 4><<<grid, WARPS * 32, 0, ctx->stream>>>(a);
+    } else {
+        rr_team_kernel<TIM_IC, Tier2, 2, 8><<<grid, WARPS * 32, 0, ctx->stream>>>(a);
+    }
+    LAUNCH_CHECK(ctx, "rr_team_kernel (tier 2)");
+    return TIM_OK;
+}
+
+}  // namespace
+
+int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    const uint64_t count = req.count;
+    const bool emit = req.flags & SAMPLE_EMIT;
+    if (count > 0xFFFFFFF0ull) return tim_fail(ctx, TIM_ERR_ARG, "too many RR sets in one call");
+    // per-set arrays grow to the next power of two so that the doubling rounds of
+    // Algorithm 2 do not reallocate every round
+    uint64_t cap_sets = 1024;
+    while (cap_sets < count + 1) cap_sets <<= 1;
+    if (emit) {
+        TIM_TRY(tim_ensure(ctx, ctx->set_start, cap_sets * sizeof(uint64_t)));
+        TIM_TRY(tim_ensure(ctx, ctx->set_len, cap_sets * sizeof(uint32_t)));
+        TIM_TRY(tim_ensure(ctx, ctx->set_width, cap_sets * sizeof(uint64_t)));
+        uint64_t want = cap_sets * 8 + 4096;
+        if (ctx->pool.bytes < want * sizeof(uint32_t)) {
+            TIM_TRY(tim_ensure(ctx, ctx->pool, want * sizeof(uint32_t)));
+            TIM_TRY(tim_ensure(ctx, ctx->pool_sid, want * sizeof(uint32_t)));
+        }
+    }
+    const uint32_t list_cap = (uint32_t)(count + 1);
+    TIM_TRY(tim_ensure(ctx, ctx->ovf_list, (size_t)cap_sets * sizeof(uint32_t)));
+    TIM_TRY(tim_ensure(ctx, ctx->ovf_list2, (size_t)cap_sets * sizeof(uint32_t)));
+
+    // tier 2 arena: one slot per resident warp, hash regions kept EMPTY between sets
+    const size_t smem1 = (size_t)WARPS * Tier1::WORDS * sizeof(uint32_t);
+    const int nb1 = ctx->model == TIM_IC ? occupancy<TIM_IC, Tier1, 1, 1>(smem1)
+                                         : occupancy<TIM_LT, Tier1, 1, 1>(smem1);
+    const int nb2 = ctx->model == TIM_IC ? occupancy<TIM_IC, Tier2, 2, 1>(0)
+                                         : occupancy<TIM_LT, Tier2, 2, 1>(0);
+    const unsigned grid1 = (unsigned)(ctx->num_sms * nb1);
+    const unsigned grid2 = (unsigned)(ctx->num_sms * nb2);
+    const size_t arena_bytes = (size_t)grid2 * WARPS * Tier2::WORDS * sizeof(uint32_t);
+    void* prev_arena = ctx->arena.p;
+    TIM_TRY(tim_ensure(ctx, ctx->arena, arena_bytes));
+    if (ctx->arena.p != prev_arena || !ctx->arena_clean) {
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->arena.p, 0xFF, ctx->arena.bytes, ctx->stream));
+        ctx->arena_clean = true;
+    }
+    // tier 3 LT slots: a bitmap of n bits and a queue of n entries each, at most ~2 GiB
+    const uint64_t words = (uint64_t)(ctx->n + 31) / 32 + 1;
+    int slots = 0;
+    if (ctx->model == TIM_LT) {
+        const uint64_t per_slot = (words + (uint64_t)ctx->n) * sizeof(uint32_t);
+        slots = ctx->num_sms;
+        const uint64_t budget = 2ull << 30;
+        if ((uint64_t)slots * per_slot > budget)
+            slots = (int)std::max<uint64_t>(1, budget / per_slot);
+        void* prev_bm = ctx->big_bitmap.p;
+        TIM_TRY(tim_ensure(ctx, ctx->big_bitmap, (size_t)slots * words * sizeof(uint32_t)));
+        TIM_TRY(tim_ensure(ctx, ctx->big_queue,
+                           (size_t)slots * (uint64_t)ctx->n * sizeof(uint32_t)));
+        if (ctx->big_bitmap.p != prev_bm || !ctx->big_bitmap_clean) {
+            CUDA_TRY(ctx, cudaMemsetAsync(ctx->big_bitmap.p, 0, ctx->big_bitmap.bytes, ctx->stream));
+            ctx->big_bitmap_clean = true;
+        }
+    }
+    SampleArgs a;
+    a.rowptr = (const uint64_t*)ctx->rowptr.p;
+    a.src = (const uint32_t*)ctx->src.p;
+    a.thr = (const uint32_t*)ctx->thr.p;
+    a.n = (uint64_t)ctx->n;
+    a.m = (uint64_t)ctx->m;
+    a.K = tim_philox_keys(req.seed);
+    a.sid0 = req.sid0;
+    a.count = count;
+    a.flags = req.flags;
+    a.k = req.k;
+    a.seed_mark = req.seed_mark;
+    a.ds = tim_dscal(ctx);
+    a.list1 = (uint32_t*)ctx->ovf_list.p;
+    a.list2 = (uint32_t*)ctx->ovf_list2.p;
+    a.list_cap = list_cap;
+    a.arena = (uint32_t*)ctx->arena.p;
+    a.big_bitmap = (uint32_t*)ctx->big_bitmap.p;
+    a.big_queue = (uint32_t*)ctx->big_queue.p;
+    a.big_words = words;
+    a.set_start = (uint64_t*)ctx->set_start.p;
+    a.set_len = (uint32_t*)ctx->set_len.p;
+    a.set_width = (uint64_t*)ctx->set_width.p;
+    a.width_budget = ctx->width_budget;
+    for (int attempt = 0; attempt < 4; attempt++) {
+        a.pool = (uint32_t*)ctx->pool.p;
+        a.pool_sid = (uint32_t*)ctx->pool_sid.p;
+        a.pool_cap = emit ? ctx->pool.bytes / sizeof(uint32_t) : 0;
+        TIM_TRY(tim_zero_scalars(ctx));
+        uint64_t live3 = 0;
+        if (count > 0) {
+            cudaEventRecord(ctx->kev[0], ctx->stream);
+            TIM_TRY(launch_tier1(ctx, a, grid1, smem1));
+            cudaEventRecord(ctx->kev[1], ctx->stream);
+            // team size of tier 2: intra-set parallelism when the listed sets are few
+            int T = 1;
+            if (ctx->model == TIM_IC) {
+                TIM_TRY(tim_read_scalars(ctx));
+                const uint64_t listed = ctx->h_scal->cnt1;
+                const uint64_t slots1 = (uint64_t)grid2 * WARPS;
+                T = ctx->team_size;
+                if (T <= 0) {
+                    T = 1;
+                    while (T < 8 && listed * 2 < slots1 / T) T *= 2;
+                }
+                ctx->last_team = T;
+            }
+            TIM_TRY(launch_tier2(ctx, a, grid2, T));
+            cudaEventRecord(ctx->kev[2], ctx->stream);
+            if (ctx->model == TIM_IC) {
+                TIM_TRY(tim_read_scalars(ctx));
+                const unsigned n3 = std::min(ctx->h_scal->cnt2, list_cap);
+                TIM_TRY(tim_bulk_ic(ctx, req, a.list2, n3, a.pool, a.pool_sid, a.pool_cap, &live3));
+            } else {
+                rr_lt_chain_kernel<<<slots, BIG_THREADS, 0, ctx->stream>>>(a);
+                LAUNCH_CHECK(ctx, "rr_lt_chain_kernel");
+            }
+            cudaEventRecord(ctx->kev[3], ctx->stream);
+        }
+        TIM_TRY(tim_read_scalars(ctx));
+        DevScalars& h = *ctx->h_scal;
+        if (ctx->model == TIM_IC) h.live[2] = live3;
+        if (h.err & TIM_DEV_ERR_POOL) {
+            uint64_t need = h.pool_used + h.pool_used / 16 + 4096;
+            tim_free(ctx->pool);
+            tim_free(ctx->pool_sid);
+            TIM_TRY(tim_ensure(ctx, ctx->pool, need * sizeof(uint32_t)));
+            TIM_TRY(tim_ensure(ctx, ctx->pool_sid, need * sizeof(uint32_t)));
+            continue;
+        }
+        if (h.err) {
+            ctx->arena_clean = ctx->big_bitmap_clean = false;
+            return tim_fail(ctx, TIM_ERR_CUDA, "device error flags set by the RR sampler");
+        }
+        if (count > 0) {
+            float t[3] = {0.f, 0.f, 0.f};
+            for (int i = 0; i < 3; i++) cudaEventElapsedTime(&t[i], ctx->kev[i], ctx->kev[i + 1]);
+            const uint64_t sets[3] = {count - h.cnt1, (uint64_t)h.cnt1 - h.cnt2, h.cnt2};
+            tim_profile& P = ctx->prof;
+            uint64_t* L[3] = {&P.pass1_launches, &P.pass2_launches, &P.pass3_launches};
+            double* T[3] = {&P.pass1_ms, &P.pass2_ms, &P.pass3_ms};
+            uint64_t* S[3] = {&P.pass1_sets, &P.pass2_sets, &P.pass3_sets};
+            uint64_t* W[3] = {&P.pass1_width, &P.pass2_width, &P.pass3_width};
+            uint64_t* V[3] = {&P.pass1_live, &P.pass2_live, &P.pass3_live};
+            uint64_t* M[3] = {&P.pass1_members, &P.pass2_members, &P.pass3_members};
+            for (int i = 0; i < 3; i++) {
+                *L[i] += 1;
+                *T[i] += t[i];
+                *S[i] += sets[i];
+                *W[i] += h.width[i];
+                *V[i] += h.live[i];
+                *M[i] += h.memb[i];
+            }
+        }
+        if (res) {
+            res->ksum = ((unsigned __int128)h.ksum_hi << 64) | h.ksum_lo;
+            res->wsum = h.wsum;
+            res->live = h.live[0] + h.live[1] + h.live[2];
+            res->covered = h.covered;
+            res->members = emit ? h.pool_used : 0;
+            res->big_sets = h.cnt1;
+        }
+        if (emit) {
+            ctx->n_sets = count;
+            ctx->members = h.pool_used;
+        }
+        return TIM_OK;
+    }
+    return tim_fail(ctx, TIM_ERR_OOM, "RR-set store kept overflowing");
+}

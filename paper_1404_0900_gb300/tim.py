@@ -1,0 +1,291 @@
+"""ctypes binding of libtim.so (include/tim.h): the same names, argument marshalling only.
+
+Every computation runs in the CUDA library; this module converts numpy arrays / torch
+tensors to pointers and status codes to exceptions. There is no fallback: if the
+library is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+TIM_IC, TIM_LT = 0, 1
+TIM_OK = 0
+
+STATUS = {0: "TIM_OK", -1: "TIM_ERR_ARG", -2: "TIM_ERR_OOM", -3: "TIM_ERR_OVERFLOW",
+          -4: "TIM_ERR_TIMEOUT", -5: "TIM_ERR_CUDA", -6: "TIM_ERR_STATE"}
+
+HEADER = os.path.join(_build.ROOT, "include", "tim.h")
+
+
+class TimError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class tim_stats(C.Structure):
+    _fields_ = [
+        ("kpt_round", C.c_int), ("kpt_last_round", C.c_int),
+        ("kpt_star", C.c_double), ("kpt_prime", C.c_double), ("kpt_plus", C.c_double),
+        ("eps_prime", C.c_double), ("lambda_", C.c_double),
+        ("theta_prime", C.c_uint64), ("covered_prime", C.c_uint64), ("theta", C.c_uint64),
+        ("covered", C.c_uint64), ("sets_total", C.c_uint64), ("members_select", C.c_uint64),
+        ("width_total", C.c_uint64), ("width_select", C.c_uint64),
+        ("ms_kpt", C.c_double), ("ms_refine", C.c_double), ("ms_select_sample", C.c_double),
+        ("ms_select_greedy", C.c_double), ("ms_total", C.c_double),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["lambda"] = d.pop("lambda_")
+        return d
+
+
+class tim_profile(C.Structure):
+    _fields_ = [
+        ("pass1_launches", C.c_uint64), ("pass1_ms", C.c_double),
+        ("pass1_sets", C.c_uint64), ("pass1_width", C.c_uint64), ("pass1_live", C.c_uint64),
+        ("pass1_members", C.c_uint64),
+        ("pass2_launches", C.c_uint64), ("pass2_ms", C.c_double),
+        ("pass2_sets", C.c_uint64), ("pass2_width", C.c_uint64), ("pass2_live", C.c_uint64),
+        ("pass2_members", C.c_uint64),
+        ("pass3_launches", C.c_uint64), ("pass3_ms", C.c_double),
+        ("pass3_sets", C.c_uint64), ("pass3_width", C.c_uint64), ("pass3_live", C.c_uint64),
+        ("pass3_members", C.c_uint64),
+    ]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+_P = C.c_void_p
+_SIGS = {
+    "tim_create": (C.c_int, [C.POINTER(_P), C.c_int, _P]),
+    "tim_destroy": (C.c_int, [_P]),
+    "tim_strerror": (C.c_char_p, [C.c_int]),
+    "tim_last_error_message": (C.c_char_p, [_P]),
+    "tim_load_graph": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, C.c_int]),
+    "tim_load_graph_device": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, C.c_int]),
+    "tim_sample_rr": (C.c_int, [_P, C.c_uint64, C.c_uint64, C.c_uint64, _P]),
+    "tim_get_rr": (C.c_int, [_P, _P, _P, C.c_uint64, _P]),
+    "tim_rr_size": (C.c_int, [_P, _P, _P]),
+    "tim_kappa_sum": (C.c_int, [_P, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, _P, _P, _P]),
+    "tim_kpt_estimate": (C.c_int, [_P, C.c_int, C.c_double, C.c_uint64, _P, _P]),
+    "tim_refine_kpt": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_uint64, _P, _P, _P]),
+    "tim_node_select": (C.c_int, [_P, C.c_int, _P, _P, _P]),
+    "tim_coverage_counts": (C.c_int, [_P, _P]),
+    "tim_covered_count": (C.c_int, [_P, _P, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, _P]),
+    "tim_run": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_uint64, _P, _P, _P,
+                          C.c_uint64]),
+    "tim_run_tim": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_uint64, _P, _P, _P]),
+    "tim_launch_count": (C.c_uint64, [_P]),
+    "tim_get_profile": (C.c_int, [_P, _P, C.c_int]),
+    "tim_set_width_budget": (C.c_int, [_P, C.c_uint64]),
+    "tim_set_team_size": (C.c_int, [_P, C.c_int]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib(build_if_missing: bool = True) -> C.CDLL:
+    """Load libtim.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is None:
+        path = _build.build() if build_if_missing else _build.LIB
+        if not os.path.exists(path):
+            raise OSError(f"libtim.so not found at {path}")
+        L = C.CDLL(path)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/tim.h declares."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"^\S.*?\b(tim_[a-z_0-9]+)\(", text, flags=re.M)))
+
+
+def _ptr(a) -> C.c_void_p:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data_as(_P)
+    if hasattr(a, "data_ptr"):  # torch tensor
+        return _P(a.data_ptr())
+    return _P(int(a))
+
+
+def _check(ctx, rc: int):
+    if rc != TIM_OK:
+        msg = lib().tim_last_error_message(ctx).decode() if ctx else ""
+        raise TimError(rc, msg or lib().tim_strerror(rc).decode())
+
+
+# ---------------------------------------------------------------- the calls
+
+def tim_create(device: int = 0, stream=None):
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (own stream)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    h = _P()
+    rc = lib().tim_create(C.byref(h), device, _P(stream) if stream else None)
+    if rc != TIM_OK:
+        raise TimError(rc, lib().tim_strerror(rc).decode())
+    return h
+
+
+def tim_destroy(ctx):
+    _check(None, lib().tim_destroy(ctx))
+
+
+def tim_load_graph(ctx, n: int, rowptr, dst, weight, model: int):
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    weight = np.ascontiguousarray(weight, dtype=np.float32)
+    _check(ctx, lib().tim_load_graph(ctx, n, dst.shape[0], _ptr(rowptr), _ptr(dst),
+                                     _ptr(weight), model))
+
+
+def tim_load_graph_device(ctx, n: int, m: int, d_rowptr, d_dst, d_weight, model: int):
+    """Device arrays: torch CUDA tensors (int64, int32, float32) or raw pointers."""
+    _check(ctx, lib().tim_load_graph_device(ctx, n, m, _ptr(d_rowptr), _ptr(d_dst),
+                                            _ptr(d_weight), model))
+
+
+def tim_sample_rr(ctx, theta: int, seed: int, first_set_id: int) -> int:
+    tot = C.c_uint64()
+    _check(ctx, lib().tim_sample_rr(ctx, theta, seed, first_set_id, C.byref(tot)))
+    return tot.value
+
+
+def tim_rr_size(ctx) -> tuple[int, int]:
+    a, b = C.c_uint64(), C.c_uint64()
+    _check(ctx, lib().tim_rr_size(ctx, C.byref(a), C.byref(b)))
+    return a.value, b.value
+
+
+def tim_get_rr(ctx):
+    """The RR-set store as (off int64[theta+1], mem int32, widths int64[theta])."""
+    ns, nm = tim_rr_size(ctx)
+    off = np.zeros(ns + 1, dtype=np.int64)
+    mem = np.zeros(max(nm, 1), dtype=np.int32)
+    widths = np.zeros(max(ns, 1), dtype=np.int64)
+    _check(ctx, lib().tim_get_rr(ctx, _ptr(off), _ptr(mem), nm, _ptr(widths)))
+    return off, mem[:nm], widths[:ns]
+
+
+def tim_kappa_sum(ctx, k: int, seed: int, first_set_id: int, count: int) -> tuple[int, int]:
+    hi, lo, ws = C.c_uint64(), C.c_uint64(), C.c_uint64()
+    _check(ctx, lib().tim_kappa_sum(ctx, k, seed, first_set_id, count, C.byref(hi), C.byref(lo),
+                                    C.byref(ws)))
+    return (hi.value << 64) | lo.value, ws.value
+
+
+def tim_kpt_estimate(ctx, k: int, ell: float, seed: int) -> tuple[float, int]:
+    kpt, rnd = C.c_double(), C.c_int()
+    _check(ctx, lib().tim_kpt_estimate(ctx, k, ell, seed, C.byref(kpt), C.byref(rnd)))
+    return kpt.value, rnd.value
+
+
+def tim_refine_kpt(ctx, k: int, ell: float, eps: float, seed: int) -> tuple[float, float, int]:
+    kp, ep, tp = C.c_double(), C.c_double(), C.c_uint64()
+    _check(ctx, lib().tim_refine_kpt(ctx, k, ell, eps, seed, C.byref(kp), C.byref(ep),
+                                     C.byref(tp)))
+    return kp.value, ep.value, tp.value
+
+
+def tim_node_select(ctx, k: int):
+    seeds = np.zeros(k, dtype=np.int32)
+    frac, cov = C.c_double(), C.c_uint64()
+    _check(ctx, lib().tim_node_select(ctx, k, _ptr(seeds), C.byref(frac), C.byref(cov)))
+    return seeds, frac.value, cov.value
+
+
+def tim_coverage_counts(ctx, n: int) -> np.ndarray:
+    counts = np.zeros(n, dtype=np.int32)
+    _check(ctx, lib().tim_coverage_counts(ctx, _ptr(counts)))
+    return counts
+
+
+def tim_covered_count(ctx, seeds, seed: int, first_set_id: int, count: int) -> int:
+    s = np.ascontiguousarray(seeds, dtype=np.int32)
+    cov = C.c_uint64()
+    _check(ctx, lib().tim_covered_count(ctx, _ptr(s), s.shape[0], seed, first_set_id, count,
+                                        C.byref(cov)))
+    return cov.value
+
+
+def tim_run(ctx, k: int, eps: float, ell: float, seed: int, theta_override: int = 0,
+            seeds_out: np.ndarray | None = None):
+    """TIM+ end to end. Returns (seeds int32[k], covered fraction, stats dict)."""
+    seeds = seeds_out if seeds_out is not None else np.zeros(k, dtype=np.int32)
+    frac = C.c_double()
+    st = tim_stats()
+    _check(ctx, lib().tim_run(ctx, k, eps, ell, seed, _ptr(seeds), C.byref(frac), C.byref(st),
+                              theta_override))
+    return seeds, frac.value, st.as_dict()
+
+
+def tim_run_tim(ctx, k: int, eps: float, ell: float, seed: int):
+    """Plain TIM end to end. Returns (seeds, covered fraction, stats dict)."""
+    seeds = np.zeros(k, dtype=np.int32)
+    frac = C.c_double()
+    st = tim_stats()
+    _check(ctx, lib().tim_run_tim(ctx, k, eps, ell, seed, _ptr(seeds), C.byref(frac),
+                                  C.byref(st)))
+    return seeds, frac.value, st.as_dict()
+
+
+def tim_launch_count(ctx) -> int:
+    return int(lib().tim_launch_count(ctx))
+
+
+def tim_set_width_budget(ctx, budget: int):
+    _check(ctx, lib().tim_set_width_budget(ctx, budget))
+
+
+def tim_set_team_size(ctx, warps: int):
+    _check(ctx, lib().tim_set_team_size(ctx, warps))
+
+
+def tim_get_profile(ctx, reset: bool = False) -> dict:
+    p = tim_profile()
+    _check(ctx, lib().tim_get_profile(ctx, C.byref(p), 1 if reset else 0))
+    return p.as_dict()
+
+
+class Engine:
+    """Owns one tim_ctx; closes it on exit."""
+
+    def __init__(self, device: int = 0, stream=None):
+        self.ctx = tim_create(device, stream)
+
+    def close(self):
+        if self.ctx:
+            tim_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,252 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle, on the same
+seeded inputs. RR sets (sorted), widths, coverage counts, covered counts and seed
+sets are compared bit for bit; the kappa sums are exact integers, so KPT*, KPT', KPT+
+and theta are compared exactly too (theta may differ by one only when lambda / KPT+
+lies within 1e-9 relative of an integer)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1404_0900_gb300 import inputs, tim
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def eng():
+    import torch
+    assert torch.cuda.is_available()
+    e = tim.Engine(0)
+    yield e
+    e.close()
+
+
+def _load(eng, g, w, model):
+    tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, model)
+    return O.load_graph(g.n, g.rowptr, g.dst, w, model)
+
+
+def _sets(off, mem):
+    return [np.sort(mem[off[j]:off[j + 1]]) for j in range(len(off) - 1)]
+
+
+def _compare_store(eng, og, seed, sid0, count):
+    tot = tim.tim_sample_rr(eng.ctx, count, seed, sid0)
+    off, mem, wid = tim.tim_get_rr(eng.ctx)
+    roff, rmem, rwid = O.sample(og, seed, sid0, count)
+    assert tot == rmem.shape[0]
+    assert np.array_equal(np.diff(off), np.diff(roff))
+    assert np.array_equal(wid, rwid)
+    for a, b in zip(_sets(off, mem), _sets(roff, rmem)):
+        assert np.array_equal(a, b)
+    return off
+
+
+GRAPHS = {
+    "rmat12_wc": lambda: (inputs.rmat(12, seed=5), "wc"),
+    "rmat14_wc": lambda: (inputs.rmat(14, seed=1), "wc"),
+    "rand_p1": lambda: (inputs.random_small(3000, 9000, seed=2), "p1"),
+    "star": lambda: (inputs.star_in(40000), "wc"),
+    "chain": lambda: (inputs.chain(3000), "p1"),
+    "rmat10_tri": lambda: (inputs.rmat(10, seed=9), "tri"),
+}
+
+
+def _weights(g, kind, model):
+    if kind == "p1":  # LT weights must sum to <= 1 per node: use 1/indeg there
+        return inputs.constant(g, 1.0) if model == O.IC else inputs.lt_inverse_indegree(g)
+    if kind == "tri":
+        return inputs.trivalency(g, seed=3) if model == O.IC else inputs.lt_random_normalised(g, 3)
+    return inputs.weighted_cascade(g)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("model", [O.IC, O.LT])
+def test_rr_sets_bit_exact(eng, name, model):
+    g, kind = GRAPHS[name]()
+    w = _weights(g, kind, model)
+    og = _load(eng, g, w, model)
+    count = 3000 if name in ("rand_p1", "chain") else 20000
+    _compare_store(eng, og, 11, O.make_sid(3, 0, 0), count)
+    # a second seed and a set-id range that does not start at zero
+    _compare_store(eng, og, 12345678901, (5 << 40) + 17, 777)
+
+
+@pytest.mark.parametrize("budget,team", [(0, 0), (64, 1), (1 << 40, 0), (0, 2), (0, 4),
+                                         (0, 8), (300, 8)])
+def test_ic_rr_sets_bit_exact_for_any_split(eng, budget, team):
+    # which pass expands a set, and how many warps share it, must not matter
+    g = inputs.rmat(13, seed=3)
+    w = inputs.weighted_cascade(g)
+    og = _load(eng, g, w, O.IC)
+    tim.tim_set_width_budget(eng.ctx, budget)
+    tim.tim_set_team_size(eng.ctx, team)
+    try:
+        _compare_store(eng, og, 5, O.make_sid(3, 0, 0), 6000)
+        k = O.kappa_sum(og, 10, 5, O.make_sid(1, 3, 0), 4000)
+        assert tim.tim_kappa_sum(eng.ctx, 10, 5, O.make_sid(1, 3, 0), 4000) == k
+        seeds = np.array([0, 1, 2, 5], dtype=np.int32)
+        assert tim.tim_covered_count(eng.ctx, seeds, 5, 77, 5000) == \
+            O.covered_count(og, 5, 77, 5000, seeds)
+    finally:
+        tim.tim_set_width_budget(eng.ctx, 16384)
+        tim.tim_set_team_size(eng.ctx, 0)
+
+
+def test_rr_sets_ragged_and_empty(eng):
+    g = inputs.rmat(11, seed=4)
+    w = inputs.weighted_cascade(g)
+    og = _load(eng, g, w, O.IC)
+    for count in (0, 1, 2, 31, 33, 4097):
+        tot = tim.tim_sample_rr(eng.ctx, count, 3, 99)
+        off, mem, wid = tim.tim_get_rr(eng.ctx)
+        assert off.shape[0] == count + 1
+        if count:
+            roff, rmem, rwid = O.sample(og, 3, 99, count)
+            assert np.array_equal(wid, rwid) and tot == rmem.shape[0]
+
+
+def test_edge_free_and_tiny_graphs(eng):
+    for g in (inputs.from_edges(2, []), inputs.from_edges(2, [(0, 1)]),
+              inputs.from_edges(5, [(4, 0), (3, 0)])):
+        for model in (O.IC, O.LT):
+            w = inputs.constant(g, 1.0 if model == O.IC else 0.5)
+            og = _load(eng, g, w, model)
+            _compare_store(eng, og, 1, 0, 500)
+
+
+@pytest.mark.parametrize("model", [O.IC, O.LT])
+def test_kappa_sum_exact(eng, model):
+    g = inputs.rmat(13, seed=7)
+    w = inputs.weighted_cascade(g)
+    og = _load(eng, g, w, model)
+    for k, count in ((1, 5000), (10, 20000), (50, 7777), (1000, 3000)):
+        sid0 = O.make_sid(1, 4, 0)
+        got = tim.tim_kappa_sum(eng.ctx, k, 5, sid0, count)
+        want = O.kappa_sum(og, k, 5, sid0, count)
+        assert got == want, (k, got, want)
+
+
+@pytest.mark.parametrize("model", [O.IC, O.LT])
+def test_coverage_counts_and_covered_count(eng, model):
+    g = inputs.rmat(12, seed=8)
+    w = inputs.weighted_cascade(g)
+    og = _load(eng, g, w, model)
+    sid0 = O.make_sid(3, 0, 0)
+    tim.tim_sample_rr(eng.ctx, 30000, 21, sid0)
+    counts = tim.tim_coverage_counts(eng.ctx, g.n)
+    roff, rmem, _ = O.sample(og, 21, sid0, 30000)
+    seeds, cov, counts0 = O.greedy(g.n, roff, rmem, 7)
+    assert np.array_equal(counts.astype(np.int64), counts0)
+    gs, frac, gcov = tim.tim_node_select(eng.ctx, 7)
+    assert np.array_equal(gs, seeds) and gcov == cov
+    assert frac == cov / 30000
+    c = tim.tim_covered_count(eng.ctx, seeds[:3], 21, O.make_sid(2, 0, 0), 25000)
+    assert c == O.covered_count(og, 21, O.make_sid(2, 0, 0), 25000, seeds[:3])
+
+
+@pytest.mark.parametrize("k", [1, 3, 16])
+def test_greedy_ties_and_k_equals_n(eng, k):
+    g = inputs.complete(16)
+    og = _load(eng, g, inputs.constant(g, 0.0), O.IC)
+    tim.tim_sample_rr(eng.ctx, 64, 2, 0)
+    roff, rmem, _ = O.sample(og, 2, 0, 64)
+    seeds, cov, _ = O.greedy(g.n, roff, rmem, k)
+    gs, _, gcov = tim.tim_node_select(eng.ctx, k)
+    assert np.array_equal(gs, seeds) and gcov == cov
+
+
+def _theta_equal(a, b, lam, kpt):
+    if a == b:
+        return True
+    x = lam / kpt
+    return abs(a - b) == 1 and abs(x - round(x)) <= 1e-9 * x
+
+
+@pytest.mark.parametrize("model", [O.IC, O.LT])
+@pytest.mark.parametrize("scale,k,eps", [(12, 5, 0.5), (14, 10, 0.5)])
+def test_tim_plus_end_to_end(eng, model, scale, k, eps):
+    g = inputs.rmat(scale, seed=1)
+    w = inputs.weighted_cascade(g)
+    og = _load(eng, g, w, model)
+    seeds, frac, st = tim.tim_run(eng.ctx, k, eps, 1.0, 1)
+    ref = O.tim_plus(og, k, eps, 1.0, 1)
+    assert st["kpt_round"] == ref.kpt.stop_round
+    assert st["kpt_last_round"] == ref.kpt.last_round
+    assert st["kpt_star"] == ref.kpt.kpt_star
+    assert st["theta_prime"] == ref.refine.theta_prime
+    assert st["covered_prime"] == ref.refine.covered
+    assert abs(st["eps_prime"] - ref.refine.eps_prime) <= 1e-15
+    assert abs(st["kpt_plus"] - ref.refine.kpt_plus) <= 1e-9 * ref.refine.kpt_plus
+    lam = O.lam(g.n, k, eps, 1.0)
+    assert abs(st["lambda"] - lam) <= 1e-9 * lam
+    assert _theta_equal(st["theta"], ref.theta, lam, ref.refine.kpt_plus)
+    if st["theta"] == ref.theta:
+        assert np.array_equal(seeds, ref.seeds)
+        assert st["covered"] == ref.covered
+        assert frac == ref.covered / ref.theta
+        assert st["members_select"] == ref.extra["members"]
+
+
+@pytest.mark.parametrize("model", [O.IC, O.LT])
+def test_plain_tim_end_to_end(eng, model):
+    g = inputs.rmat(12, seed=2)
+    w = inputs.weighted_cascade(g)
+    og = _load(eng, g, w, model)
+    seeds, frac, st = tim.tim_run_tim(eng.ctx, 4, 0.5, 1.0, 3)
+    ref = O.tim(og, 4, 0.5, 1.0, 3)
+    assert st["kpt_star"] == ref.kpt.kpt_star
+    lam = O.lam(g.n, 4, 0.5, 1.0)
+    assert _theta_equal(st["theta"], ref.theta, lam, ref.kpt.kpt_star)
+    if st["theta"] == ref.theta:
+        assert np.array_equal(seeds, ref.seeds) and st["covered"] == ref.covered
+
+
+def test_kpt_strongly_connected_closed_form(eng):
+    g = inputs.complete(12)
+    _load(eng, g, inputs.constant(g, 1.0), O.IC)
+    kpt, rnd = tim.tim_kpt_estimate(eng.ctx, 3, 1.0, 5)
+    assert rnd == 1 and kpt == g.n / 2
+
+
+def test_invalid_inputs_are_rejected(eng):
+    rowptr = np.array([0, 2, 3, 3], dtype=np.int64)
+    for dst in ([1, 0, 2], [1, 1, 2], [1, 7, 2]):
+        with pytest.raises(tim.TimError) as ei:
+            tim.tim_load_graph(eng.ctx, 3, rowptr, np.array(dst, np.int32),
+                               np.full(3, 0.5, np.float32), O.IC)
+        assert ei.value.code == -1
+    with pytest.raises(tim.TimError):
+        tim.tim_load_graph(eng.ctx, 3, rowptr, np.array([1, 2, 0], np.int32),
+                           np.array([0.5, 1.5, 0.5], np.float32), O.IC)
+    g = inputs.star_in(4)
+    with pytest.raises(tim.TimError):
+        tim.tim_load_graph(eng.ctx, 4, g.rowptr, g.dst, np.full(3, 0.5, np.float32), O.LT)
+    with pytest.raises(tim.TimError) as ei:
+        tim.tim_kpt_estimate(eng.ctx, 1, 1.0, 1)  # graph was not loaded
+    assert ei.value.code == -6
+    g = inputs.rmat(8)
+    _load(eng, g, inputs.weighted_cascade(g), O.IC)
+    with pytest.raises(tim.TimError):
+        tim.tim_node_select(eng.ctx, g.n + 1)
+
+
+def test_device_resident_load_matches_host_load(eng):
+    import torch
+    g = inputs.rmat(12, seed=6)
+    w = inputs.weighted_cascade(g)
+    tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, O.IC)
+    a = tim.tim_sample_rr(eng.ctx, 5000, 4, 0)
+    off_a, mem_a, wid_a = tim.tim_get_rr(eng.ctx)
+    dr = torch.from_numpy(g.rowptr).cuda()
+    dd = torch.from_numpy(g.dst).cuda()
+    dw = torch.from_numpy(w).cuda()
+    torch.cuda.synchronize()
+    tim.tim_load_graph_device(eng.ctx, g.n, g.m, dr, dd, dw, O.IC)
+    b = tim.tim_sample_rr(eng.ctx, 5000, 4, 0)
+    off_b, mem_b, wid_b = tim.tim_get_rr(eng.ctx)
+    assert a == b and np.array_equal(off_a, off_b) and np.array_equal(wid_a, wid_b)
+    for x, y in zip(_sets(off_a, mem_a), _sets(off_b, mem_b)):
+        assert np.array_equal(x, y)
