@@ -89,6 +89,8 @@ _SIGS = {
     "tim_get_profile": (C.c_int, [_P, _P, C.c_int]),
     "tim_set_width_budget": (C.c_int, [_P, C.c_uint64]),
     "tim_set_team_size": (C.c_int, [_P, C.c_int]),
+    "tim_node_select_noalloc": (C.c_int, [C.c_int, _P, C.c_int64, C.c_uint64, _P, _P, C.c_int,
+                                          _P, _P]),
 }
 
 
@@ -247,6 +249,19 @@ def tim_run_tim(ctx, k: int, eps: float, ell: float, seed: int):
     _check(ctx, lib().tim_run_tim(ctx, k, eps, ell, seed, _ptr(seeds), C.byref(frac),
                                   C.byref(st)))
     return seeds, frac.value, st.as_dict()
+
+
+def tim_node_select_noalloc(device: int, stream, n: int, n_sets: int, d_off, d_mem, k: int,
+                            d_seeds, d_covered):
+    """Greedy selection on caller-owned device buffers, without any device allocation
+    by the library (torch CUDA tensors or raw device pointers)."""
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    rc = lib().tim_node_select_noalloc(device, _P(stream) if stream else None, n, n_sets,
+                                       _ptr(d_off), _ptr(d_mem), k, _ptr(d_seeds),
+                                       _ptr(d_covered))
+    if rc != TIM_OK:
+        raise TimError(rc, lib().tim_strerror(rc).decode())
 
 
 def tim_launch_count(ctx) -> int:
