@@ -85,14 +85,6 @@ __device__ __forceinline__ bool marked(const uint32_t* mark, uint32_t u) {
     return (__ldg(mark + (u >> 5)) >> (u & 31)) & 1u;
 }
 
-__device__ __forceinline__ uint32_t pick(uint4 v, int c) {
-    return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
-}
-
-__device__ __forceinline__ bool ic_live(uint32_t x, uint32_t thr) {
-    return thr == 0xFFFFFFFFu || x < thr;
-}
-
 __device__ __forceinline__ unsigned long long warp_sum_u64(unsigned long long v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -163,28 +155,41 @@ __device__ __forceinline__ void team_sync(int team) {
         asm volatile("bar.sync %0, %1;" ::"r"(team + 1), "r"(T * 32) : "memory");
 }
 
-// Coins of the in-CSR positions [4g, 4g + 4) that lie in [beg, end): follow the live
-// in-edges. Returns bit 0 if the set overflowed, bit 1 if it met the seed set.
+// Which of the in-CSR positions 4g .. 4g+3 lie in [beg, end) (bit c = position 4g+c).
+// Positions are 32-bit: the graph loader rejects m >= 2^32.
+__device__ __forceinline__ uint32_t range_mask(uint32_t g, uint32_t beg, uint32_t end) {
+    const uint32_t p0 = g << 2;
+    if (p0 >= beg && p0 + 4u <= end) return 0xFu;
+    const uint32_t lo = beg > p0 ? beg - p0 : 0u;
+    const uint32_t hi = end < p0 + 4u ? end - p0 : 4u;
+    return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+}
+
+// Live coins of one group: bit c set iff word c < thr c, or thr c marks p >= 1.
+__device__ __forceinline__ uint32_t live_mask(uint4 x, uint4 t) {
+    return ((x.x < t.x) | (t.x == 0xFFFFFFFFu) ? 1u : 0u) |
+           ((x.y < t.y) | (t.y == 0xFFFFFFFFu) ? 2u : 0u) |
+           ((x.z < t.z) | (t.z == 0xFFFFFFFFu) ? 4u : 0u) |
+           ((x.w < t.w) | (t.w == 0xFFFFFFFFu) ? 8u : 0u);
+}
+
+// Follow the live in-edges of group g given their mask: insert each source. Returns
+// bit 0 if the set overflowed, bit 1 if it met the seed set.
 template <class C>
-__device__ __forceinline__ int ic_group(const SampleArgs& a, uint64_t g, uint64_t beg,
-                                        uint64_t end, uint4 x, uint4 tv, uint32_t* hash,
-                                        uint32_t* queue, uint16_t* slot, int* ctl,
-                                        unsigned long long& live) {
+__device__ __noinline__ int follow_live(const SampleArgs& a, uint32_t g, uint32_t mask,
+                                        uint32_t* hash, uint32_t* queue, uint16_t* slot,
+                                        int* ctl) {
     int f = 0;
-    const uint64_t p0 = g << 2;
-#pragma unroll
-    for (int c = 0; c < 4; c++) {
-        const uint64_t p = p0 + c;
-        if (p >= beg && p < end && ic_live(pick(x, c), pick(tv, c))) {
-            const uint32_t u = __ldg(a.src + p);
-            live++;
-            const int r = set_insert<C>(hash, queue, slot, ctl, u);
-            if (r == INS_FULL) {
-                f |= 1;
-            } else if (r == INS_NEW && (a.flags & SAMPLE_COVER) && marked(a.seed_mark, u)) {
-                atomicOr(&ctl[1], ST_COVERED);
-                f |= 2;
-            }
+    while (mask) {
+        const int c = __ffs(mask) - 1;
+        mask &= mask - 1;
+        const uint32_t u = __ldg(a.src + ((g << 2) + c));
+        const int r = set_insert<C>(hash, queue, slot, ctl, u);
+        if (r == INS_FULL) {
+            f |= 1;
+        } else if (r == INS_NEW && (a.flags & SAMPLE_COVER) && marked(a.seed_mark, u)) {
+            atomicOr(&ctl[1], ST_COVERED);
+            f |= 2;
         }
     }
     return f;
@@ -248,34 +253,42 @@ __device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32
                 break;
             }
             width += dw;
-            const uint32_t ng = end > beg ? (uint32_t)(((end - 1) >> 2) - (beg >> 2) + 1) : 0u;
+            // 32-bit in-CSR positions (m < 2^32)
+            const uint32_t b32 = (uint32_t)beg, e32 = (uint32_t)end;
+            const uint32_t ng = e32 > b32 ? ((e32 - 1) >> 2) - (b32 >> 2) + 1 : 0u;
             const bool big = ng >= BIG_GROUPS;
             int flags = 0;
-            // hubs first: the whole team strides over one in-list at a time
+            // hubs first: the whole team strides over one in-list at a time, two groups in
+            // flight per lane; only the in-list's first and last group need a range mask
             uint32_t bigmask = __ballot_sync(0xffffffffu, big);
             while (bigmask && !(flags & 3)) {
                 const int b = __ffs(bigmask) - 1;
                 bigmask &= bigmask - 1;
-                const uint64_t bb = __shfl_sync(0xffffffffu, beg, b);
-                const uint64_t be = __shfl_sync(0xffffffffu, end, b);
-                const uint64_t g1 = ((be - 1) >> 2) + 1;
-                for (uint64_t g = (bb >> 2) + (uint64_t)(wt * 32 + lane);; g += 64 * T) {
-                    const bool v0 = g < g1, v1 = g + 32 * T < g1;
-                    if (!__any_sync(0xffffffffu, v0)) break;
-                    uint4 x0 = make_uint4(0, 0, 0, 0), t0 = x0, x1 = x0, t1 = x0;
+                const uint32_t bb = __shfl_sync(0xffffffffu, b32, b);
+                const uint32_t be = __shfl_sync(0xffffffffu, e32, b);
+                const uint32_t gfirst = bb >> 2, glast = (be - 1) >> 2;
+                for (uint32_t gb = gfirst + (uint32_t)(wt * 32); gb <= glast; gb += 64u * T) {
+                    const uint32_t g0 = gb + lane, g1 = gb + 32u * T + lane;
+                    const bool v0 = g0 <= glast, v1 = g1 <= glast;
+                    uint32_t m0 = 0, m1 = 0;
                     if (v0) {
-                        x0 = philox4x32_10(s0, s1, (uint32_t)g, TIM_TAG_IC, K);
-                        t0 = __ldg(thr4 + g);
+                        const uint4 x = philox4x32_10(s0, s1, g0, TIM_TAG_IC, K);
+                        const uint4 t = __ldg(thr4 + g0);
+                        m0 = live_mask(x, t);
                     }
                     if (v1) {
-                        x1 = philox4x32_10(s0, s1, (uint32_t)(g + 32 * T), TIM_TAG_IC, K);
-                        t1 = __ldg(thr4 + g + 32 * T);
+                        const uint4 x = philox4x32_10(s0, s1, g1, TIM_TAG_IC, K);
+                        const uint4 t = __ldg(thr4 + g1);
+                        m1 = live_mask(x, t);
                     }
-                    if (v0) flags |= ic_group<C>(a, g, bb, be, x0, t0, hash, queue, slot, ctl, live);
-                    if (v1)
-                        flags |= ic_group<C>(a, g + 32 * T, bb, be, x1, t1, hash, queue, slot, ctl,
-                                             live);
-                    if (__any_sync(0xffffffffu, flags & 3)) break;
+                    if (__any_sync(0xffffffffu, (m0 | m1) != 0u)) {
+                        if (m0 && (g0 == gfirst || g0 == glast)) m0 &= range_mask(g0, bb, be);
+                        if (m1 && (g1 == gfirst || g1 == glast)) m1 &= range_mask(g1, bb, be);
+                        live += __popc(m0) + __popc(m1);
+                        if (m0) flags |= follow_live<C>(a, g0, m0, hash, queue, slot, ctl);
+                        if (m1) flags |= follow_live<C>(a, g1, m1, hash, queue, slot, ctl);
+                        if (__any_sync(0xffffffffu, flags & 3)) break;
+                    }
                 }
                 flags = __reduce_or_sync(0xffffffffu, flags);
             }
@@ -297,16 +310,22 @@ __device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32
                     const uint32_t ic = __shfl_sync(0xffffffffu, incl, own + sft - 1);
                     if (ic <= t) own += sft;
                 }
-                const uint64_t o_beg = __shfl_sync(0xffffffffu, beg, own);
-                const uint64_t o_end = __shfl_sync(0xffffffffu, end, own);
+                const uint32_t o_beg = __shfl_sync(0xffffffffu, b32, own);
+                const uint32_t o_end = __shfl_sync(0xffffffffu, e32, own);
                 const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own);
+                uint32_t m = 0, g = 0;
                 if (t < total) {
-                    const uint64_t g = (o_beg >> 2) + (t - o_excl);
-                    const uint4 x = philox4x32_10(s0, s1, (uint32_t)g, TIM_TAG_IC, K);
+                    g = (o_beg >> 2) + (t - o_excl);
+                    const uint4 x = philox4x32_10(s0, s1, g, TIM_TAG_IC, K);
                     const uint4 tv = __ldg(thr4 + g);
-                    flags |= ic_group<C>(a, g, o_beg, o_end, x, tv, hash, queue, slot, ctl, live);
+                    m = live_mask(x, tv);
+                    if (m) m &= range_mask(g, o_beg, o_end);
                 }
-                flags = __reduce_or_sync(0xffffffffu, flags);
+                if (__any_sync(0xffffffffu, m != 0u)) {
+                    live += __popc(m);
+                    if (m) flags |= follow_live<C>(a, g, m, hash, queue, slot, ctl);
+                    flags = __reduce_or_sync(0xffffffffu, flags);
+                }
             }
             team_sync<T>(team);
             head += nb;
