@@ -29,6 +29,12 @@ sys.path.insert(0, ROOT)
 from paper_1404_0900_gb300 import inputs  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# DRAM bytes (read + write) per examined in-edge of the IC sampler passes, from the ncu
+# capture of `bench.py --mode sample --scale 18 --theta 300000` (dram__bytes_read.sum +
+# dram__bytes_write.sum / examined in-edges of that launch); used to scale the traffic of
+# one full-size launch in proportion to its work. None where no capture exists for the
+# current kernel.
+DRAM_BYTES_PER_EDGE = {1: 33.64e6 / 328604055, 2: 704.2e6 / 2766776059, 3: None}
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
@@ -48,6 +54,11 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU time of the oracle baseline sample")
+    p.add_argument("--mode", choices=["timplus", "sample"], default="timplus",
+                   help="timplus: the TIM+ step (default); sample: only RR-set generation "
+                        "(tim_sample_rr of --theta NodeSelection sets), for profiling")
+    p.add_argument("--theta", type=int, default=1_000_000)
+    p.add_argument("--model", choices=["ic", "lt"], default="ic")
     return p.parse_args(argv)
 
 
@@ -277,6 +288,8 @@ def run_ours(args):
         peak, peak_src = FALLBACK_HBM_GBS, "fallback"
     ms_dom = p[f"pass{dom}_ms"]
     achieved = alg_bytes / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
+    ratio = DRAM_BYTES_PER_EDGE.get(dom)
+    traffic = ratio * p[f"pass{dom}_width"] / launches_dom if ratio else None
     ic = per_model[tim.TIM_IC][-1]
     lt = per_model[tim.TIM_LT][-1]
     line = {
@@ -306,7 +319,9 @@ def run_ours(args):
                      "achieved": achieved, "peak": peak, "peak_source": peak_src,
                      "unit": "GB/s", "frac": achieved / peak,
                      "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
-                     "traffic": None},
+                     "traffic": traffic,
+                     "traffic_note": "DRAM bytes per launch scaled by examined in-edges from "
+                                     "the R-MAT scale-18 ncu capture"},
         "sampler_profile": {"IC": prof_ic, "LT": prof_lt},
         "clocks": clk,
         "gpu_launches": launches,
@@ -396,8 +411,53 @@ def run_reference(args):
                     "d2h_bytes_per_step": 0}}
 
 
+def run_sample_only(args):
+    """Time tim_sample_rr alone: --theta RR sets with NodeSelection set ids."""
+    import torch
+
+    from paper_1404_0900_gb300 import tim
+    g = inputs.rmat(args.scale, seed=1)
+    model = tim.TIM_IC if args.model == "ic" else tim.TIM_LT
+    w = inputs.weighted_cascade(g) if model == tim.TIM_IC else inputs.lt_inverse_indegree(g)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    sid0 = 3 << 56
+    with tim.Engine(0, stream) as eng:
+        tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, model)
+        for _ in range(args.warmup):
+            tim.tim_sample_rr(eng.ctx, args.theta, args.seed, sid0)
+        tim.tim_get_profile(eng.ctx, reset=True)
+        ms = 0.0
+        for _ in range(args.steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            tim.tim_sample_rr(eng.ctx, args.theta, args.seed, sid0)
+            e1.record(stream)
+            e1.synchronize()
+            ms += e0.elapsed_time(e1)
+        prof = tim.tim_get_profile(eng.ctx)
+    passes = {}
+    for i in (1, 2, 3):
+        t = prof[f"pass{i}_ms"]
+        b = sampler_bytes(prof, i)
+        passes[f"pass{i}"] = {"ms": t, "sets": prof[f"pass{i}_sets"],
+                              "width": prof[f"pass{i}_width"], "algorithmic_bytes": b,
+                              "GB/s": b / (t / 1e3) / 1e9 if t > 0 else 0.0}
+    width = sum(prof[f"pass{i}_width"] for i in (1, 2, 3))
+    return {"mode": "sample", "model": args.model, "scale": args.scale, "theta": args.theta,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "RR sets/s": args.theta * args.steps / (ms / 1e3),
+            "GTEPS (in-edges examined)": width / (ms / 1e3) / 1e9, "passes": passes}
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.mode == "sample" and args.impl == "ours":
+        print(json.dumps(run_sample_only(args)), flush=True)
+        return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
         print(json.dumps(line), flush=True)
