@@ -59,6 +59,8 @@ struct tim_ctx {
     DevBuf rowptr;  // uint64[n+1]
     DevBuf src;     // uint32[m + 4]
     DevBuf thr;     // uint32[m + 4] IC thresholds or LT inclusive cumulative thresholds
+    DevBuf node_thr;  // IC: uint64[n], low word = threshold shared by all in-edges of v,
+                      // bit 32 set when they do share one (empty in-lists included)
 
     // RR-set store
     uint64_t n_sets = 0;

@@ -127,6 +127,23 @@ __global__ void lt_prefix_kernel(const uint64_t* __restrict__ rowptr, int64_t n,
     }
 }
 
+// IC: does every in-edge of v carry the same threshold? One warp per node.
+__global__ void uniform_thr_kernel(const uint64_t* __restrict__ rowptr, int64_t n,
+                                   const uint32_t* __restrict__ thr,
+                                   unsigned long long* __restrict__ node_thr) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        const uint64_t a = rowptr[v], b = rowptr[v + 1];
+        const uint32_t t0 = b > a ? thr[a] : 0u;
+        bool same = true;
+        for (uint64_t j = a + lane; j < b && same; j += 32) same = thr[j] == t0;
+        same = __all_sync(0xffffffffu, same);
+        if (lane == 0) node_thr[v] = (unsigned long long)t0 | (same ? (1ull << 32) : 0ull);
+    }
+}
+
 }  // namespace
 
 int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
@@ -191,6 +208,13 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
                     (const uint32_t*)vals.p, d_w, (uint32_t*)ctx->thr.p, &ds->err);
                 ctx->launches++;
             }
+        }
+        if (model == TIM_IC) {
+            if ((rc = tim_ensure(ctx, ctx->node_thr, (size_t)(n + 1) * 8))) break;
+            uniform_thr_kernel<<<G, T, 0, ctx->stream>>>(
+                (const uint64_t*)ctx->rowptr.p, n, (const uint32_t*)ctx->thr.p,
+                (unsigned long long*)ctx->node_thr.p);
+            ctx->launches++;
         }
         if ((rc = tim_cuda_check(ctx, cudaGetLastError(), "graph kernels"))) break;
         if ((rc = tim_read_scalars(ctx))) break;

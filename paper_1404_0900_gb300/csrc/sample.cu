@@ -54,6 +54,7 @@ struct SampleArgs {
     const uint64_t* rowptr;
     const uint32_t* src;
     const uint32_t* thr;
+    const unsigned long long* node_thr;  // IC: per-node shared threshold (bit 32: shared)
     uint64_t n, m;
     PhiloxKeys K;
     uint64_t sid0, count;
@@ -165,6 +166,12 @@ __device__ __forceinline__ uint32_t range_mask(uint32_t g, uint32_t beg, uint32_
     return ((1u << hi) - 1u) & ~((1u << lo) - 1u);
 }
 
+// Live coins of one group whose 4 in-edges share threshold t (0 < t < 0xFFFFFFFF).
+__device__ __forceinline__ uint32_t live_mask_shared(uint4 x, uint32_t t) {
+    return (x.x < t ? 1u : 0u) | (x.y < t ? 2u : 0u) | (x.z < t ? 4u : 0u) |
+           (x.w < t ? 8u : 0u);
+}
+
 // Live coins of one group: bit c set iff word c < thr c, or thr c marks p >= 1.
 __device__ __forceinline__ uint32_t live_mask(uint4 x, uint4 t) {
     return ((x.x < t.x) | (t.x == 0xFFFFFFFFu) ? 1u : 0u) |
@@ -260,26 +267,43 @@ __device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32
             int flags = 0;
             // hubs first: the whole team strides over one in-list at a time, two groups in
             // flight per lane; only the in-list's first and last group need a range mask
+            // a node's in-edges often share one threshold (weighted cascade: p = 1/indeg);
+            // then no threshold is loaded, t = 0 needs no coins and t = 2^32-1 (p >= 1)
+            // makes every in-edge live without a draw
+            unsigned long long nt = 0;
+            if (lane < nb) nt = __ldg(a.node_thr + queue[head + lane]);
             uint32_t bigmask = __ballot_sync(0xffffffffu, big);
             while (bigmask && !(flags & 3)) {
                 const int b = __ffs(bigmask) - 1;
                 bigmask &= bigmask - 1;
                 const uint32_t bb = __shfl_sync(0xffffffffu, b32, b);
                 const uint32_t be = __shfl_sync(0xffffffffu, e32, b);
+                const unsigned long long bt = __shfl_sync(0xffffffffu, nt, b);
+                const bool shared = (bt >> 32) != 0;
+                const uint32_t t = (uint32_t)bt;
+                if (shared && t == 0u) continue;
                 const uint32_t gfirst = bb >> 2, glast = (be - 1) >> 2;
                 for (uint32_t gb = gfirst + (uint32_t)(wt * 32); gb <= glast; gb += 64u * T) {
                     const uint32_t g0 = gb + lane, g1 = gb + 32u * T + lane;
                     const bool v0 = g0 <= glast, v1 = g1 <= glast;
                     uint32_t m0 = 0, m1 = 0;
-                    if (v0) {
-                        const uint4 x = philox4x32_10(s0, s1, g0, TIM_TAG_IC, K);
-                        const uint4 t = __ldg(thr4 + g0);
-                        m0 = live_mask(x, t);
-                    }
-                    if (v1) {
-                        const uint4 x = philox4x32_10(s0, s1, g1, TIM_TAG_IC, K);
-                        const uint4 t = __ldg(thr4 + g1);
-                        m1 = live_mask(x, t);
+                    if (shared) {
+                        if (t == 0xFFFFFFFFu) {
+                            m0 = v0 ? 0xFu : 0u;
+                            m1 = v1 ? 0xFu : 0u;
+                        } else {
+                            if (v0) m0 = live_mask_shared(philox4x32_10(s0, s1, g0, TIM_TAG_IC, K), t);
+                            if (v1) m1 = live_mask_shared(philox4x32_10(s0, s1, g1, TIM_TAG_IC, K), t);
+                        }
+                    } else {
+                        if (v0) {
+                            const uint4 x = philox4x32_10(s0, s1, g0, TIM_TAG_IC, K);
+                            m0 = live_mask(x, __ldg(thr4 + g0));
+                        }
+                        if (v1) {
+                            const uint4 x = philox4x32_10(s0, s1, g1, TIM_TAG_IC, K);
+                            m1 = live_mask(x, __ldg(thr4 + g1));
+                        }
                     }
                     if (__any_sync(0xffffffffu, (m0 | m1) != 0u)) {
                         if (m0 && (g0 == gfirst || g0 == glast)) m0 &= range_mask(g0, bb, be);
@@ -313,12 +337,17 @@ __device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32
                 const uint32_t o_beg = __shfl_sync(0xffffffffu, b32, own);
                 const uint32_t o_end = __shfl_sync(0xffffffffu, e32, own);
                 const uint32_t o_excl = __shfl_sync(0xffffffffu, excl, own);
+                const unsigned long long o_nt = __shfl_sync(0xffffffffu, nt, own);
                 uint32_t m = 0, g = 0;
                 if (t < total) {
                     g = (o_beg >> 2) + (t - o_excl);
-                    const uint4 x = philox4x32_10(s0, s1, g, TIM_TAG_IC, K);
-                    const uint4 tv = __ldg(thr4 + g);
-                    m = live_mask(x, tv);
+                    const uint32_t ot = (uint32_t)o_nt;
+                    if (!(o_nt >> 32))
+                        m = live_mask(philox4x32_10(s0, s1, g, TIM_TAG_IC, K), __ldg(thr4 + g));
+                    else if (ot == 0xFFFFFFFFu)
+                        m = 0xFu;
+                    else if (ot != 0u)
+                        m = live_mask_shared(philox4x32_10(s0, s1, g, TIM_TAG_IC, K), ot);
                     if (m) m &= range_mask(g, o_beg, o_end);
                 }
                 if (__any_sync(0xffffffffu, m != 0u)) {
@@ -693,6 +722,7 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
     a.rowptr = (const uint64_t*)ctx->rowptr.p;
     a.src = (const uint32_t*)ctx->src.p;
     a.thr = (const uint32_t*)ctx->thr.p;
+    a.node_thr = (const unsigned long long*)ctx->node_thr.p;
     a.n = (uint64_t)ctx->n;
     a.m = (uint64_t)ctx->m;
     a.K = tim_philox_keys(req.seed);

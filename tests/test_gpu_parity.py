@@ -51,6 +51,7 @@ GRAPHS = {
     "star": lambda: (inputs.star_in(40000), "wc"),
     "chain": lambda: (inputs.chain(3000), "p1"),
     "rmat10_tri": lambda: (inputs.rmat(10, seed=9), "tri"),
+    "rmat13_mixed": lambda: (inputs.rmat(13, seed=4), "mixed"),
 }
 
 
@@ -59,6 +60,16 @@ def _weights(g, kind, model):
         return inputs.constant(g, 1.0) if model == O.IC else inputs.lt_inverse_indegree(g)
     if kind == "tri":
         return inputs.trivalency(g, seed=3) if model == O.IC else inputs.lt_random_normalised(g, 3)
+    if kind == "mixed":
+        # in-lists with one shared probability (even nodes), per-edge probabilities (odd
+        # nodes), some p = 0 and p = 1 in-lists
+        w = inputs.weighted_cascade(g).copy()
+        if model == O.IC:
+            odd = (g.dst % 2) == 1
+            w[odd] = inputs.trivalency(g, seed=5)[odd]
+            w[g.dst % 7 == 0] = 1.0
+            w[g.dst % 11 == 0] = 0.0
+        return w
     return inputs.weighted_cascade(g)
 
 
