@@ -54,7 +54,10 @@ def parse_args(argv=None):
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-seconds", type=float, default=12.0,
                    help="target CPU time of the oracle baseline sample")
-    p.add_argument("--mode", choices=["timplus", "sample"], default="timplus",
+    p.add_argument("--no-batch", action="store_true",
+                   help="skip the 64-query batched-vs-plain comparison")
+    p.add_argument("--batch-queries", type=int, default=64)
+    p.add_argument("--mode", choices=["timplus", "sample", "batch"], default="timplus",
                    help="timplus: the TIM+ step (default); sample: only RR-set generation "
                         "(tim_sample_rr of --theta NodeSelection sets), for profiling")
     p.add_argument("--theta", type=int, default=1_000_000)
@@ -330,6 +333,8 @@ def run_ours(args):
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, g, w_ic, w_lt,
                                             n_ic=ic["sets_total"], n_lt=lt["sets_total"])
+    if not args.no_batch and world == 1:
+        line["batched_vs_plain"] = run_batch_compare(args)
     return line
 
 
@@ -453,10 +458,88 @@ def run_sample_only(args):
             "GTEPS (in-edges examined)": width / (ms / 1e3) / 1e9, "passes": passes}
 
 
+def batch_specs(nq: int):
+    """The batched workload: query q has an R-MAT graph of scale U{12..20} (graph seed
+    q + 1), k ~ U{1..50}, eps from {0.1, 0.2, 0.3, 0.5}; even q use IC weighted cascade,
+    odd q LT with 1/indeg in-weights."""
+    rng = np.random.Generator(np.random.Philox(20140900))
+    out = []
+    for q in range(nq):
+        scale = int(rng.integers(12, 21))
+        k = int(rng.integers(1, 51))
+        eps = float(rng.choice([0.1, 0.2, 0.3, 0.5]))
+        out.append((scale, q + 1, q % 2, k, eps))
+    return out
+
+
+def run_batch_compare(args, reps: int = 2):
+    """End-to-end TIM+ seconds for nq queries: one after another with tim_run (plain)
+    against tim_run_batch (batched), both on graphs already loaded; the seeds of every
+    query must be the same both ways."""
+    import torch
+
+    from paper_1404_0900_gb300 import tim
+    specs = batch_specs(args.batch_queries)
+    graphs = []
+    for scale, gseed, model, k, eps in specs:
+        g = inputs.rmat(scale, seed=gseed)
+        w = inputs.weighted_cascade(g) if model == 0 else inputs.lt_inverse_indegree(g)
+        graphs.append((g, w, model, k, eps))
+    stream = torch.cuda.Stream()
+    engines = [tim.Engine(0, stream) for _ in graphs]
+    try:
+        for (g, w, model, _, _), e in zip(graphs, engines):
+            tim.tim_load_graph(e.ctx, g.n, g.rowptr, g.dst, w, model)
+        queries = [{"ctx": e.ctx, "k": k, "eps": eps, "ell": 1.0, "tag": i + 1}
+                   for i, (e, (_, _, _, k, eps)) in enumerate(zip(engines, graphs))]
+        for i, e in enumerate(engines):
+            tim.tim_set_query_tag(e.ctx, i + 1)
+
+        def plain():
+            outs = []
+            for q in queries:
+                seeds, _, st = tim.tim_run(q["ctx"], q["k"], q["eps"], 1.0, args.seed)
+                outs.append((seeds, st))
+            return outs
+
+        def timed(fn):
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            return out, e0.elapsed_time(e1)
+
+        plain()
+        tim.tim_run_batch(queries, args.seed)
+        t_plain, t_batch = [], []
+        for _ in range(reps):
+            p_out, tp = timed(plain)
+            (b_out, bst), tb = timed(lambda: tim.tim_run_batch(queries, args.seed))
+            t_plain.append(tp)
+            t_batch.append(tb)
+        same = all(np.array_equal(p[0], b[0]) and p[1]["theta"] == b[2]["theta"]
+                   for p, b in zip(p_out, b_out))
+        sets = sum(st["sets_total"] for _, st in p_out)
+    finally:
+        for e in engines:
+            e.close()
+    tp, tb = min(t_plain), min(t_batch)
+    return {"queries": len(specs), "scales": "R-MAT U{12..20}", "plain_ms": tp,
+            "batched_ms": tb, "speedup": tp / tb, "seeds_identical": bool(same),
+            "rr_sets": sets, "batched_rr_sets_per_s": sets / (tb / 1e3),
+            "batched_phase_ms": {k: bst[k] for k in ("ms_kpt", "ms_refine", "ms_select_sample",
+                                                     "ms_select_greedy")}}
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.mode == "sample" and args.impl == "ours":
         print(json.dumps(run_sample_only(args)), flush=True)
+        return
+    if args.mode == "batch" and args.impl == "ours":
+        print(json.dumps(run_batch_compare(args)), flush=True)
         return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

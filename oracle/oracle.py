@@ -57,7 +57,7 @@ def lib():
             "or_lambda_prime": (dbl, [i64, dbl, dbl]),
             "or_c_i": (i64, [i64, dbl, i32]),
             "or_kpt_rounds": (i32, [i64]),
-            "or_kpt_estimate": (i32, [P, P, P, i64, i64, i32, i32, dbl, u64, i32,
+            "or_kpt_estimate": (i32, [P, P, P, i64, i64, i32, i32, dbl, u64, u64, i32,
                                       P, P, P, P, P, P]),
             "or_greedy": (i64, [i64, i64, P, P, i32, P, P]),
             "or_covered_count": (i64, [P, P, P, i64, i64, i32, u64, u64, i64, P, i32]),
@@ -264,10 +264,11 @@ class KptResult:
     sets_generated: int = 0
 
 
-def kpt_estimation(g: OracleGraph, k: int, ell: float, seed: int, nthreads: int = 0) -> KptResult:
+def kpt_estimation(g: OracleGraph, k: int, ell: float, seed: int, nthreads: int = 0,
+                   tag: int = 0) -> KptResult:
     out = [np.zeros(1, dtype=t) for t in (np.float64, np.int32, np.int32, np.int64, np.uint64,
                                           np.uint64)]
-    rc = lib().or_kpt_estimate(*g.args(), k, ell, seed, nthreads, *[_p(a) for a in out])
+    rc = lib().or_kpt_estimate(*g.args(), k, ell, seed, tag, nthreads, *[_p(a) for a in out])
     if rc != 0:
         raise MemoryError
     last_round = int(out[2][0])
@@ -290,10 +291,10 @@ class RefineResult:
 
 
 def refine_kpt(g: OracleGraph, k: int, ell: float, eps: float, seed: int, kpt: KptResult,
-               nthreads: int = 0) -> RefineResult:
+               nthreads: int = 0, tag: int = 0) -> RefineResult:
     # line 1: R' = the RR sets of the last iteration of Algorithm 2
     if kpt.last_round > 0:
-        off, mem, _ = sample(g, seed, make_sid(PHASE_KPT, kpt.last_round, 0), kpt.last_c,
+        off, mem, _ = sample(g, seed, make_sid(PHASE_KPT, kpt.last_round, tag << 32), kpt.last_c,
                              nthreads)
     else:
         off, mem = np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32)
@@ -304,7 +305,7 @@ def refine_kpt(g: OracleGraph, k: int, ell: float, eps: float, seed: int, kpt: K
     lp = lam_prime(g.n, ep, ell)
     theta_p = int(math.ceil(lp / kpt.kpt_star))
     # lines 9-10: fraction of theta' fresh RR sets covered by S'_k
-    cov = covered_count(g, seed, make_sid(PHASE_REFINE, 0, 0), theta_p, seeds_p, nthreads)
+    cov = covered_count(g, seed, make_sid(PHASE_REFINE, 0, tag << 32), theta_p, seeds_p, nthreads)
     f = cov / theta_p
     # lines 11-12
     kpt_prime = f * g.n / (1.0 + ep)
@@ -322,8 +323,9 @@ class SelectResult:
     members: int
 
 
-def node_selection(g: OracleGraph, k: int, theta: int, seed: int, nthreads: int = 0) -> SelectResult:
-    off, mem, _ = sample(g, seed, make_sid(PHASE_SELECT, 0, 0), theta, nthreads)
+def node_selection(g: OracleGraph, k: int, theta: int, seed: int, nthreads: int = 0,
+                   tag: int = 0) -> SelectResult:
+    off, mem, _ = sample(g, seed, make_sid(PHASE_SELECT, 0, tag << 32), theta, nthreads)
     seeds, cov, _ = greedy(g.n, off, mem, k)
     return SelectResult(seeds=seeds, covered=cov, theta=theta, members=int(mem.shape[0]))
 
@@ -348,20 +350,21 @@ class TimResult:
 
 
 def tim_plus(g: OracleGraph, k: int, eps: float, ell: float, seed: int, nthreads: int = 0,
-             theta_override: int | None = None) -> TimResult:
-    kpt = kpt_estimation(g, k, ell, seed, nthreads)
-    ref = refine_kpt(g, k, ell, eps, seed, kpt, nthreads)
+             theta_override: int | None = None, tag: int = 0) -> TimResult:
+    kpt = kpt_estimation(g, k, ell, seed, nthreads, tag)
+    ref = refine_kpt(g, k, ell, eps, seed, kpt, nthreads, tag)
     theta = theta_override if theta_override is not None else theta_from(g.n, k, eps, ell,
                                                                           ref.kpt_plus)
-    sel = node_selection(g, k, theta, seed, nthreads)
+    sel = node_selection(g, k, theta, seed, nthreads, tag)
     return TimResult(seeds=sel.seeds, covered=sel.covered, theta=theta, kpt=kpt, refine=ref,
                      extra={"members": sel.members})
 
 
-def tim(g: OracleGraph, k: int, eps: float, ell: float, seed: int, nthreads: int = 0) -> TimResult:
-    kpt = kpt_estimation(g, k, ell, seed, nthreads)
+def tim(g: OracleGraph, k: int, eps: float, ell: float, seed: int, nthreads: int = 0,
+        tag: int = 0) -> TimResult:
+    kpt = kpt_estimation(g, k, ell, seed, nthreads, tag)
     theta = theta_from(g.n, k, eps, ell, kpt.kpt_star)
-    sel = node_selection(g, k, theta, seed, nthreads)
+    sel = node_selection(g, k, theta, seed, nthreads, tag)
     return TimResult(seeds=sel.seeds, covered=sel.covered, theta=theta, kpt=kpt, refine=None,
                      extra={"members": sel.members})
 

@@ -37,8 +37,9 @@
  *   - Loop bound of Algorithm 2: i = 1 .. floor(log2 n) - 1; c_i rounded up.
  *   - theta, theta' rounded up.
  *   - Greedy ties: largest count, then smallest node id; chosen nodes excluded.
- *   - Set ids: sid = (phase << 56) | (round << 48) | j, with phase 1 = KptEstimation,
- *     2 = RefineKPT's theta' sets, 3 = NodeSelection.
+ *   - Set ids: sid = (phase << 56) | (round << 48) | (tag << 32) | j, with phase 1 =
+ *     KptEstimation, 2 = RefineKPT's theta' sets, 3 = NodeSelection; the tag (0 by
+ *     default) separates queries that share a seed.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off -fopenmp -shared -fPIC.
  * Floating point contraction must stay off so that every FP64 operation is a single
@@ -563,7 +564,8 @@ int or_kpt_rounds(int64_t n) {
  * KPT*. Also returns the last executed round (the R' of Algorithm 3) and that
  * round's exact fixed-point kappa sum and set count. */
 int or_kpt_estimate(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
-                    int64_t m, int model, int k, double ell, uint64_t seed, int nthreads,
+                    int64_t m, int model, int k, double ell, uint64_t seed, uint64_t tag,
+                    int nthreads,
                     double* kpt_star, int* stop_round, int* last_round, int64_t* last_c,
                     uint64_t* last_sum_hi, uint64_t* last_sum_lo) {
     int rounds = or_kpt_rounds(n);
@@ -575,8 +577,8 @@ int or_kpt_estimate(const int64_t* rowptr, const int32_t* src, const uint32_t* t
     for (int i = 1; i <= rounds; i++) {
         int64_t c = or_c_i(n, ell, i);
         uint64_t hi, lo;
-        int rc = or_kappa_sum(rowptr, src, thr, n, m, model, k, seed, or_make_sid(PHASE_KPT, i, 0),
-                              c, &hi, &lo, NULL, nthreads);
+        int rc = or_kappa_sum(rowptr, src, thr, n, m, model, k, seed,
+                              or_make_sid(PHASE_KPT, i, tag << 32), c, &hi, &lo, NULL, nthreads);
         if (rc) return rc;
         *last_round = i;
         *last_c = c;

@@ -200,7 +200,7 @@ int tim_destroy(tim_ctx* ctx) {
                       &ctx->scratch_a, &ctx->scratch_b, &ctx->scratch_c, &ctx->scratch_d,
                       &ctx->scratch_e, &ctx->scal,      &ctx->bulk_bitmap, &ctx->bulk_slot,
                       &ctx->bulk_F,    &ctx->bulk_M,    &ctx->bulk_ng,   &ctx->bulk_gp,
-                      &ctx->bulk_scal};
+                      &ctx->bulk_scal, &ctx->batch,     &ctx->greedy_batch};
     for (DevBuf* b : bufs) tim_free(*b);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     for (int i = 0; i < 8; i++)
@@ -217,6 +217,20 @@ uint64_t tim_launch_count(tim_ctx* ctx) { return ctx ? ctx->launches : 0; }
 int tim_set_width_budget(tim_ctx* ctx, uint64_t budget) {
     if (!ctx) return TIM_ERR_ARG;
     ctx->width_budget = budget;
+    return TIM_OK;
+}
+
+int tim_set_query_tag(tim_ctx* ctx, uint32_t tag) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (tag > 0xFFFF) return tim_fail(ctx, TIM_ERR_ARG, "query tag must be < 65536");
+    ctx->query_tag = tag;
+    return TIM_OK;
+}
+
+int tim_set_chunk(tim_ctx* ctx, int sets) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (sets < 1 || sets > 64) return tim_fail(ctx, TIM_ERR_ARG, "chunk must be in [1, 64]");
+    ctx->chunk = sets;
     return TIM_OK;
 }
 
@@ -379,7 +393,7 @@ int tim_kpt_estimate(tim_ctx* ctx, int k, double ell, uint64_t seed, double* kpt
         const uint64_t c = tim_host_c_i(ctx->n, ell, i);
         SampleRequest req;
         req.seed = seed;
-        req.sid0 = make_sid(1, (uint64_t)i, 0);
+        req.sid0 = make_sid(1, (uint64_t)i, (uint64_t)ctx->query_tag << 32);
         req.count = c;
         req.flags = SAMPLE_EMIT | SAMPLE_KAPPA;
         req.k = k;
@@ -425,7 +439,7 @@ int tim_refine_kpt(tim_ctx* ctx, int k, double ell, double eps, uint64_t seed, d
     // lines 9-10
     SampleRequest req;
     req.seed = seed;
-    req.sid0 = make_sid(2, 0, 0);
+    req.sid0 = make_sid(2, 0, (uint64_t)ctx->query_tag << 32);
     req.count = theta_p;
     req.flags = SAMPLE_COVER;
     req.seed_mark = (const uint32_t*)ctx->seed_mark.p;
@@ -515,7 +529,7 @@ static int run_common(tim_ctx* ctx, bool plus, int k, double eps, double ell, ui
     const uint64_t theta = theta_override ? theta_override : (uint64_t)ceil(s.lambda / lower);
     SampleRequest req;
     req.seed = seed;
-    req.sid0 = make_sid(3, 0, 0);
+    req.sid0 = make_sid(3, 0, (uint64_t)ctx->query_tag << 32);
     req.count = theta;
     req.flags = SAMPLE_EMIT;
     SampleResult res;
@@ -558,6 +572,182 @@ int tim_run(tim_ctx* ctx, int k, double eps, double ell, uint64_t seed, int32_t*
 int tim_run_tim(tim_ctx* ctx, int k, double eps, double ell, uint64_t seed, int32_t* seeds,
                 double* covered_fraction, tim_stats* stats) {
     return run_common(ctx, false, k, eps, ell, seed, seeds, covered_fraction, stats, 0);
+}
+
+
+// TIM+ (or TIM) for several queries at once: every phase samples all active queries
+// in one multi-query launch per tier, and the greedy rounds of all queries run as
+// shared launches captured in a CUDA graph. Query q draws from the key of `seed` with
+// set-id tag queries[q].tag, so its result equals tim_run on its context with
+// tim_set_query_tag(ctx, tag) and the same seed.
+int tim_run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_batch_stats* bst) {
+    if (!qs || nq <= 0 || nq > 256) return TIM_ERR_ARG;
+    tim_ctx* owner = qs[0].ctx;
+    if (!owner) return TIM_ERR_ARG;
+    for (int i = 0; i < nq; i++) {
+        tim_ctx* c = qs[i].ctx;
+        if (!c || !c->have_graph) return tim_fail(owner, TIM_ERR_STATE, "query without a graph");
+        if (c->device != owner->device) return tim_fail(owner, TIM_ERR_ARG, "queries on several devices");
+        if (qs[i].k < 1 || qs[i].k > c->n || !(qs[i].eps > 0.0) || !(qs[i].ell > 0.0) ||
+            !qs[i].seeds || qs[i].tag > 0xFFFF)
+            return tim_fail(owner, TIM_ERR_ARG, "need 1 <= k <= n, eps > 0, l > 0, seeds, tag < 65536");
+        for (int j = 0; j < i; j++)
+            if (qs[j].ctx == c) return tim_fail(owner, TIM_ERR_ARG, "one context per query");
+    }
+    DeviceGuard g(owner->device);
+    // the queries' own streams must be idle: the batch runs on the owner's stream
+    for (int i = 0; i < nq; i++) CUDA_TRY(owner, cudaStreamSynchronize(qs[i].ctx->stream));
+    cudaEvent_t* ev = owner->ev;
+    cudaEventRecord(ev[0], owner->stream);
+    std::vector<int> rounds(nq), stop(nq, 0), last(nq, 0);
+    std::vector<uint64_t> last_c(nq, 0), sets(nq, 0), width(nq, 0);
+    std::vector<double> kpt(nq, 1.0);
+    std::vector<char> active(nq, 1);
+    int max_rounds = 0;
+    for (int i = 0; i < nq; i++) {
+        rounds[i] = tim_host_rounds(qs[i].ctx->n);
+        max_rounds = std::max(max_rounds, rounds[i]);
+        qs[i].ctx->n_sets = qs[i].ctx->members = 0;
+        memset(&qs[i].stats, 0, sizeof(tim_stats));
+    }
+    std::vector<MultiQuery> mq;
+    std::vector<int> idx;
+    // Algorithm 2, all queries in lockstep
+    int launched_rounds = 0;
+    for (int r = 1; r <= max_rounds; r++) {
+        mq.clear();
+        idx.clear();
+        for (int i = 0; i < nq; i++) {
+            if (!active[i] || r > rounds[i]) continue;
+            MultiQuery m;
+            m.ctx = qs[i].ctx;
+            m.req.seed = seed;
+            m.req.sid0 = make_sid(1, (uint64_t)r, (uint64_t)qs[i].tag << 32);
+            m.req.count = tim_host_c_i(qs[i].ctx->n, qs[i].ell, r);
+            m.req.flags = SAMPLE_EMIT | SAMPLE_KAPPA;
+            m.req.k = qs[i].k;
+            mq.push_back(m);
+            idx.push_back(i);
+        }
+        if (mq.empty()) break;
+        launched_rounds++;
+        TIM_TRY(tim_sample_multi(owner, mq.data(), (int)mq.size(), seed));
+        for (size_t t = 0; t < mq.size(); t++) {
+            const int i = idx[t];
+            const uint64_t c = mq[t].req.count;
+            last[i] = r;
+            last_c[i] = c;
+            sets[i] += c;
+            width[i] += mq[t].res.wsum;
+            const unsigned __int128 bound = (unsigned __int128)c << (63 - r);
+            if (mq[t].res.ksum > bound) {
+                kpt[i] = (double)qs[i].ctx->n * ldexp((double)mq[t].res.ksum, -63) / (2.0 * (double)c);
+                stop[i] = r;
+                active[i] = 0;
+            }
+        }
+    }
+    cudaEventRecord(ev[1], owner->stream);
+    std::vector<double> kpt_plus(kpt), kpt_prime(nq, 0.0), eps_p(nq, 0.0);
+    std::vector<uint64_t> theta_p(nq, 0), cov_p(nq, 0), width_p(nq, 0);
+    std::vector<tim_ctx*> ctxs(nq);
+    std::vector<int> ks(nq);
+    for (int i = 0; i < nq; i++) {
+        ctxs[i] = qs[i].ctx;
+        ks[i] = qs[i].k;
+    }
+    if (plus) {
+        // Algorithm 3: greedy on every query's R', then theta' fresh sets each
+        TIM_TRY(tim_greedy_batch(owner, ctxs.data(), ks.data(), nq, nullptr, nullptr, true));
+        mq.clear();
+        for (int i = 0; i < nq; i++) {
+            TIM_TRY(tim_mark_seeds(qs[i].ctx, (const int32_t*)qs[i].ctx->seeds_dev.p, qs[i].k));
+            eps_p[i] = tim_host_eps_prime(qs[i].eps, qs[i].k, qs[i].ell);
+            const double lp = tim_host_lambda_prime(qs[i].ctx->n, eps_p[i], qs[i].ell);
+            theta_p[i] = (uint64_t)ceil(lp / kpt[i]);
+            MultiQuery m;
+            m.ctx = qs[i].ctx;
+            m.req.seed = seed;
+            m.req.sid0 = make_sid(2, 0, (uint64_t)qs[i].tag << 32);
+            m.req.count = theta_p[i];
+            m.req.flags = SAMPLE_COVER;
+            m.req.seed_mark = (const uint32_t*)qs[i].ctx->seed_mark.p;
+            mq.push_back(m);
+        }
+        for (int i = 0; i < nq; i++) CUDA_TRY(owner, cudaStreamSynchronize(qs[i].ctx->stream));
+        TIM_TRY(tim_sample_multi(owner, mq.data(), nq, seed));
+        for (int i = 0; i < nq; i++) {
+            cov_p[i] = mq[i].res.covered;
+            width_p[i] = mq[i].res.wsum;
+            const double f = (double)cov_p[i] / (double)theta_p[i];
+            kpt_prime[i] = f * (double)qs[i].ctx->n / (1.0 + eps_p[i]);
+            kpt_plus[i] = std::max(kpt_prime[i], kpt[i]);
+        }
+    }
+    cudaEventRecord(ev[2], owner->stream);
+    // Algorithm 1 for every query
+    std::vector<double> lam(nq);
+    std::vector<uint64_t> theta(nq);
+    mq.clear();
+    for (int i = 0; i < nq; i++) {
+        lam[i] = tim_host_lambda(qs[i].ctx->n, qs[i].k, qs[i].eps, qs[i].ell);
+        theta[i] = (uint64_t)ceil(lam[i] / kpt_plus[i]);
+        MultiQuery m;
+        m.ctx = qs[i].ctx;
+        m.req.seed = seed;
+        m.req.sid0 = make_sid(3, 0, (uint64_t)qs[i].tag << 32);
+        m.req.count = theta[i];
+        m.req.flags = SAMPLE_EMIT;
+        mq.push_back(m);
+    }
+    TIM_TRY(tim_sample_multi(owner, mq.data(), nq, seed));
+    cudaEventRecord(ev[3], owner->stream);
+    std::vector<int32_t*> hs(nq);
+    std::vector<uint64_t> cov(nq, 0);
+    for (int i = 0; i < nq; i++) hs[i] = qs[i].seeds;
+    TIM_TRY(tim_greedy_batch(owner, ctxs.data(), ks.data(), nq, hs.data(), cov.data(), true));
+    cudaEventRecord(ev[4], owner->stream);
+    TIM_TRY(tim_sync(owner));
+    uint64_t sets_all = 0;
+    for (int i = 0; i < nq; i++) {
+        tim_stats& s = qs[i].stats;
+        s.kpt_round = stop[i];
+        s.kpt_last_round = last[i];
+        s.kpt_star = kpt[i];
+        s.kpt_prime = kpt_prime[i];
+        s.kpt_plus = kpt_plus[i];
+        s.eps_prime = eps_p[i];
+        s.lambda = lam[i];
+        s.theta_prime = theta_p[i];
+        s.covered_prime = cov_p[i];
+        s.theta = theta[i];
+        s.covered = cov[i];
+        s.sets_total = sets[i] + theta_p[i] + theta[i];
+        s.members_select = mq[i].res.members;
+        s.width_select = mq[i].res.wsum;
+        s.width_total = width[i] + width_p[i] + mq[i].res.wsum;
+        qs[i].covered_fraction = theta[i] ? (double)cov[i] / (double)theta[i] : 0.0;
+        sets_all += s.sets_total;
+        // keep the per-context state consistent with a single run
+        tim_ctx* c = qs[i].ctx;
+        c->have_kpt = true;
+        c->kpt_round = stop[i];
+        c->kpt_last_round = last[i];
+        c->kpt_last_c = last_c[i];
+        c->kpt_star = kpt[i];
+    }
+    if (bst) {
+        memset(bst, 0, sizeof *bst);
+        bst->queries = nq;
+        bst->kpt_launch_rounds = launched_rounds;
+        bst->sets_total = sets_all;
+        bst->ms_kpt = elapsed_ms(owner, 0, 1);
+        bst->ms_refine = elapsed_ms(owner, 1, 2);
+        bst->ms_select_sample = elapsed_ms(owner, 2, 3);
+        bst->ms_select_greedy = elapsed_ms(owner, 3, 4);
+        bst->ms_total = elapsed_ms(owner, 0, 4);
+    }
+    return TIM_OK;
 }
 
 }  // extern "C"

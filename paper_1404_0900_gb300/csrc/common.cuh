@@ -100,6 +100,13 @@ struct tim_ctx {
     unsigned long long width_budget = 16384;
     // IC tier 2: warps per RR set (1, 2, 4 or 8); 0 = chosen from the number of sets
     int team_size = 0;
+    // sets claimed per work-counter increment in tiers 1 and 2
+    int chunk = 2;
+    // set-id tag of this context's runs: ids are (phase << 56) | (round << 48) |
+    // (tag << 32) | j
+    uint32_t query_tag = 0;
+    // batch scratch (owner of a multi-query launch / batched greedy)
+    DevBuf batch, greedy_batch;
     int last_team = 1;
 
     // generic scratch for scans and sorts
@@ -185,12 +192,28 @@ struct SampleResult {
 int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res);
 // Third tier for the heavy IC sets list[0 .. count) (sample_bulk.cu).
 int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, uint32_t count,
-                uint32_t* pool, uint32_t* pool_sid, uint64_t pool_cap, uint64_t* live_out);
+                uint32_t* pool, uint32_t* pool_sid, uint64_t pool_cap, DevScalars* ds,
+                uint64_t* live_out);
+
+// Several queries, each with its own context (graph, RR-set store), sampled by one
+// launch per tier; all share the Philox key of `seed` and use the owner's stream and
+// scratch. Per-query results in qs[i].res.
+struct MultiQuery {
+    tim_ctx* ctx = nullptr;
+    SampleRequest req;
+    SampleResult res;
+};
+int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed);
 
 // select.cu
 int tim_build_index(tim_ctx* ctx);
 int tim_greedy(tim_ctx* ctx, int k, int32_t* host_seeds, uint64_t* covered);
 int tim_mark_seeds(tim_ctx* ctx, const int32_t* d_seeds, int k);
+// Greedy of Algorithm 1 for several queries (each on its own context's store) with
+// shared launches, optionally captured into one CUDA graph; seeds stay in each
+// context's seeds_dev, host copies where host_seeds[i] is not NULL.
+int tim_greedy_batch(tim_ctx* owner, tim_ctx* const* ctxs, const int* ks, int nq,
+                     int32_t* const* host_seeds, uint64_t* covered, bool use_graph);
 
 // scalar formulas (api.cu)
 uint64_t tim_host_c_i(int64_t n, double ell, int i);

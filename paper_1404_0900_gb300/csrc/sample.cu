@@ -26,6 +26,7 @@
 // (Eq. 6) in 2^-63 fixed point, and test COVER (does the set meet a given seed set;
 // Algorithm 3 lines 9-10; the BFS stops at the first member in the seed set).
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 
@@ -35,7 +36,6 @@ constexpr uint32_t EMPTY = 0xFFFFFFFFu;
 constexpr int ST_OVERFLOW = 1;
 constexpr int ST_COVERED = 2;
 constexpr int WARPS = 8;          // warps per CTA (tiers 1 and 2)
-constexpr int CHUNK = 2;          // sets claimed per work-counter increment
 constexpr int BIG_THREADS = 256;  // tier 3 LT CTA size
 
 // Queue capacity Q and hash size 2^LOG2H (>= 2Q) of one warp's set.
@@ -75,6 +75,7 @@ struct SampleArgs {
     uint32_t* big_queue;
     uint64_t big_words;
     unsigned long long width_budget;  // tier 1 IC: in-edges one warp may examine per set
+    int chunk;                        // sets claimed per work-counter increment
 };
 
 __device__ __forceinline__ uint4 draw(const SampleArgs& a, uint64_t sid, uint32_t elem,
@@ -182,8 +183,8 @@ __device__ __forceinline__ uint32_t live_mask(uint4 x, uint4 t) {
 
 // Follow the live in-edges of group g given their mask: insert each source. Returns
 // bit 0 if the set overflowed, bit 1 if it met the seed set.
-template <class C>
-__device__ __noinline__ int follow_live(const SampleArgs& a, uint32_t g, uint32_t mask,
+template <class C, class A>
+__device__ __noinline__ int follow_live(const A& a, uint32_t g, uint32_t mask,
                                         uint32_t* hash, uint32_t* queue, uint16_t* slot,
                                         int* ctl) {
     int f = 0;
@@ -209,8 +210,8 @@ constexpr uint32_t BIG_GROUPS = 32;
 // Expand one RR set with a team of T warps (wt = warp index in the team, team = team
 // index in the block). Returns the status bits; *width_out = w(R) (Eq. 1); *live_out
 // counts live in-edges followed (per lane).
-template <int MODEL, class C, int T>
-__device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32_t* hash,
+template <int MODEL, class C, int T, class A>
+__device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t sid, uint32_t* hash,
                                        uint32_t* queue, uint16_t* slot, int* ctl,
                                        unsigned long long budget, int wt, int team,
                                        unsigned long long* width_out,
@@ -218,7 +219,7 @@ __device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32
     const int lane = threadIdx.x & 31;
     volatile int* vctl = ctl;
     const bool cover = a.flags & SAMPLE_COVER;
-    const uint32_t root = rr_root(sid, a.n, a.K);
+    const uint32_t root = rr_root(sid, a.n, K);
     if (wt == 0 && lane == 0) {
         uint32_t h = (root * 0x9E3779B1u) >> (32 - C::LOG2H);
         hash[h] = root;
@@ -230,7 +231,6 @@ __device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32
     team_sync<T>(team);
     unsigned long long width = 0, live = 0;
     if (MODEL == TIM_IC) {
-        const PhiloxKeys& K = a.K;
         const uint32_t s0 = (uint32_t)sid, s1 = (uint32_t)(sid >> 32);
         const uint4* thr4 = reinterpret_cast<const uint4*>(a.thr);
         int head = 0;
@@ -309,8 +309,8 @@ __device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32
                         if (m0 && (g0 == gfirst || g0 == glast)) m0 &= range_mask(g0, bb, be);
                         if (m1 && (g1 == gfirst || g1 == glast)) m1 &= range_mask(g1, bb, be);
                         live += __popc(m0) + __popc(m1);
-                        if (m0) flags |= follow_live<C>(a, g0, m0, hash, queue, slot, ctl);
-                        if (m1) flags |= follow_live<C>(a, g1, m1, hash, queue, slot, ctl);
+                        if (m0) flags |= follow_live<C, A>(a, g0, m0, hash, queue, slot, ctl);
+                        if (m1) flags |= follow_live<C, A>(a, g1, m1, hash, queue, slot, ctl);
                         if (__any_sync(0xffffffffu, flags & 3)) break;
                     }
                 }
@@ -352,21 +352,23 @@ __device__ __forceinline__ int team_rr(const SampleArgs& a, uint64_t sid, uint32
                 }
                 if (__any_sync(0xffffffffu, m != 0u)) {
                     live += __popc(m);
-                    if (m) flags |= follow_live<C>(a, g, m, hash, queue, slot, ctl);
+                    if (m) flags |= follow_live<C, A>(a, g, m, hash, queue, slot, ctl);
                     flags = __reduce_or_sync(0xffffffffu, flags);
                 }
             }
             team_sync<T>(team);
             head += nb;
         }
-    } else {
+    } else if (wt == 0) {
+        // an LT set is a chain: one warp walks it, the team's other warps wait
         uint32_t v = root;
         for (int guard = 0; guard < C::Q + 1; guard++) {
             if (__shfl_sync(0xffffffffu, vctl[1], 0)) break;
             const uint64_t beg = __ldg(a.rowptr + v), end = __ldg(a.rowptr + v + 1);
             width += end - beg;
             if (beg == end) break;
-            const uint32_t x = draw(a, sid, v, TIM_TAG_LT).x;
+            const uint32_t x =
+                philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32), v, TIM_TAG_LT, K).x;
             const uint64_t j = warp_lt_search(a.thr, beg, end, x, lane);
             if (j >= end) break;
             const uint32_t u = __ldg(a.src + j);
@@ -423,7 +425,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) rr_team_kernel(SampleArgs a) {
     const bool leader = wt == 0 && lane == 0;
     for (;;) {
         unsigned long long i0 = 0;
-        if (leader) i0 = atomicAdd(counter, (unsigned long long)CHUNK);
+        if (leader) i0 = atomicAdd(counter, (unsigned long long)a.chunk);
         if (T == 1) {
             i0 = __shfl_sync(0xffffffffu, i0, 0);
         } else {
@@ -433,12 +435,12 @@ __global__ void __launch_bounds__(WARPS * 32, 4) rr_team_kernel(SampleArgs a) {
             team_sync<T>(team);
         }
         if (i0 >= items) break;
-        const unsigned long long i1 = min(i0 + CHUNK, (unsigned long long)items);
+        const unsigned long long i1 = min(i0 + (unsigned long long)a.chunk, (unsigned long long)items);
         for (unsigned long long it = i0; it < i1; it++) {
             const uint64_t j = TIER == 1 ? it : a.list1[it];
             unsigned long long width;
-            const int st = team_rr<MODEL, C, T>(a, a.sid0 + j, hash, queue, slot, ctl, budget, wt,
-                                                team, &width, &live);
+            const int st = team_rr<MODEL, C, T, SampleArgs>(a, a.K, a.sid0 + j, hash, queue, slot,
+                                                            ctl, budget, wt, team, &width, &live);
             const int tail = min(T == 1 ? __shfl_sync(0xffffffffu, ((volatile int*)ctl)[0], 0)
                                         : ((volatile int*)ctl)[0],
                                  C::Q);
@@ -660,6 +662,247 @@ int launch_tier2(tim_ctx* ctx, const SampleArgs& a, unsigned grid, int T) {
     return TIM_OK;
 }
 
+
+// ------------------------------------------------------- several queries at once
+
+// One query of a multi-query launch (device memory).
+struct QueryDesc {
+    const uint64_t* rowptr;
+    const uint32_t* src;
+    const uint32_t* thr;
+    const unsigned long long* node_thr;
+    uint64_t n, m;
+    uint64_t sid0, count;
+    int model, flags, k, pad;
+    const uint32_t* seed_mark;
+    uint32_t* pool;
+    uint32_t* pool_sid;
+    uint64_t pool_cap;
+    uint64_t* set_start;
+    uint32_t* set_len;
+    uint64_t* set_width;
+    DevScalars* ds;
+    unsigned long long width_budget;
+};
+
+struct MultiArgs {
+    PhiloxKeys K;
+    const QueryDesc* q;
+    const unsigned long long* prefix;  // prefix[i] = sets of queries before i; [nq] = total
+    int nq;
+    int chunk;
+    unsigned long long* next;  // [0] tier-1, [1] tier-2 work counters
+    unsigned* cnt;             // [0] sets listed for tier 2, [1] for tier 3
+    int* err;
+    uint2* list1;  // (query, set index)
+    uint2* list2;
+    uint32_t list_cap;
+    uint32_t* arena;
+};
+
+// What team_rr reads of one query: its graph and flags, plus the launch's keys.
+struct QArgs {
+    const uint64_t* rowptr;
+    const uint32_t* src;
+    const uint32_t* thr;
+    const unsigned long long* node_thr;
+    uint64_t n, m;
+    int flags, k;
+    const uint32_t* seed_mark;
+};
+
+constexpr int MAXQ = 256;  // queries per multi-query launch
+
+struct QAcc {
+    unsigned long long k_lo, k_hi, wsum, cov, live, memb;
+};
+
+template <int TIER>
+__device__ __forceinline__ void flush_acc(const QueryDesc* qd, int qi, QAcc& acc, int lane) {
+    const unsigned long long lv = warp_sum_u64(acc.live);
+    if (qi >= 0 && lane == 0) {
+        DevScalars* ds = qd[qi].ds;
+        if (acc.k_lo || acc.k_hi) atomic_add_u128(&ds->ksum_lo, &ds->ksum_hi, acc.k_lo, acc.k_hi);
+        if (acc.wsum) {
+            atomicAdd(&ds->wsum, acc.wsum);
+            atomicAdd(&ds->width[TIER - 1], acc.wsum);
+        }
+        if (acc.cov) atomicAdd(&ds->covered, acc.cov);
+        if (lv) atomicAdd(&ds->live[TIER - 1], lv);
+        if (acc.memb) atomicAdd(&ds->memb[TIER - 1], acc.memb);
+    }
+    acc = QAcc{0, 0, 0, 0, 0, 0};
+}
+
+// TIER 1: shared-memory sets of every query (global set index across queries); TIER 2:
+// the listed (query, set) pairs with a global arena and teams of T warps.
+template <class C, int TIER, int T>
+__global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
+    extern __shared__ uint32_t smem[];
+    __shared__ unsigned long long s_claim[WARPS];
+    __shared__ unsigned long long s_prefix[MAXQ + 1];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int wt = wid % T, team = wid / T;
+    const int tl = wt * 32 + lane;
+    for (int i = threadIdx.x; i <= ma.nq; i += blockDim.x) s_prefix[i] = ma.prefix[i];
+    __syncthreads();
+    uint32_t* hash;
+    if (TIER == 1) {
+        hash = smem + team * C::WORDS;
+        for (int i = tl; i < C::H; i += 32 * T) hash[i] = EMPTY;
+    } else {
+        const uint64_t slot_id = (uint64_t)blockIdx.x * (WARPS / T) + team;
+        hash = ma.arena + slot_id * C::WORDS;
+    }
+    team_sync<T>(team);
+    uint32_t* queue = hash + C::H;
+    uint16_t* slot = reinterpret_cast<uint16_t*>(queue + C::Q);
+    int* ctl = reinterpret_cast<int*>(queue + C::Q + C::Q / 2);
+    unsigned long long* counter = &ma.next[TIER - 1];
+    const uint64_t items = TIER == 1 ? s_prefix[ma.nq]
+                                     : (uint64_t)min(((volatile unsigned*)ma.cnt)[0], ma.list_cap);
+    uint2* out_list = TIER == 1 ? ma.list1 : ma.list2;
+    unsigned* out_cnt = TIER == 1 ? &ma.cnt[0] : &ma.cnt[1];
+    const bool leader = wt == 0 && lane == 0;
+    QAcc acc{0, 0, 0, 0, 0, 0};
+    int cur_q = -1;
+    for (;;) {
+        unsigned long long i0 = 0;
+        if (leader) i0 = atomicAdd(counter, (unsigned long long)ma.chunk);
+        if (T == 1) {
+            i0 = __shfl_sync(0xffffffffu, i0, 0);
+        } else {
+            if (leader) s_claim[team] = i0;
+            team_sync<T>(team);
+            i0 = s_claim[team];
+            team_sync<T>(team);
+        }
+        if (i0 >= items) break;
+        const unsigned long long i1 = min(i0 + (unsigned long long)ma.chunk, (unsigned long long)items);
+        for (unsigned long long it = i0; it < i1; it++) {
+            int qi;
+            uint64_t j;
+            if (TIER == 1) {
+                int lo = 0, hi = ma.nq;  // s_prefix[lo] <= it < s_prefix[hi]
+                while (hi - lo > 1) {
+                    const int mid = (lo + hi) >> 1;
+                    if (s_prefix[mid] <= it)
+                        lo = mid;
+                    else
+                        hi = mid;
+                }
+                qi = lo;
+                j = it - s_prefix[lo];
+            } else {
+                const uint2 e = ma.list1[it];
+                qi = (int)e.x;
+                j = e.y;
+            }
+            if (qi != cur_q) {
+                flush_acc<TIER>(ma.q, cur_q, acc, lane);
+                cur_q = qi;
+            }
+            const QueryDesc& d = ma.q[qi];
+            const QArgs qa{d.rowptr, d.src, d.thr, d.node_thr, d.n, d.m, d.flags, d.k, d.seed_mark};
+            const int model = d.model;
+            const unsigned long long budget =
+                (TIER == 1 && model == TIM_IC) ? d.width_budget : ~0ull;
+            unsigned long long width;
+            int st;
+            if (model == TIM_IC)
+                st = team_rr<TIM_IC, C, T, QArgs>(qa, ma.K, d.sid0 + j, hash, queue, slot, ctl,
+                                                  budget, wt, team, &width, &acc.live);
+            else
+                st = team_rr<TIM_LT, C, T, QArgs>(qa, ma.K, d.sid0 + j, hash, queue, slot, ctl,
+                                                  budget, wt, team, &width, &acc.live);
+            const int tail = min(T == 1 ? __shfl_sync(0xffffffffu, ((volatile int*)ctl)[0], 0)
+                                        : ((volatile int*)ctl)[0],
+                                 C::Q);
+            team_sync<T>(team);
+            if (st & ST_OVERFLOW) {
+                if (leader) {
+                    const unsigned idx = atomicAdd(out_cnt, 1u);
+                    if (idx < ma.list_cap)
+                        out_list[idx] = make_uint2((uint32_t)qi, (uint32_t)j);
+                    else
+                        atomicOr(ma.err, TIM_DEV_ERR_OVF_LIST);
+                }
+                for (int i = tl; i < C::H; i += 32 * T) hash[i] = EMPTY;
+                team_sync<T>(team);
+                continue;
+            }
+            if (leader) {
+                acc.wsum += width;
+                acc.memb += tail;
+                if (st & ST_COVERED) acc.cov++;
+                if (d.flags & SAMPLE_KAPPA) {
+                    const unsigned long long kf = kappa_fixed(kappa_fp64(width, d.m, d.k));
+                    acc.k_lo += kf;
+                    if (acc.k_lo < kf) acc.k_hi++;
+                }
+            }
+            if (d.flags & SAMPLE_EMIT) {
+                unsigned long long base = 0;
+                if (leader) base = atomicAdd(&d.ds->pool_used, (unsigned long long)tail);
+                if (T == 1) {
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                } else {
+                    if (leader) s_claim[team] = base;
+                    team_sync<T>(team);
+                    base = s_claim[team];
+                }
+                if (base + tail <= d.pool_cap) {
+                    for (int i = tl; i < tail; i += 32 * T) {
+                        d.pool[base + i] = queue[i];
+                        d.pool_sid[base + i] = (uint32_t)j;
+                    }
+                    if (leader) {
+                        d.set_start[j] = base;
+                        d.set_len[j] = (uint32_t)tail;
+                        d.set_width[j] = width;
+                    }
+                } else if (leader) {
+                    atomicOr(&d.ds->err, TIM_DEV_ERR_POOL);
+                }
+            }
+            for (int i = tl; i < tail; i += 32 * T) hash[slot[i]] = EMPTY;
+            team_sync<T>(team);
+        }
+    }
+    flush_acc<TIER>(ma.q, cur_q, acc, lane);
+}
+
+int launch_multi(tim_ctx* owner, const MultiArgs& ma, int tier, int T, unsigned grid,
+                 size_t smem) {
+    if (tier == 1) {
+        rr_multi_kernel<Tier1, 1, 1><<<grid, WARPS * 32, smem, owner->stream>>>(ma);
+    } else if (T == 1) {
+        rr_multi_kernel<Tier2, 2, 1><<<grid, WARPS * 32, 0, owner->stream>>>(ma);
+    } else if (T == 2) {
+        rr_multi_kernel<Tier2, 2, 2><<<grid, WARPS * 32, 0, owner->stream>>>(ma);
+    } else if (T == 4) {
+        rr_multi_kernel<Tier2, 2, 4><<<grid, WARPS * 32, 0, owner->stream>>>(ma);
+    } else {
+        rr_multi_kernel<Tier2, 2, 8><<<grid, WARPS * 32, 0, owner->stream>>>(ma);
+    }
+    LAUNCH_CHECK(owner, tier == 1 ? "rr_multi_kernel (tier 1)" : "rr_multi_kernel (tier 2)");
+    return TIM_OK;
+}
+
+template <class C, int TIER, int T>
+int multi_occupancy(size_t smem) {
+    int nb = 0;
+    auto k = rr_multi_kernel<C, TIER, T>;
+    if (smem > 48 * 1024)
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, WARPS * 32, smem) != cudaSuccess ||
+        nb < 1) {
+        cudaGetLastError();
+        nb = 1;
+    }
+    return nb;
+}
+
 }  // namespace
 
 int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
@@ -743,6 +986,7 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
     a.set_len = (uint32_t*)ctx->set_len.p;
     a.set_width = (uint64_t*)ctx->set_width.p;
     a.width_budget = ctx->width_budget;
+    a.chunk = std::max(1, ctx->chunk);
     for (int attempt = 0; attempt < 4; attempt++) {
         a.pool = (uint32_t*)ctx->pool.p;
         a.pool_sid = (uint32_t*)ctx->pool_sid.p;
@@ -771,7 +1015,8 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
             if (ctx->model == TIM_IC) {
                 TIM_TRY(tim_read_scalars(ctx));
                 const unsigned n3 = std::min(ctx->h_scal->cnt2, list_cap);
-                TIM_TRY(tim_bulk_ic(ctx, req, a.list2, n3, a.pool, a.pool_sid, a.pool_cap, &live3));
+                TIM_TRY(tim_bulk_ic(ctx, req, a.list2, n3, a.pool, a.pool_sid, a.pool_cap, a.ds,
+                                    &live3));
             } else {
                 rr_lt_chain_kernel<<<slots, BIG_THREADS, 0, ctx->stream>>>(a);
                 LAUNCH_CHECK(ctx, "rr_lt_chain_kernel");
@@ -828,4 +1073,281 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
         return TIM_OK;
     }
     return tim_fail(ctx, TIM_ERR_OOM, "RR-set store kept overflowing");
+}
+
+// ----------------------------------------------------- multi-query host driver
+
+namespace {
+
+// Tier-3 LT slots of one context: a visited bitmap of n bits and a queue of n entries
+// each, at most ~2 GiB in total.
+int ensure_lt_slots(tim_ctx* ctx, int* slots_out, uint64_t* words_out) {
+    const uint64_t words = (uint64_t)(ctx->n + 31) / 32 + 1;
+    const uint64_t per_slot = (words + (uint64_t)ctx->n) * sizeof(uint32_t);
+    int slots = ctx->num_sms;
+    const uint64_t budget = 2ull << 30;
+    if ((uint64_t)slots * per_slot > budget) slots = (int)std::max<uint64_t>(1, budget / per_slot);
+    void* prev_bm = ctx->big_bitmap.p;
+    TIM_TRY(tim_ensure(ctx, ctx->big_bitmap, (size_t)slots * words * sizeof(uint32_t)));
+    TIM_TRY(tim_ensure(ctx, ctx->big_queue, (size_t)slots * (uint64_t)ctx->n * sizeof(uint32_t)));
+    if (ctx->big_bitmap.p != prev_bm || !ctx->big_bitmap_clean) {
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->big_bitmap.p, 0, ctx->big_bitmap.bytes, ctx->stream));
+        ctx->big_bitmap_clean = true;
+    }
+    *slots_out = slots;
+    *words_out = words;
+    return TIM_OK;
+}
+
+// Tier 3 for one query of a multi-query launch: the sets list_dev[0 .. n3) of ctx's
+// graph, accumulating into ds. Runs on `stream`.
+int run_tier3(tim_ctx* ctx, cudaStream_t stream, const SampleRequest& req, DevScalars* ds,
+              uint32_t* pool, uint32_t* pool_sid, uint64_t pool_cap, const uint32_t* list_dev,
+              unsigned n3, uint64_t* live3) {
+    cudaStream_t saved = ctx->stream;
+    ctx->stream = stream;
+    int rc = TIM_OK;
+    if (ctx->model == TIM_IC) {
+        rc = tim_bulk_ic(ctx, req, list_dev, n3, pool, pool_sid, pool_cap, ds, live3);
+    } else {
+        int slots = 0;
+        uint64_t words = 0;
+        rc = ensure_lt_slots(ctx, &slots, &words);
+        if (rc == TIM_OK) {
+            SampleArgs a{};
+            a.rowptr = (const uint64_t*)ctx->rowptr.p;
+            a.src = (const uint32_t*)ctx->src.p;
+            a.thr = (const uint32_t*)ctx->thr.p;
+            a.n = (uint64_t)ctx->n;
+            a.m = (uint64_t)ctx->m;
+            a.K = tim_philox_keys(req.seed);
+            a.sid0 = req.sid0;
+            a.count = req.count;
+            a.flags = req.flags;
+            a.k = req.k;
+            a.seed_mark = req.seed_mark;
+            a.pool = pool;
+            a.pool_sid = pool_sid;
+            a.pool_cap = pool_cap;
+            a.set_start = (uint64_t*)ctx->set_start.p;
+            a.set_len = (uint32_t*)ctx->set_len.p;
+            a.set_width = (uint64_t*)ctx->set_width.p;
+            a.ds = ds;
+            a.list2 = const_cast<uint32_t*>(list_dev);
+            a.list_cap = n3 + 1;
+            a.big_bitmap = (uint32_t*)ctx->big_bitmap.p;
+            a.big_queue = (uint32_t*)ctx->big_queue.p;
+            a.big_words = words;
+            a.chunk = 1;
+            rc = tim_cuda_check(ctx, cudaMemcpyAsync(&ds->cnt2, &n3, sizeof(unsigned),
+                                                     cudaMemcpyHostToDevice, stream),
+                                "tier-3 count");
+            if (rc == TIM_OK) rc = tim_cuda_check(ctx, cudaMemsetAsync(&ds->next3, 0, 8, stream), "memset");
+            if (rc == TIM_OK) rc = tim_cuda_check(ctx, cudaStreamSynchronize(stream), "sync");
+            if (rc == TIM_OK) {
+                rr_lt_chain_kernel<<<slots, BIG_THREADS, 0, stream>>>(a);
+                ctx->launches++;
+                rc = tim_cuda_check(ctx, cudaGetLastError(), "rr_lt_chain_kernel");
+            }
+        }
+        *live3 = 0;
+    }
+    ctx->stream = saved;
+    return rc;
+}
+
+}  // namespace
+
+int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
+    if (nq <= 0) return TIM_OK;
+    if (nq > MAXQ) return tim_fail(owner, TIM_ERR_ARG, "too many queries in one launch");
+    std::vector<unsigned long long> prefix(nq + 1, 0);
+    uint64_t total = 0;
+    for (int i = 0; i < nq; i++) {
+        tim_ctx* c = qs[i].ctx;
+        if (!c || !c->have_graph) return tim_fail(owner, TIM_ERR_STATE, "query without a graph");
+        if (c->device != owner->device) return tim_fail(owner, TIM_ERR_ARG, "queries on several devices");
+        const uint64_t count = qs[i].req.count;
+        if (count > 0xFFFFFFF0ull) return tim_fail(owner, TIM_ERR_ARG, "too many RR sets in one call");
+        prefix[i] = total;
+        total += count;
+        if (qs[i].req.flags & SAMPLE_EMIT) {
+            uint64_t cap_sets = 1024;
+            while (cap_sets < count + 1) cap_sets <<= 1;
+            TIM_TRY(tim_ensure(c, c->set_start, cap_sets * sizeof(uint64_t)));
+            TIM_TRY(tim_ensure(c, c->set_len, cap_sets * sizeof(uint32_t)));
+            TIM_TRY(tim_ensure(c, c->set_width, cap_sets * sizeof(uint64_t)));
+            const uint64_t want = cap_sets * 8 + 4096;
+            if (c->pool.bytes < want * sizeof(uint32_t)) {
+                TIM_TRY(tim_ensure(c, c->pool, want * sizeof(uint32_t)));
+                TIM_TRY(tim_ensure(c, c->pool_sid, want * sizeof(uint32_t)));
+            }
+        }
+    }
+    prefix[nq] = total;
+    if (total > 0xFFFFFFF0ull) return tim_fail(owner, TIM_ERR_ARG, "too many RR sets in one launch");
+    // owner scratch: descriptors | prefix | per-query scalars | next[2] | cnt[2] | err
+    const size_t off_prefix = ((size_t)nq * sizeof(QueryDesc) + 255) & ~size_t(255);
+    const size_t off_scal = (off_prefix + (size_t)(nq + 1) * 8 + 255) & ~size_t(255);
+    const size_t off_ctr = (off_scal + (size_t)nq * sizeof(DevScalars) + 255) & ~size_t(255);
+    const size_t batch_bytes = off_ctr + 64;
+    TIM_TRY(tim_ensure(owner, owner->batch, batch_bytes));
+    char* bb = (char*)owner->batch.p;
+    QueryDesc* d_desc = (QueryDesc*)bb;
+    unsigned long long* d_prefix = (unsigned long long*)(bb + off_prefix);
+    DevScalars* d_scal = (DevScalars*)(bb + off_scal);
+    unsigned long long* d_next = (unsigned long long*)(bb + off_ctr);
+    unsigned* d_cnt = (unsigned*)(bb + off_ctr + 16);
+    int* d_err = (int*)(bb + off_ctr + 24);
+    TIM_TRY(tim_ensure(owner, owner->ovf_list, (size_t)(total + 1) * sizeof(uint2)));
+    TIM_TRY(tim_ensure(owner, owner->ovf_list2, (size_t)(total + 1) * sizeof(uint2)));
+    // arena and occupancy as in the single-query path
+    const size_t smem1 = (size_t)WARPS * Tier1::WORDS * sizeof(uint32_t);
+    const int nb1 = multi_occupancy<Tier1, 1, 1>(smem1);
+    const int nb2 = multi_occupancy<Tier2, 2, 1>(0);
+    const unsigned grid1 = (unsigned)(owner->num_sms * nb1);
+    const unsigned grid2 = (unsigned)(owner->num_sms * nb2);
+    const size_t arena_bytes = (size_t)grid2 * WARPS * Tier2::WORDS * sizeof(uint32_t);
+    void* prev_arena = owner->arena.p;
+    TIM_TRY(tim_ensure(owner, owner->arena, arena_bytes));
+    if (owner->arena.p != prev_arena || !owner->arena_clean) {
+        CUDA_TRY(owner, cudaMemsetAsync(owner->arena.p, 0xFF, owner->arena.bytes, owner->stream));
+        owner->arena_clean = true;
+    }
+    MultiArgs ma;
+    ma.K = tim_philox_keys(seed);
+    ma.q = d_desc;
+    ma.prefix = d_prefix;
+    ma.nq = nq;
+    ma.chunk = std::max(1, owner->chunk);
+    ma.next = d_next;
+    ma.cnt = d_cnt;
+    ma.err = d_err;
+    ma.list1 = (uint2*)owner->ovf_list.p;
+    ma.list2 = (uint2*)owner->ovf_list2.p;
+    ma.list_cap = (uint32_t)(total + 1);
+    ma.arena = (uint32_t*)owner->arena.p;
+    std::vector<QueryDesc> h_desc(nq);
+    std::vector<DevScalars> h_scal(nq);
+    for (int attempt = 0; attempt < 4; attempt++) {
+        for (int i = 0; i < nq; i++) {
+            tim_ctx* c = qs[i].ctx;
+            const SampleRequest& r = qs[i].req;
+            QueryDesc& d = h_desc[i];
+            d.rowptr = (const uint64_t*)c->rowptr.p;
+            d.src = (const uint32_t*)c->src.p;
+            d.thr = (const uint32_t*)c->thr.p;
+            d.node_thr = (const unsigned long long*)c->node_thr.p;
+            d.n = (uint64_t)c->n;
+            d.m = (uint64_t)c->m;
+            d.sid0 = r.sid0;
+            d.count = r.count;
+            d.model = c->model;
+            d.flags = r.flags;
+            d.k = r.k;
+            d.pad = 0;
+            d.seed_mark = r.seed_mark;
+            const bool emit = r.flags & SAMPLE_EMIT;
+            d.pool = emit ? (uint32_t*)c->pool.p : nullptr;
+            d.pool_sid = emit ? (uint32_t*)c->pool_sid.p : nullptr;
+            d.pool_cap = emit ? c->pool.bytes / sizeof(uint32_t) : 0;
+            d.set_start = (uint64_t*)c->set_start.p;
+            d.set_len = (uint32_t*)c->set_len.p;
+            d.set_width = (uint64_t*)c->set_width.p;
+            d.ds = d_scal + i;
+            d.width_budget = c->width_budget;
+        }
+        CUDA_TRY(owner, cudaMemcpyAsync(d_desc, h_desc.data(), (size_t)nq * sizeof(QueryDesc),
+                                        cudaMemcpyHostToDevice, owner->stream));
+        CUDA_TRY(owner, cudaMemcpyAsync(d_prefix, prefix.data(), (size_t)(nq + 1) * 8,
+                                        cudaMemcpyHostToDevice, owner->stream));
+        CUDA_TRY(owner, cudaMemsetAsync(d_scal, 0, (size_t)nq * sizeof(DevScalars), owner->stream));
+        CUDA_TRY(owner, cudaMemsetAsync(d_next, 0, 64, owner->stream));
+        uint64_t live3_total = 0;
+        std::vector<uint64_t> live3(nq, 0);
+        if (total > 0) {
+            TIM_TRY(launch_multi(owner, ma, 1, 1, grid1, smem1));
+            unsigned h_cnt[2] = {0, 0};
+            CUDA_TRY(owner, cudaMemcpyAsync(h_cnt, d_cnt, sizeof h_cnt, cudaMemcpyDeviceToHost,
+                                            owner->stream));
+            TIM_TRY(tim_sync(owner));
+            int T = owner->team_size;
+            if (T <= 0) {
+                T = 1;
+                const uint64_t slots1 = (uint64_t)grid2 * WARPS;
+                while (T < 8 && (uint64_t)h_cnt[0] * 2 < slots1 / T) T *= 2;
+            }
+            TIM_TRY(launch_multi(owner, ma, 2, T, grid2, 0));
+            CUDA_TRY(owner, cudaMemcpyAsync(h_cnt, d_cnt, sizeof h_cnt, cudaMemcpyDeviceToHost,
+                                            owner->stream));
+            TIM_TRY(tim_sync(owner));
+            const unsigned n3 = std::min<unsigned>(h_cnt[1], ma.list_cap);
+            if (n3 > 0) {
+                // the rare sets beyond tier 2: per query, with that query's context
+                std::vector<uint2> l2(n3);
+                CUDA_TRY(owner, cudaMemcpyAsync(l2.data(), ma.list2, (size_t)n3 * sizeof(uint2),
+                                                cudaMemcpyDeviceToHost, owner->stream));
+                TIM_TRY(tim_sync(owner));
+                std::vector<std::vector<uint32_t>> per(nq);
+                for (const uint2& e : l2) per[e.x].push_back(e.y);
+                for (int i = 0; i < nq; i++) {
+                    if (per[i].empty()) continue;
+                    tim_ctx* c = qs[i].ctx;
+                    TIM_TRY(tim_ensure(c, c->ovf_list2, per[i].size() * sizeof(uint32_t)));
+                    CUDA_TRY(owner, cudaMemcpyAsync(c->ovf_list2.p, per[i].data(),
+                                                    per[i].size() * sizeof(uint32_t),
+                                                    cudaMemcpyHostToDevice, owner->stream));
+                    SampleRequest r = qs[i].req;
+                    TIM_TRY(run_tier3(c, owner->stream, r, d_scal + i, h_desc[i].pool,
+                                      h_desc[i].pool_sid, h_desc[i].pool_cap,
+                                      (const uint32_t*)c->ovf_list2.p, (unsigned)per[i].size(),
+                                      &live3[i]));
+                    live3_total += live3[i];
+                }
+            }
+        }
+        CUDA_TRY(owner, cudaMemcpyAsync(h_scal.data(), d_scal, (size_t)nq * sizeof(DevScalars),
+                                        cudaMemcpyDeviceToHost, owner->stream));
+        int h_err = 0;
+        CUDA_TRY(owner, cudaMemcpyAsync(&h_err, d_err, sizeof(int), cudaMemcpyDeviceToHost,
+                                        owner->stream));
+        TIM_TRY(tim_sync(owner));
+        bool regrow = false;
+        for (int i = 0; i < nq; i++) {
+            if (h_scal[i].err & TIM_DEV_ERR_POOL) {
+                tim_ctx* c = qs[i].ctx;
+                const uint64_t need = h_scal[i].pool_used + h_scal[i].pool_used / 16 + 4096;
+                tim_free(c->pool);
+                tim_free(c->pool_sid);
+                TIM_TRY(tim_ensure(c, c->pool, need * sizeof(uint32_t)));
+                TIM_TRY(tim_ensure(c, c->pool_sid, need * sizeof(uint32_t)));
+                regrow = true;
+            } else if (h_scal[i].err) {
+                h_err |= h_scal[i].err;
+            }
+        }
+        if (regrow) continue;
+        if (h_err) {
+            owner->arena_clean = false;
+            return tim_fail(owner, TIM_ERR_CUDA, "device error flags set by the multi-query sampler");
+        }
+        for (int i = 0; i < nq; i++) {
+            const DevScalars& h = h_scal[i];
+            SampleResult& res = qs[i].res;
+            res.ksum = ((unsigned __int128)h.ksum_hi << 64) | h.ksum_lo;
+            res.wsum = h.wsum;
+            res.live = h.live[0] + h.live[1] + live3[i];
+            res.covered = h.covered;
+            const bool emit = qs[i].req.flags & SAMPLE_EMIT;
+            res.members = emit ? h.pool_used : 0;
+            res.big_sets = 0;
+            if (emit) {
+                qs[i].ctx->n_sets = qs[i].req.count;
+                qs[i].ctx->members = h.pool_used;
+            }
+        }
+        (void)live3_total;
+        return TIM_OK;
+    }
+    return tim_fail(owner, TIM_ERR_OOM, "RR-set stores kept overflowing");
 }

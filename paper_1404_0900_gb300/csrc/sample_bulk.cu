@@ -287,7 +287,8 @@ __global__ void bulk_emit_clear_kernel(BulkArgs a, unsigned long long mcount, in
 
 // Heavy IC sets listed in ctx->ovf_list[0 .. count): expand them in batches.
 int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, uint32_t count,
-                uint32_t* pool, uint32_t* pool_sid, uint64_t pool_cap, uint64_t* live_out) {
+                uint32_t* pool, uint32_t* pool_sid, uint64_t pool_cap, DevScalars* ds,
+                uint64_t* live_out) {
     if (count == 0) return TIM_OK;
     const uint64_t n = (uint64_t)ctx->n;
     const uint64_t words = (n + 31) / 32 + 1;
@@ -332,7 +333,7 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
     a.slot_flag = (uint32_t*)(sl + smax * 20);
     a.slot_cursor = (uint32_t*)(sl + smax * 24);
     a.bs = (BulkScalars*)ctx->bulk_scal.p;
-    a.ds = tim_dscal(ctx);
+    a.ds = ds;
     a.pool = pool;
     a.pool_sid = pool_sid;
     a.pool_cap = pool_cap;

@@ -9,6 +9,9 @@
 // then every not-yet-covered set in the chosen node's list is marked covered and each
 // of its members loses one from its count. The chosen node is read on the device, so
 // the k rounds run without host round trips.
+#include <algorithm>
+#include <vector>
+
 #include "common.cuh"
 
 namespace {
@@ -182,5 +185,230 @@ int tim_mark_seeds(tim_ctx* ctx, const int32_t* d_seeds, int k) {
                                                                     (uint32_t*)ctx->seed_mark.p);
         LAUNCH_CHECK(ctx, "mark_seeds_kernel");
     }
+    return TIM_OK;
+}
+
+// ------------------------------------------------------ several queries at once
+//
+// The greedy of Algorithm 1 for a batch of queries, each over its own context's
+// RR-set store: every kernel covers all queries (blockIdx.y = query), so one round of
+// the batch is two launches whatever the number of queries, and the whole sequence
+// (index build and the k rounds) is captured once into a CUDA graph and launched as
+// one unit.
+
+namespace {
+
+struct GreedyDesc {
+    const uint32_t* pool;
+    const uint32_t* pool_sid;
+    uint64_t members;
+    const uint64_t* set_start;
+    const uint32_t* set_len;
+    int* counts;
+    uint64_t* node_off;
+    uint32_t* cursor;
+    uint32_t* node_sets;
+    uint8_t* covered;
+    uint8_t* chosen;
+    unsigned long long* best;
+    int32_t* seeds;
+    unsigned long long* ncov;
+    uint64_t n;
+    int k;
+    int pad;
+};
+
+__global__ void mcount_kernel(const GreedyDesc* __restrict__ gd) {
+    const GreedyDesc& d = gd[blockIdx.y];
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < d.members;
+         p += (uint64_t)gridDim.x * blockDim.x)
+        atomicAdd((unsigned*)&d.counts[d.pool[p]], 1u);
+}
+
+__global__ void mscatter_kernel(const GreedyDesc* __restrict__ gd) {
+    const GreedyDesc& d = gd[blockIdx.y];
+    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < d.members;
+         p += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t u = d.pool[p];
+        const uint32_t slot = atomicAdd(&d.cursor[u], 1u);
+        d.node_sets[d.node_off[u] + slot] = d.pool_sid[p];
+    }
+}
+
+__global__ void margmax_kernel(const GreedyDesc* __restrict__ gd, int r) {
+    const GreedyDesc& d = gd[blockIdx.y];
+    if (r >= d.k) return;
+    unsigned long long b = 0;
+    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < d.n;
+         v += (uint64_t)gridDim.x * blockDim.x) {
+        if (!d.chosen[v]) {
+            const unsigned long long key = greedy_key(d.counts[v], (uint32_t)v);
+            b = key > b ? key : b;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+        b = y > b ? y : b;
+    }
+    if ((threadIdx.x & 31) == 0 && b) atomicMax(&d.best[r], b);
+}
+
+__global__ void mcover_kernel(const GreedyDesc* __restrict__ gd, int r) {
+    const GreedyDesc& d = gd[blockIdx.y];
+    if (r >= d.k) return;
+    const unsigned long long key = d.best[r];
+    if (key == 0) return;
+    const uint32_t v = ~(uint32_t)(key & 0xFFFFFFFFull);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        d.chosen[v] = 1;
+        d.seeds[r] = (int32_t)v;
+    }
+    const int lane = threadIdx.x & 31;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t a = d.node_off[v], b = d.node_off[v + 1];
+    unsigned long long fresh = 0;
+    for (uint64_t i = a + warp; i < b; i += nwarps) {
+        const uint32_t s = d.node_sets[i];
+        if (d.covered[s]) continue;
+        __syncwarp();
+        if (lane == 0) {
+            d.covered[s] = 1;
+            fresh++;
+        }
+        const uint64_t st = d.set_start[s];
+        const uint32_t len = d.set_len[s];
+        for (uint32_t t = lane; t < len; t += 32) atomicSub(&d.counts[d.pool[st + t]], 1);
+    }
+    if (lane == 0 && fresh) atomicAdd(d.ncov, fresh);
+}
+
+}  // namespace
+
+int tim_greedy_batch(tim_ctx* owner, tim_ctx* const* ctxs, const int* ks, int nq,
+                     int32_t* const* host_seeds, uint64_t* covered, bool use_graph) {
+    if (nq <= 0) return TIM_OK;
+    int kmax = 0;
+    std::vector<GreedyDesc> gd(nq);
+    for (int i = 0; i < nq; i++) {
+        tim_ctx* c = ctxs[i];
+        const uint64_t n = (uint64_t)c->n;
+        const int k = ks[i];
+        if (k < 1 || (uint64_t)k > n) return tim_fail(owner, TIM_ERR_ARG, "k must be in [1, n]");
+        kmax = std::max(kmax, k);
+        TIM_TRY(tim_ensure(c, c->counts, (n + 1) * sizeof(int)));
+        TIM_TRY(tim_ensure(c, c->node_off, (n + 1) * sizeof(uint64_t)));
+        TIM_TRY(tim_ensure(c, c->cursor, (n + 1) * sizeof(uint32_t)));
+        TIM_TRY(tim_ensure(c, c->node_sets, (c->members + 1) * sizeof(uint32_t)));
+        TIM_TRY(tim_ensure(c, c->covered, c->n_sets + 1));
+        TIM_TRY(tim_ensure(c, c->chosen, n + 1));
+        TIM_TRY(tim_ensure(c, c->best, (size_t)k * sizeof(unsigned long long) + 8));
+        TIM_TRY(tim_ensure(c, c->seeds_dev, (size_t)k * sizeof(int32_t)));
+        // the scan's block sums, so that nothing is allocated inside the capture
+        TIM_TRY(tim_ensure(c, c->scratch_e, ((n + 4095) / 4096 + 1) * sizeof(unsigned long long)));
+        if (!c->pool.p) TIM_TRY(tim_ensure(c, c->pool, 16));
+        if (!c->pool_sid.p) TIM_TRY(tim_ensure(c, c->pool_sid, 16));
+        if (!c->set_start.p) TIM_TRY(tim_ensure(c, c->set_start, 16));
+        if (!c->set_len.p) TIM_TRY(tim_ensure(c, c->set_len, 16));
+        GreedyDesc& d = gd[i];
+        d.pool = (const uint32_t*)c->pool.p;
+        d.pool_sid = (const uint32_t*)c->pool_sid.p;
+        d.members = c->members;
+        d.set_start = (const uint64_t*)c->set_start.p;
+        d.set_len = (const uint32_t*)c->set_len.p;
+        d.counts = (int*)c->counts.p;
+        d.node_off = (uint64_t*)c->node_off.p;
+        d.cursor = (uint32_t*)c->cursor.p;
+        d.node_sets = (uint32_t*)c->node_sets.p;
+        d.covered = (uint8_t*)c->covered.p;
+        d.chosen = (uint8_t*)c->chosen.p;
+        d.best = (unsigned long long*)c->best.p;
+        d.seeds = (int32_t*)c->seeds_dev.p;
+        d.n = n;
+        d.k = k;
+        d.pad = 0;
+    }
+    // per-query covered counters after the descriptors in the owner's batch buffer
+    const size_t off_cov = ((size_t)nq * sizeof(GreedyDesc) + 255) & ~size_t(255);
+    TIM_TRY(tim_ensure(owner, owner->greedy_batch, off_cov + (size_t)nq * 8));
+    GreedyDesc* d_gd = (GreedyDesc*)owner->greedy_batch.p;
+    unsigned long long* d_cov = (unsigned long long*)((char*)owner->greedy_batch.p + off_cov);
+    for (int i = 0; i < nq; i++) gd[i].ncov = d_cov + i;
+    cudaStream_t st = owner->stream;
+    CUDA_TRY(owner, cudaMemcpyAsync(d_gd, gd.data(), (size_t)nq * sizeof(GreedyDesc),
+                                    cudaMemcpyHostToDevice, st));
+    CUDA_TRY(owner, cudaStreamSynchronize(st));
+    std::vector<cudaStream_t> saved(nq);
+    for (int i = 0; i < nq; i++) {
+        saved[i] = ctxs[i]->stream;
+        ctxs[i]->stream = st;
+    }
+    cudaGraph_t graph = nullptr;
+    int rc = TIM_OK;
+    if (use_graph &&
+        cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        use_graph = false;
+    }
+    const unsigned GX = (unsigned)std::max(1, owner->num_sms * 4 / std::max(1, nq));
+    do {
+        if ((rc = tim_cuda_check(owner, cudaMemsetAsync(d_cov, 0, (size_t)nq * 8, st), "memset")))
+            break;
+        for (int i = 0; i < nq && rc == TIM_OK; i++) {
+            const GreedyDesc& d = gd[i];
+            if ((rc = tim_cuda_check(owner, cudaMemsetAsync(d.counts, 0, (d.n + 1) * 4, st), "memset")))
+                break;
+            if ((rc = tim_cuda_check(owner, cudaMemsetAsync(d.cursor, 0, (d.n + 1) * 4, st), "memset")))
+                break;
+            if ((rc = tim_cuda_check(owner, cudaMemsetAsync(d.covered, 0, ctxs[i]->n_sets + 1, st),
+                                     "memset")))
+                break;
+            if ((rc = tim_cuda_check(owner, cudaMemsetAsync(d.chosen, 0, d.n + 1, st), "memset")))
+                break;
+            if ((rc = tim_cuda_check(owner, cudaMemsetAsync(d.best, 0, (size_t)d.k * 8, st), "memset")))
+                break;
+        }
+        if (rc) break;
+        mcount_kernel<<<dim3(GX, nq), 256, 0, st>>>(d_gd);
+        owner->launches++;
+        for (int i = 0; i < nq && rc == TIM_OK; i++)
+            rc = tim_scan_u32_to_u64(ctxs[i], (const uint32_t*)gd[i].counts, gd[i].node_off, gd[i].n);
+        if (rc) break;
+        mscatter_kernel<<<dim3(GX, nq), 256, 0, st>>>(d_gd);
+        owner->launches++;
+        for (int r = 0; r < kmax; r++) {
+            margmax_kernel<<<dim3(GX, nq), 512, 0, st>>>(d_gd, r);
+            mcover_kernel<<<dim3(GX, nq), 256, 0, st>>>(d_gd, r);
+            owner->launches += 2;
+        }
+        rc = tim_cuda_check(owner, cudaGetLastError(), "batched greedy kernels");
+    } while (0);
+    if (use_graph) {
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (rc == TIM_OK && e != cudaSuccess) rc = tim_cuda_check(owner, e, "cudaStreamEndCapture");
+        if (rc == TIM_OK) {
+            cudaGraphExec_t exec = nullptr;
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e == cudaSuccess) {
+                e = cudaGraphLaunch(exec, st);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+                cudaGraphExecDestroy(exec);
+            }
+            rc = tim_cuda_check(owner, e, "batched greedy graph");
+        }
+        if (graph) cudaGraphDestroy(graph);
+    }
+    for (int i = 0; i < nq; i++) ctxs[i]->stream = saved[i];
+    if (rc) return rc;
+    std::vector<unsigned long long> hc(nq);
+    CUDA_TRY(owner, cudaMemcpyAsync(hc.data(), d_cov, (size_t)nq * 8, cudaMemcpyDeviceToHost, st));
+    for (int i = 0; i < nq; i++)
+        if (host_seeds && host_seeds[i])
+            CUDA_TRY(owner, cudaMemcpyAsync(host_seeds[i], gd[i].seeds, (size_t)gd[i].k * 4,
+                                            cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(owner, cudaStreamSynchronize(st));
+    for (int i = 0; i < nq; i++)
+        if (covered) covered[i] = hc[i];
     return TIM_OK;
 }

@@ -53,7 +53,9 @@ def csr_from_pairs(n: int, src: np.ndarray, dst: np.ndarray, name: str = "") -> 
     src = np.asarray(src, dtype=np.int64)
     dst = np.asarray(dst, dtype=np.int64)
     keep = src != dst
-    key = np.unique(src[keep] * np.int64(n) + dst[keep])
+    key = np.sort(src[keep] * np.int64(n) + dst[keep])
+    if key.size:
+        key = key[np.concatenate(([True], key[1:] != key[:-1]))]
     s = key // n
     d = (key % n).astype(np.int32)
     rowptr = np.zeros(n + 1, dtype=np.int64)
@@ -67,26 +69,33 @@ def rmat(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
 
     Each draw descends `scale` levels of the adjacency matrix, picking the
     (src-bit, dst-bit) quadrant (0,0) w.p. a, (0,1) w.p. b, (1,0) w.p. c and
-    (1,1) w.p. 1-a-b-c. No noise, no relabelling; self-loops and duplicates are
-    removed afterwards, so m is below the number of draws.
+    (1,1) w.p. 1-a-b-c (each probability rounded to a multiple of 2^-16: one 16-bit
+    draw per level picks the quadrant through a lookup table). No noise, no
+    relabelling; self-loops and duplicates are removed afterwards, so m is below the
+    number of draws.
     """
     n = 1 << scale
     draws = edge_factor * n
     rng = _rng(seed)
-    src = np.zeros(draws, dtype=np.int64)
-    dst = np.zeros(draws, dtype=np.int64)
-    ab, abc = a + b, a + b + c
-    chunk = 1 << 22
+    cut = np.round(np.array([a, a + b, a + b + c]) * 65536).astype(np.int64)
+    lut = np.zeros(65536, dtype=np.uint8)
+    lut[cut[0]:cut[1]] = 1  # (0, 1)
+    lut[cut[1]:cut[2]] = 2  # (1, 0)
+    lut[cut[2]:] = 3        # (1, 1)
+    sdt = np.int32 if scale <= 30 else np.int64
+    src = np.empty(draws, dtype=np.int64)
+    dst = np.empty(draws, dtype=np.int64)
+    chunk = 1 << 23
     for lo in range(0, draws, chunk):
         hi = min(draws, lo + chunk)
-        s = np.zeros(hi - lo, dtype=np.int64)
-        d = np.zeros(hi - lo, dtype=np.int64)
+        s = np.zeros(hi - lo, dtype=sdt)
+        d = np.zeros(hi - lo, dtype=sdt)
         for _ in range(scale):
-            u = rng.random(hi - lo)
-            sb = u >= ab
-            db = ((u >= a) & (u < ab)) | (u >= abc)
-            s = (s << 1) | sb
-            d = (d << 1) | db
+            q = lut[rng.integers(0, 65536, size=hi - lo, dtype=np.uint16)]
+            s <<= 1
+            d <<= 1
+            s |= q >> 1
+            d |= q & 1
         src[lo:hi] = s
         dst[lo:hi] = d
     return csr_from_pairs(n, src, dst, name=f"rmat{scale}")
@@ -117,8 +126,8 @@ def chung_lu(n: int, m_target: int, gamma: float = 2.1, seed: int = 1,
         s = np.minimum(s, n - 1)
         d = np.minimum(d, n - 1)
         keep = s != d
-        key = s[keep].astype(np.int64) * n + d[keep]
-        have = np.unique(np.concatenate([have, key]))
+        key = np.sort(np.concatenate([have, s[keep].astype(np.int64) * n + d[keep]]))
+        have = key[np.concatenate(([True], key[1:] != key[:-1]))] if key.size else key
     if have.shape[0] > m_target:
         pick = np.sort(rng.choice(have.shape[0], size=m_target, replace=False))
         have = have[pick]

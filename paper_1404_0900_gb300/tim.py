@@ -64,6 +64,21 @@ class tim_profile(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class tim_query(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("k", C.c_int), ("eps", C.c_double), ("ell", C.c_double),
+                ("tag", C.c_uint32), ("seeds", C.c_void_p), ("covered_fraction", C.c_double),
+                ("stats", tim_stats)]
+
+
+class tim_batch_stats(C.Structure):
+    _fields_ = [("queries", C.c_int), ("kpt_launch_rounds", C.c_int), ("sets_total", C.c_uint64),
+                ("ms_kpt", C.c_double), ("ms_refine", C.c_double), ("ms_select_sample", C.c_double),
+                ("ms_select_greedy", C.c_double), ("ms_total", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 _P = C.c_void_p
 _SIGS = {
@@ -89,6 +104,9 @@ _SIGS = {
     "tim_get_profile": (C.c_int, [_P, _P, C.c_int]),
     "tim_set_width_budget": (C.c_int, [_P, C.c_uint64]),
     "tim_set_team_size": (C.c_int, [_P, C.c_int]),
+    "tim_set_query_tag": (C.c_int, [_P, C.c_uint32]),
+    "tim_set_chunk": (C.c_int, [_P, C.c_int]),
+    "tim_run_batch": (C.c_int, [_P, C.c_int, C.c_uint64, C.c_int, _P]),
     "tim_node_select_noalloc": (C.c_int, [C.c_int, _P, C.c_int64, C.c_uint64, _P, _P, C.c_int,
                                           _P, _P]),
 }
@@ -270,6 +288,36 @@ def tim_launch_count(ctx) -> int:
 
 def tim_set_width_budget(ctx, budget: int):
     _check(ctx, lib().tim_set_width_budget(ctx, budget))
+
+
+def tim_set_query_tag(ctx, tag: int):
+    _check(ctx, lib().tim_set_query_tag(ctx, tag))
+
+
+def tim_set_chunk(ctx, sets: int):
+    _check(ctx, lib().tim_set_chunk(ctx, sets))
+
+
+def tim_run_batch(queries, seed: int, plus: bool = True):
+    """queries: list of dicts {ctx, k, eps, ell, tag}. Returns (list of (seeds, covered
+    fraction, stats dict), batch stats dict)."""
+    nq = len(queries)
+    arr = (tim_query * nq)()
+    seeds = []
+    for i, q in enumerate(queries):
+        s = np.zeros(q["k"], dtype=np.int32)
+        seeds.append(s)
+        arr[i].ctx = q["ctx"]
+        arr[i].k = q["k"]
+        arr[i].eps = q["eps"]
+        arr[i].ell = q.get("ell", 1.0)
+        arr[i].tag = q.get("tag", i + 1)
+        arr[i].seeds = s.ctypes.data_as(_P)
+    bst = tim_batch_stats()
+    ctx0 = queries[0]["ctx"] if nq else None
+    _check(ctx0, lib().tim_run_batch(C.cast(arr, _P), nq, seed, 1 if plus else 0, C.byref(bst)))
+    out = [(seeds[i], arr[i].covered_fraction, arr[i].stats.as_dict()) for i in range(nq)]
+    return out, bst.as_dict()
 
 
 def tim_set_team_size(ctx, warps: int):
