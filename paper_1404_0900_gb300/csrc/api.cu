@@ -242,6 +242,72 @@ int tim_set_team_size(tim_ctx* ctx, int warps) {
     return TIM_OK;
 }
 
+int tim_autotune(tim_ctx* ctx, uint64_t sample_sets, uint64_t seed, tim_tuning* out) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    if (sample_sets == 0) return tim_fail(ctx, TIM_ERR_ARG, "sample_sets must be > 0");
+    DeviceGuard g(ctx->device);
+    const uint64_t budgets_ic[] = {4096, 16384, 65536};
+    const uint64_t budgets_lt[] = {16384};
+    // pass-2 team size stays automatic: it is chosen per call from the number of sets
+    // handed over, which a fixed calibration size cannot stand in for
+    const int teams[] = {0};
+    const int chunks[] = {1, 2, 4};
+    const bool ic = ctx->model == TIM_IC;
+    const uint64_t* budgets = ic ? budgets_ic : budgets_lt;
+    const int nbud = ic ? 3 : 1;
+    const int nteam = 1;
+    const tim_profile saved_prof = ctx->prof;
+    SampleRequest req;
+    req.seed = seed;
+    req.sid0 = make_sid(4, 0, (uint64_t)ctx->query_tag << 32);
+    req.count = sample_sets;
+    req.flags = SAMPLE_EMIT;
+    auto run_once = [&](double* ms) -> int {
+        cudaEventRecord(ctx->ev[5], ctx->stream);
+        SampleResult res;
+        TIM_TRY(tim_sample(ctx, req, &res));
+        cudaEventRecord(ctx->ev[6], ctx->stream);
+        TIM_TRY(tim_sync(ctx));
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ctx->ev[5], ctx->ev[6]);
+        *ms = t;
+        return TIM_OK;
+    };
+    tim_tuning best{};
+    best.best_ms = 1e300;
+    int trials = 0;
+    double def_ms = 0.0;
+    for (int b = 0; b < nbud; b++)
+        for (int t = 0; t < nteam; t++)
+            for (int c = 0; c < 3; c++) {
+                ctx->width_budget = budgets[b];
+                ctx->team_size = teams[t];
+                ctx->chunk = chunks[c];
+                double ms = 0.0, ms2 = 0.0;
+                TIM_TRY(run_once(&ms));   // warm: allocations settle
+                TIM_TRY(run_once(&ms2));
+                ms = std::min(ms, ms2);
+                trials++;
+                if (budgets[b] == 16384 && teams[t] == 0 && chunks[c] == 2) def_ms = ms;
+                if (ms < best.best_ms) {
+                    best.best_ms = ms;
+                    best.width_budget = budgets[b];
+                    best.team_size = teams[t];
+                    best.chunk = chunks[c];
+                }
+            }
+    ctx->width_budget = best.width_budget;
+    ctx->team_size = best.team_size;
+    ctx->chunk = best.chunk;
+    ctx->prof = saved_prof;
+    ctx->have_kpt = false;
+    best.trials = trials;
+    best.default_ms = def_ms;
+    if (out) *out = best;
+    return TIM_OK;
+}
+
 int tim_get_profile(tim_ctx* ctx, tim_profile* out, int reset) {
     if (!ctx) return TIM_ERR_ARG;
     if (out) *out = ctx->prof;

@@ -191,8 +191,9 @@ int tim_mark_seeds(tim_ctx* ctx, const int32_t* d_seeds, int k) {
 // ------------------------------------------------------ several queries at once
 //
 // The greedy of Algorithm 1 for a batch of queries, each over its own context's
-// RR-set store: every kernel covers all queries (blockIdx.y = query), so one round of
-// the batch is two launches whatever the number of queries, and the whole sequence
+// RR-set store: every kernel covers all queries (each query owns a range of blocks in
+// proportion to its work), so one round of the batch is two launches whatever the
+// number of queries, and the whole sequence
 // (index build and the k rounds) is captured once into a CUDA graph and launched as
 // one unit.
 
@@ -218,29 +219,53 @@ struct GreedyDesc {
     int pad;
 };
 
-__global__ void mcount_kernel(const GreedyDesc* __restrict__ gd) {
-    const GreedyDesc& d = gd[blockIdx.y];
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < d.members;
-         p += (uint64_t)gridDim.x * blockDim.x)
+// Blocks are shared out among the queries in proportion to their work; block b belongs
+// to the query q with bstart[q] <= b < bstart[q + 1] and is its (b - bstart[q])-th.
+__device__ __forceinline__ int block_query(const unsigned* __restrict__ bstart, int nq,
+                                           unsigned* local, unsigned* count) {
+    int lo = 0, hi = nq;  // bstart[lo] <= b < bstart[hi]
+    const unsigned b = blockIdx.x;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bstart[mid] <= b)
+            lo = mid;
+        else
+            hi = mid;
+    }
+    *local = b - bstart[lo];
+    *count = bstart[lo + 1] - bstart[lo];
+    return lo;
+}
+
+__global__ void mcount_kernel(const GreedyDesc* __restrict__ gd, const unsigned* __restrict__ bstart,
+                              int nq) {
+    unsigned lb, nb;
+    const GreedyDesc& d = gd[block_query(bstart, nq, &lb, &nb)];
+    for (uint64_t p = lb * (uint64_t)blockDim.x + threadIdx.x; p < d.members;
+         p += (uint64_t)nb * blockDim.x)
         atomicAdd((unsigned*)&d.counts[d.pool[p]], 1u);
 }
 
-__global__ void mscatter_kernel(const GreedyDesc* __restrict__ gd) {
-    const GreedyDesc& d = gd[blockIdx.y];
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < d.members;
-         p += (uint64_t)gridDim.x * blockDim.x) {
+__global__ void mscatter_kernel(const GreedyDesc* __restrict__ gd,
+                                const unsigned* __restrict__ bstart, int nq) {
+    unsigned lb, nb;
+    const GreedyDesc& d = gd[block_query(bstart, nq, &lb, &nb)];
+    for (uint64_t p = lb * (uint64_t)blockDim.x + threadIdx.x; p < d.members;
+         p += (uint64_t)nb * blockDim.x) {
         const uint32_t u = d.pool[p];
         const uint32_t slot = atomicAdd(&d.cursor[u], 1u);
         d.node_sets[d.node_off[u] + slot] = d.pool_sid[p];
     }
 }
 
-__global__ void margmax_kernel(const GreedyDesc* __restrict__ gd, int r) {
-    const GreedyDesc& d = gd[blockIdx.y];
+__global__ void margmax_kernel(const GreedyDesc* __restrict__ gd, const unsigned* __restrict__ bstart,
+                               int nq, int r) {
+    unsigned lb, nb;
+    const GreedyDesc& d = gd[block_query(bstart, nq, &lb, &nb)];
     if (r >= d.k) return;
     unsigned long long b = 0;
-    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < d.n;
-         v += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t v = lb * (uint64_t)blockDim.x + threadIdx.x; v < d.n;
+         v += (uint64_t)nb * blockDim.x) {
         if (!d.chosen[v]) {
             const unsigned long long key = greedy_key(d.counts[v], (uint32_t)v);
             b = key > b ? key : b;
@@ -254,19 +279,21 @@ __global__ void margmax_kernel(const GreedyDesc* __restrict__ gd, int r) {
     if ((threadIdx.x & 31) == 0 && b) atomicMax(&d.best[r], b);
 }
 
-__global__ void mcover_kernel(const GreedyDesc* __restrict__ gd, int r) {
-    const GreedyDesc& d = gd[blockIdx.y];
+__global__ void mcover_kernel(const GreedyDesc* __restrict__ gd, const unsigned* __restrict__ bstart,
+                              int nq, int r) {
+    unsigned lb, nb;
+    const GreedyDesc& d = gd[block_query(bstart, nq, &lb, &nb)];
     if (r >= d.k) return;
     const unsigned long long key = d.best[r];
     if (key == 0) return;
     const uint32_t v = ~(uint32_t)(key & 0xFFFFFFFFull);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (lb == 0 && threadIdx.x == 0) {
         d.chosen[v] = 1;
         d.seeds[r] = (int32_t)v;
     }
     const int lane = threadIdx.x & 31;
-    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t warp = (lb * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)nb * blockDim.x) >> 5;
     const uint64_t a = d.node_off[v], b = d.node_off[v + 1];
     unsigned long long fresh = 0;
     for (uint64_t i = a + warp; i < b; i += nwarps) {
@@ -329,14 +356,39 @@ int tim_greedy_batch(tim_ctx* owner, tim_ctx* const* ctxs, const int* ks, int nq
         d.k = k;
         d.pad = 0;
     }
-    // per-query covered counters after the descriptors in the owner's batch buffer
+    // blocks per query in proportion to its work: nodes (argmax) and members (index,
+    // cover); every query gets at least one block
+    const unsigned total_blocks = (unsigned)std::max(nq, owner->num_sms * 8);
+    std::vector<unsigned> bs_nodes(nq + 1, 0), bs_memb(nq + 1, 0);
+    {
+        double wn = 0, wm = 0;
+        for (int i = 0; i < nq; i++) {
+            wn += (double)gd[i].n;
+            wm += (double)gd[i].members + 1.0;
+        }
+        for (int i = 0; i < nq; i++) {
+            bs_nodes[i + 1] = bs_nodes[i] +
+                              std::max(1u, (unsigned)(total_blocks * ((double)gd[i].n / wn)));
+            bs_memb[i + 1] = bs_memb[i] + std::max(1u, (unsigned)(total_blocks *
+                                                                  (((double)gd[i].members + 1.0) / wm)));
+        }
+    }
+    // descriptors | covered counters | block starts (nodes) | block starts (members)
     const size_t off_cov = ((size_t)nq * sizeof(GreedyDesc) + 255) & ~size_t(255);
-    TIM_TRY(tim_ensure(owner, owner->greedy_batch, off_cov + (size_t)nq * 8));
+    const size_t off_bn = (off_cov + (size_t)nq * 8 + 255) & ~size_t(255);
+    const size_t off_bm = (off_bn + (size_t)(nq + 1) * 4 + 255) & ~size_t(255);
+    TIM_TRY(tim_ensure(owner, owner->greedy_batch, off_bm + (size_t)(nq + 1) * 4));
     GreedyDesc* d_gd = (GreedyDesc*)owner->greedy_batch.p;
     unsigned long long* d_cov = (unsigned long long*)((char*)owner->greedy_batch.p + off_cov);
+    unsigned* d_bn = (unsigned*)((char*)owner->greedy_batch.p + off_bn);
+    unsigned* d_bm = (unsigned*)((char*)owner->greedy_batch.p + off_bm);
     for (int i = 0; i < nq; i++) gd[i].ncov = d_cov + i;
     cudaStream_t st = owner->stream;
     CUDA_TRY(owner, cudaMemcpyAsync(d_gd, gd.data(), (size_t)nq * sizeof(GreedyDesc),
+                                    cudaMemcpyHostToDevice, st));
+    CUDA_TRY(owner, cudaMemcpyAsync(d_bn, bs_nodes.data(), (size_t)(nq + 1) * 4,
+                                    cudaMemcpyHostToDevice, st));
+    CUDA_TRY(owner, cudaMemcpyAsync(d_bm, bs_memb.data(), (size_t)(nq + 1) * 4,
                                     cudaMemcpyHostToDevice, st));
     CUDA_TRY(owner, cudaStreamSynchronize(st));
     std::vector<cudaStream_t> saved(nq);
@@ -351,7 +403,6 @@ int tim_greedy_batch(tim_ctx* owner, tim_ctx* const* ctxs, const int* ks, int nq
         cudaGetLastError();
         use_graph = false;
     }
-    const unsigned GX = (unsigned)std::max(1, owner->num_sms * 4 / std::max(1, nq));
     do {
         if ((rc = tim_cuda_check(owner, cudaMemsetAsync(d_cov, 0, (size_t)nq * 8, st), "memset")))
             break;
@@ -370,16 +421,16 @@ int tim_greedy_batch(tim_ctx* owner, tim_ctx* const* ctxs, const int* ks, int nq
                 break;
         }
         if (rc) break;
-        mcount_kernel<<<dim3(GX, nq), 256, 0, st>>>(d_gd);
+        mcount_kernel<<<bs_memb[nq], 256, 0, st>>>(d_gd, d_bm, nq);
         owner->launches++;
         for (int i = 0; i < nq && rc == TIM_OK; i++)
             rc = tim_scan_u32_to_u64(ctxs[i], (const uint32_t*)gd[i].counts, gd[i].node_off, gd[i].n);
         if (rc) break;
-        mscatter_kernel<<<dim3(GX, nq), 256, 0, st>>>(d_gd);
+        mscatter_kernel<<<bs_memb[nq], 256, 0, st>>>(d_gd, d_bm, nq);
         owner->launches++;
         for (int r = 0; r < kmax; r++) {
-            margmax_kernel<<<dim3(GX, nq), 512, 0, st>>>(d_gd, r);
-            mcover_kernel<<<dim3(GX, nq), 256, 0, st>>>(d_gd, r);
+            margmax_kernel<<<bs_nodes[nq], 512, 0, st>>>(d_gd, d_bn, nq, r);
+            mcover_kernel<<<bs_memb[nq], 256, 0, st>>>(d_gd, d_bm, nq, r);
             owner->launches += 2;
         }
         rc = tim_cuda_check(owner, cudaGetLastError(), "batched greedy kernels");

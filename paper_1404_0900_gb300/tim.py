@@ -79,6 +79,14 @@ class tim_batch_stats(C.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class tim_tuning(C.Structure):
+    _fields_ = [("width_budget", C.c_uint64), ("team_size", C.c_int), ("chunk", C.c_int),
+                ("trials", C.c_int), ("best_ms", C.c_double), ("default_ms", C.c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 _lib = None
 _P = C.c_void_p
 _SIGS = {
@@ -107,6 +115,7 @@ _SIGS = {
     "tim_set_query_tag": (C.c_int, [_P, C.c_uint32]),
     "tim_set_chunk": (C.c_int, [_P, C.c_int]),
     "tim_run_batch": (C.c_int, [_P, C.c_int, C.c_uint64, C.c_int, _P]),
+    "tim_autotune": (C.c_int, [_P, C.c_uint64, C.c_uint64, _P]),
     "tim_node_select_noalloc": (C.c_int, [C.c_int, _P, C.c_int64, C.c_uint64, _P, _P, C.c_int,
                                           _P, _P]),
 }
@@ -318,6 +327,12 @@ def tim_run_batch(queries, seed: int, plus: bool = True):
     _check(ctx0, lib().tim_run_batch(C.cast(arr, _P), nq, seed, 1 if plus else 0, C.byref(bst)))
     out = [(seeds[i], arr[i].covered_fraction, arr[i].stats.as_dict()) for i in range(nq)]
     return out, bst.as_dict()
+
+
+def tim_autotune(ctx, sample_sets: int, seed: int = 1) -> dict:
+    t = tim_tuning()
+    _check(ctx, lib().tim_autotune(ctx, sample_sets, seed, C.byref(t)))
+    return t.as_dict()
 
 
 def tim_set_team_size(ctx, warps: int):

@@ -261,3 +261,19 @@ def test_device_resident_load_matches_host_load(eng):
     assert a == b and np.array_equal(off_a, off_b) and np.array_equal(wid_a, wid_b)
     for x, y in zip(_sets(off_a, mem_a), _sets(off_b, mem_b)):
         assert np.array_equal(x, y)
+
+
+def test_autotune_keeps_results(eng):
+    g = inputs.rmat(13, seed=2)
+    w = inputs.weighted_cascade(g)
+    og = _load(eng, g, w, O.IC)
+    before = tim.tim_run(eng.ctx, 5, 0.5, 1.0, 9)
+    t = tim.tim_autotune(eng.ctx, 20000, 9)
+    assert t["trials"] >= 3 and t["best_ms"] <= t["default_ms"] + 1e-9
+    after = tim.tim_run(eng.ctx, 5, 0.5, 1.0, 9)
+    assert np.array_equal(before[0], after[0]) and before[2]["theta"] == after[2]["theta"]
+    ref = O.tim_plus(og, 5, 0.5, 1.0, 9)
+    assert np.array_equal(after[0], ref.seeds)
+    tim.tim_set_width_budget(eng.ctx, 16384)
+    tim.tim_set_team_size(eng.ctx, 0)
+    tim.tim_set_chunk(eng.ctx, 2)
