@@ -278,6 +278,36 @@ def kpt_estimation(g: OracleGraph, k: int, ell: float, seed: int, nthreads: int 
                      sets_generated=gen)
 
 
+def kpt_estimation_from(g: OracleGraph, k: int, ell: float, seed: int, i0: int,
+                        nthreads: int = 0, tag: int = 0) -> tuple[KptResult, bool]:
+    """Algorithm 2 started at a predicted round i0 (a rule the paper does not have).
+
+    The prediction is accepted when round i0 - 1 fails the stop test of Algorithm 2
+    and round i0 passes it (for i0 = 1: when round 1 passes); the result is then
+    round i0's estimate KPT* = n sum / (2 c_i0), with round i0's sets as R'. Otherwise
+    the result is plain Algorithm 2's. Rounds use the same set ids as the plain sweep,
+    so round i's sets do not depend on which rounds ran. Returns (result, accepted)."""
+    rounds = kpt_rounds(g.n)
+    if rounds < 1 or i0 < 1:
+        return kpt_estimation(g, k, ell, seed, nthreads, tag), False
+    i0 = min(i0, rounds)
+
+    def round_sum(i):
+        c = c_i(g.n, ell, i)
+        s, _ = kappa_sum(g, k, seed, make_sid(PHASE_KPT, i, tag << 32), c, nthreads)
+        return s, c
+
+    lo_pass = False
+    if i0 >= 2:
+        s, c = round_sum(i0 - 1)
+        lo_pass = s > (c << (63 - (i0 - 1)))
+    s, c = round_sum(i0)
+    if not lo_pass and s > (c << (63 - i0)):
+        kpt = float(g.n) * math.ldexp(float(s), -63) / (2.0 * float(c))
+        return KptResult(kpt_star=kpt, stop_round=i0, last_round=i0, last_c=c, last_sum=s), True
+    return kpt_estimation(g, k, ell, seed, nthreads, tag), False
+
+
 # --------------------------------------------------------------- Algorithm 3
 
 @dataclass
@@ -350,8 +380,13 @@ class TimResult:
 
 
 def tim_plus(g: OracleGraph, k: int, eps: float, ell: float, seed: int, nthreads: int = 0,
-             theta_override: int | None = None, tag: int = 0) -> TimResult:
-    kpt = kpt_estimation(g, k, ell, seed, nthreads, tag)
+             theta_override: int | None = None, tag: int = 0,
+             start_round: int | None = None) -> TimResult:
+    """TIM+ (Section 4.1); with start_round, Algorithm 2 is kpt_estimation_from."""
+    if start_round is None:
+        kpt = kpt_estimation(g, k, ell, seed, nthreads, tag)
+    else:
+        kpt, _ = kpt_estimation_from(g, k, ell, seed, start_round, nthreads, tag)
     ref = refine_kpt(g, k, ell, eps, seed, kpt, nthreads, tag)
     theta = theta_override if theta_override is not None else theta_from(g.n, k, eps, ell,
                                                                           ref.kpt_plus)

@@ -9,6 +9,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <vector>
 
@@ -75,18 +76,6 @@ int tim_read_scalars(tim_ctx* ctx) {
     return TIM_OK;
 }
 
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev) {
-        cudaGetDevice(&prev);
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard() {
-        int cur = -1;
-        cudaGetDevice(&cur);
-        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
-    }
-};
 
 static double elapsed_ms(tim_ctx* ctx, int a, int b) {
     float ms = 0.f;
@@ -126,9 +115,6 @@ double tim_host_lambda_prime(int64_t n, double eps_p, double ell) {
     return (2.0 + eps_p) * ell * (double)n * log((double)n) / (eps_p * eps_p);
 }
 
-static inline uint64_t make_sid(uint64_t phase, uint64_t round, uint64_t j) {
-    return (phase << 56) | (round << 48) | j;
-}
 
 // ------------------------------------------------------------------- the ABI
 
@@ -438,6 +424,152 @@ int tim_kappa_sum(tim_ctx* ctx, int k, uint64_t seed, uint64_t first_set_id, uin
     return TIM_OK;
 }
 
+// Stop test of Algorithm 2 at round i: sum / c_i > 2^-i with the sum in 2^-63 fixed
+// point, i.e. S > c_i 2^(63 - i), compared exactly in integers.
+static inline bool kpt_passes(unsigned __int128 ksum, uint64_t c, int i) {
+    return ksum > ((unsigned __int128)c << (63 - i));
+}
+
+// One query of kpt_multi: inputs, then Algorithm 2's outputs.
+struct KptJob {
+    tim_ctx* ctx = nullptr;
+    int k = 0;
+    double ell = 1.0;
+    uint32_t tag = 0;
+    int i0 = 0;  // learned start round; 0 = plain sweep
+    double kpt = 1.0;
+    int stop = 0, last = 0, accepted = 0;
+    uint64_t last_c = 0, sets = 0, width = 0;
+};
+
+static constexpr int MULTI_MAX = 256;  // entries per multi-query launch
+
+static int run_multi_chunks(tim_ctx* owner, std::vector<MultiQuery>& mq, uint64_t seed) {
+    for (size_t b = 0; b < mq.size(); b += MULTI_MAX)
+        TIM_TRY(tim_sample_multi(owner, mq.data() + b,
+                                 (int)std::min<size_t>(MULTI_MAX, mq.size() - b), seed));
+    return TIM_OK;
+}
+
+// Algorithm 2 for several queries, each on its own context, sampled by shared
+// multi-query launches. A job with a start round i0 first runs rounds i0 - 1 (kappa
+// only) and i0 (stored) in one launch together with every other such job; it is
+// accepted when round i0 - 1 fails the stop test and round i0 passes (i0 = 1: when
+// round 1 passes). All other jobs then run the plain sweep in lockstep from round 1;
+// rounds already seen to fail are not sampled again unless they are a job's last
+// round (whose sets must end up in the store), so a rejected job returns exactly what
+// the plain sweep returns. *launches counts the multi-query sampling calls.
+static int kpt_multi(tim_ctx* owner, KptJob* jobs, int nq, uint64_t seed, int* launches) {
+    std::vector<int> rounds(nq);
+    std::vector<std::array<int, 2>> known_fail(nq, {0, 0});
+    std::vector<char> active(nq, 1);
+    int max_rounds = 0;
+    for (int q = 0; q < nq; q++) {
+        KptJob& J = jobs[q];
+        rounds[q] = tim_host_rounds(J.ctx->n);
+        if (rounds[q] < 1) J.i0 = 0;
+        J.i0 = std::min(J.i0, rounds[q]);
+        max_rounds = std::max(max_rounds, rounds[q]);
+        J.ctx->n_sets = J.ctx->members = 0;
+    }
+    std::vector<MultiQuery> mq;
+    std::vector<std::pair<int, int>> who;  // (job, round) of each entry
+    auto add = [&](int q, int r, int flags) {
+        const KptJob& J = jobs[q];
+        MultiQuery m;
+        m.ctx = J.ctx;
+        m.req.seed = seed;
+        m.req.sid0 = make_sid(1, (uint64_t)r, (uint64_t)J.tag << 32);
+        m.req.count = tim_host_c_i(J.ctx->n, J.ell, r);
+        m.req.flags = flags;
+        m.req.k = J.k;
+        mq.push_back(m);
+        who.push_back({q, r});
+    };
+    // learned start rounds: rounds i0 - 1 and i0 of every predicted job in one launch
+    for (int q = 0; q < nq; q++) {
+        if (jobs[q].i0 < 1) continue;
+        if (jobs[q].i0 >= 2) add(q, jobs[q].i0 - 1, SAMPLE_KAPPA);
+        add(q, jobs[q].i0, SAMPLE_EMIT | SAMPLE_KAPPA);
+    }
+    if (!mq.empty()) {
+        TIM_TRY(run_multi_chunks(owner, mq, seed));
+        ++*launches;
+        std::vector<int> lo_pass(nq, 0), hi_pass(nq, 0);
+        for (size_t e = 0; e < mq.size(); e++) {
+            const int q = who[e].first, r = who[e].second;
+            KptJob& J = jobs[q];
+            const uint64_t c = mq[e].req.count;
+            J.sets += c;
+            J.width += mq[e].res.wsum;
+            const bool pass = kpt_passes(mq[e].res.ksum, c, r);
+            if (r == J.i0) {
+                hi_pass[q] = pass;
+                if (pass) J.kpt = (double)J.ctx->n * ldexp((double)mq[e].res.ksum, -63) / (2.0 * (double)c);
+                J.last = r;
+                J.last_c = c;
+            } else {
+                lo_pass[q] = pass;
+            }
+        }
+        for (int q = 0; q < nq; q++) {
+            KptJob& J = jobs[q];
+            if (J.i0 < 1) continue;
+            if (!lo_pass[q] && hi_pass[q]) {
+                J.accepted = 1;
+                J.stop = J.i0;
+                active[q] = 0;
+            } else {
+                J.kpt = 1.0;
+                if (J.i0 >= 2 && !lo_pass[q]) known_fail[q][0] = J.i0 - 1;
+                if (!hi_pass[q]) known_fail[q][1] = J.i0;
+            }
+        }
+    }
+    // the plain sweep, all remaining jobs in lockstep
+    for (int r = 1; r <= max_rounds; r++) {
+        mq.clear();
+        who.clear();
+        for (int q = 0; q < nq; q++) {
+            if (!active[q] || r > rounds[q]) continue;
+            const bool seen_fail = known_fail[q][0] == r || known_fail[q][1] == r;
+            if (seen_fail && r != rounds[q]) continue;
+            add(q, r, SAMPLE_EMIT | SAMPLE_KAPPA);
+        }
+        if (mq.empty()) continue;
+        TIM_TRY(run_multi_chunks(owner, mq, seed));
+        ++*launches;
+        for (size_t e = 0; e < mq.size(); e++) {
+            const int q = who[e].first;
+            KptJob& J = jobs[q];
+            const uint64_t c = mq[e].req.count;
+            J.last = r;
+            J.last_c = c;
+            J.sets += c;
+            J.width += mq[e].res.wsum;
+            if (kpt_passes(mq[e].res.ksum, c, r)) {
+                J.kpt = (double)J.ctx->n * ldexp((double)mq[e].res.ksum, -63) / (2.0 * (double)c);
+                J.stop = r;
+                active[q] = 0;
+            }
+        }
+    }
+    return TIM_OK;
+}
+
+static void kpt_keep_state(tim_ctx* c, const KptJob& J, uint64_t seed) {
+    c->have_kpt = true;
+    c->kpt_star = J.kpt;
+    c->kpt_round = J.stop;
+    c->kpt_last_round = J.last;
+    c->kpt_last_c = J.last_c;
+    c->kpt_sets = J.sets;
+    c->kpt_width = J.width;
+    c->kpt_k = J.k;
+    c->kpt_ell = J.ell;
+    c->kpt_seed = seed;
+}
+
 // Algorithm 2. Every round emits its sets too, so that the stopping round's sets are
 // R' of Algorithm 3 without regenerating them.
 int tim_kpt_estimate(tim_ctx* ctx, int k, double ell, uint64_t seed, double* kpt_star,
@@ -484,6 +616,31 @@ int tim_kpt_estimate(tim_ctx* ctx, int k, double ell, uint64_t seed, double* kpt
     ctx->kpt_seed = seed;
     if (kpt_star) *kpt_star = ctx->kpt_star;
     if (round) *round = ctx->kpt_round;
+    return TIM_OK;
+}
+
+int tim_kpt_estimate_learned(tim_ctx* ctx, tim_mlp* mlp, int k, double ell, uint64_t seed,
+                             double* kpt_star, int* round, int* predicted, int* accepted) {
+    if (!ctx || !mlp) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    if (k < 1 || k > ctx->n || !(ell > 0.0)) return tim_fail(ctx, TIM_ERR_ARG, "need 1 <= k <= n, l > 0");
+    DeviceGuard g(ctx->device);
+    ctx->have_kpt = false;
+    KptJob J;
+    J.ctx = ctx;
+    J.k = k;
+    J.ell = ell;
+    J.tag = ctx->query_tag;
+    tim_ctx* one[1] = {ctx};
+    TIM_TRY(tim_learned_start_rounds(mlp, one, &k, 1, &J.i0));
+    const int i0 = J.i0;
+    int launches = 0;
+    TIM_TRY(kpt_multi(ctx, &J, 1, seed, &launches));
+    kpt_keep_state(ctx, J, seed);
+    if (kpt_star) *kpt_star = J.kpt;
+    if (round) *round = J.stop;
+    if (predicted) *predicted = i0;
+    if (accepted) *accepted = J.accepted;
     return TIM_OK;
 }
 
@@ -574,7 +731,7 @@ int tim_covered_count(tim_ctx* ctx, const int32_t* seeds, int n_seeds, uint64_t 
 
 static int run_common(tim_ctx* ctx, bool plus, int k, double eps, double ell, uint64_t seed,
                       int32_t* seeds, double* covered_fraction, tim_stats* st,
-                      uint64_t theta_override) {
+                      uint64_t theta_override, tim_mlp* mlp) {
     if (!ctx || !seeds) return TIM_ERR_ARG;
     if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
     if (k < 1 || k > ctx->n || !(eps > 0.0) || !(ell > 0.0))
@@ -583,7 +740,12 @@ static int run_common(tim_ctx* ctx, bool plus, int k, double eps, double ell, ui
     tim_stats s;
     memset(&s, 0, sizeof s);
     cudaEventRecord(ctx->ev[0], ctx->stream);
-    TIM_TRY(tim_kpt_estimate(ctx, k, ell, seed, nullptr, nullptr));
+    int predicted = 0, accepted = 0;
+    if (mlp)
+        TIM_TRY(tim_kpt_estimate_learned(ctx, mlp, k, ell, seed, nullptr, nullptr, &predicted,
+                                         &accepted));
+    else
+        TIM_TRY(tim_kpt_estimate(ctx, k, ell, seed, nullptr, nullptr));
     cudaEventRecord(ctx->ev[1], ctx->stream);
     double lower = ctx->kpt_star;
     if (plus) {
@@ -625,6 +787,9 @@ static int run_common(tim_ctx* ctx, bool plus, int k, double eps, double ell, ui
     s.ms_select_sample = elapsed_ms(ctx, 2, 3);
     s.ms_select_greedy = elapsed_ms(ctx, 3, 4);
     s.ms_total = elapsed_ms(ctx, 0, 4);
+    s.kpt_sets = ctx->kpt_sets;
+    s.kpt_predicted_round = predicted;
+    s.kpt_accepted = accepted;
     if (covered_fraction) *covered_fraction = theta ? (double)cov / (double)theta : 0.0;
     if (st) *st = s;
     return TIM_OK;
@@ -632,12 +797,19 @@ static int run_common(tim_ctx* ctx, bool plus, int k, double eps, double ell, ui
 
 int tim_run(tim_ctx* ctx, int k, double eps, double ell, uint64_t seed, int32_t* seeds,
             double* covered_fraction, tim_stats* stats, uint64_t theta_override) {
-    return run_common(ctx, true, k, eps, ell, seed, seeds, covered_fraction, stats, theta_override);
+    return run_common(ctx, true, k, eps, ell, seed, seeds, covered_fraction, stats, theta_override,
+                      nullptr);
+}
+
+int tim_run_learned(tim_ctx* ctx, tim_mlp* mlp, int k, double eps, double ell, uint64_t seed,
+                    int32_t* seeds, double* covered_fraction, tim_stats* stats) {
+    if (!mlp) return TIM_ERR_ARG;
+    return run_common(ctx, true, k, eps, ell, seed, seeds, covered_fraction, stats, 0, mlp);
 }
 
 int tim_run_tim(tim_ctx* ctx, int k, double eps, double ell, uint64_t seed, int32_t* seeds,
                 double* covered_fraction, tim_stats* stats) {
-    return run_common(ctx, false, k, eps, ell, seed, seeds, covered_fraction, stats, 0);
+    return run_common(ctx, false, k, eps, ell, seed, seeds, covered_fraction, stats, 0, nullptr);
 }
 
 
@@ -646,7 +818,8 @@ int tim_run_tim(tim_ctx* ctx, int k, double eps, double ell, uint64_t seed, int3
 // shared launches captured in a CUDA graph. Query q draws from the key of `seed` with
 // set-id tag queries[q].tag, so its result equals tim_run on its context with
 // tim_set_query_tag(ctx, tag) and the same seed.
-int tim_run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_batch_stats* bst) {
+static int run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_mlp* mlp,
+                     tim_batch_stats* bst) {
     if (!qs || nq <= 0 || nq > 256) return TIM_ERR_ARG;
     tim_ctx* owner = qs[0].ctx;
     if (!owner) return TIM_ERR_ARG;
@@ -665,63 +838,41 @@ int tim_run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_batch_stat
     for (int i = 0; i < nq; i++) CUDA_TRY(owner, cudaStreamSynchronize(qs[i].ctx->stream));
     cudaEvent_t* ev = owner->ev;
     cudaEventRecord(ev[0], owner->stream);
-    std::vector<int> rounds(nq), stop(nq, 0), last(nq, 0);
-    std::vector<uint64_t> last_c(nq, 0), sets(nq, 0), width(nq, 0);
-    std::vector<double> kpt(nq, 1.0);
-    std::vector<char> active(nq, 1);
-    int max_rounds = 0;
+    std::vector<KptJob> jobs(nq);
     for (int i = 0; i < nq; i++) {
-        rounds[i] = tim_host_rounds(qs[i].ctx->n);
-        max_rounds = std::max(max_rounds, rounds[i]);
-        qs[i].ctx->n_sets = qs[i].ctx->members = 0;
+        jobs[i].ctx = qs[i].ctx;
+        jobs[i].k = qs[i].k;
+        jobs[i].ell = qs[i].ell;
+        jobs[i].tag = qs[i].tag;
         memset(&qs[i].stats, 0, sizeof(tim_stats));
     }
-    std::vector<MultiQuery> mq;
-    std::vector<int> idx;
-    // Algorithm 2, all queries in lockstep
-    int launched_rounds = 0;
-    for (int r = 1; r <= max_rounds; r++) {
-        mq.clear();
-        idx.clear();
-        for (int i = 0; i < nq; i++) {
-            if (!active[i] || r > rounds[i]) continue;
-            MultiQuery m;
-            m.ctx = qs[i].ctx;
-            m.req.seed = seed;
-            m.req.sid0 = make_sid(1, (uint64_t)r, (uint64_t)qs[i].tag << 32);
-            m.req.count = tim_host_c_i(qs[i].ctx->n, qs[i].ell, r);
-            m.req.flags = SAMPLE_EMIT | SAMPLE_KAPPA;
-            m.req.k = qs[i].k;
-            mq.push_back(m);
-            idx.push_back(i);
-        }
-        if (mq.empty()) break;
-        launched_rounds++;
-        TIM_TRY(tim_sample_multi(owner, mq.data(), (int)mq.size(), seed));
-        for (size_t t = 0; t < mq.size(); t++) {
-            const int i = idx[t];
-            const uint64_t c = mq[t].req.count;
-            last[i] = r;
-            last_c[i] = c;
-            sets[i] += c;
-            width[i] += mq[t].res.wsum;
-            const unsigned __int128 bound = (unsigned __int128)c << (63 - r);
-            if (mq[t].res.ksum > bound) {
-                kpt[i] = (double)qs[i].ctx->n * ldexp((double)mq[t].res.ksum, -63) / (2.0 * (double)c);
-                stop[i] = r;
-                active[i] = 0;
-            }
-        }
-    }
-    cudaEventRecord(ev[1], owner->stream);
-    std::vector<double> kpt_plus(kpt), kpt_prime(nq, 0.0), eps_p(nq, 0.0);
-    std::vector<uint64_t> theta_p(nq, 0), cov_p(nq, 0), width_p(nq, 0);
+    // Algorithm 2 for every query: learned start rounds first when a network is given
     std::vector<tim_ctx*> ctxs(nq);
-    std::vector<int> ks(nq);
+    std::vector<int> ks(nq), i0(nq, 0);
     for (int i = 0; i < nq; i++) {
         ctxs[i] = qs[i].ctx;
         ks[i] = qs[i].k;
     }
+    double ms_predict = 0.0;
+    if (mlp) {
+        cudaEventRecord(ev[5], owner->stream);
+        TIM_TRY(tim_learned_start_rounds(mlp, ctxs.data(), ks.data(), nq, i0.data()));
+        cudaEventRecord(ev[6], owner->stream);
+        for (int i = 0; i < nq; i++) jobs[i].i0 = i0[i];
+    }
+    int launched_rounds = 0;
+    TIM_TRY(kpt_multi(owner, jobs.data(), nq, seed, &launched_rounds));
+    std::vector<double> kpt(nq);
+    std::vector<uint64_t> sets(nq), width(nq);
+    for (int i = 0; i < nq; i++) {
+        kpt[i] = jobs[i].kpt;
+        sets[i] = jobs[i].sets;
+        width[i] = jobs[i].width;
+    }
+    cudaEventRecord(ev[1], owner->stream);
+    std::vector<double> kpt_plus(kpt), kpt_prime(nq, 0.0), eps_p(nq, 0.0);
+    std::vector<uint64_t> theta_p(nq, 0), cov_p(nq, 0), width_p(nq, 0);
+    std::vector<MultiQuery> mq;
     if (plus) {
         // Algorithm 3: greedy on every query's R', then theta' fresh sets each
         TIM_TRY(tim_greedy_batch(owner, ctxs.data(), ks.data(), nq, nullptr, nullptr, true));
@@ -775,11 +926,15 @@ int tim_run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_batch_stat
     cudaEventRecord(ev[4], owner->stream);
     TIM_TRY(tim_sync(owner));
     uint64_t sets_all = 0;
+    int accepted_all = 0;
     for (int i = 0; i < nq; i++) {
         tim_stats& s = qs[i].stats;
-        s.kpt_round = stop[i];
-        s.kpt_last_round = last[i];
+        s.kpt_round = jobs[i].stop;
+        s.kpt_last_round = jobs[i].last;
         s.kpt_star = kpt[i];
+        s.kpt_sets = sets[i];
+        s.kpt_predicted_round = i0[i];
+        s.kpt_accepted = jobs[i].accepted;
         s.kpt_prime = kpt_prime[i];
         s.kpt_plus = kpt_plus[i];
         s.eps_prime = eps_p[i];
@@ -795,13 +950,10 @@ int tim_run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_batch_stat
         qs[i].covered_fraction = theta[i] ? (double)cov[i] / (double)theta[i] : 0.0;
         sets_all += s.sets_total;
         // keep the per-context state consistent with a single run
-        tim_ctx* c = qs[i].ctx;
-        c->have_kpt = true;
-        c->kpt_round = stop[i];
-        c->kpt_last_round = last[i];
-        c->kpt_last_c = last_c[i];
-        c->kpt_star = kpt[i];
+        kpt_keep_state(qs[i].ctx, jobs[i], seed);
+        accepted_all += jobs[i].accepted;
     }
+    if (mlp) ms_predict = elapsed_ms(owner, 5, 6);
     if (bst) {
         memset(bst, 0, sizeof *bst);
         bst->queries = nq;
@@ -812,8 +964,20 @@ int tim_run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_batch_stat
         bst->ms_select_sample = elapsed_ms(owner, 2, 3);
         bst->ms_select_greedy = elapsed_ms(owner, 3, 4);
         bst->ms_total = elapsed_ms(owner, 0, 4);
+        bst->learned_accepted = accepted_all;
+        bst->ms_predict = ms_predict;
     }
     return TIM_OK;
+}
+
+int tim_run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_batch_stats* bst) {
+    return run_batch(qs, nq, seed, plus, nullptr, bst);
+}
+
+int tim_run_batch_learned(tim_query* qs, int nq, uint64_t seed, int plus, tim_mlp* mlp,
+                          tim_batch_stats* bst) {
+    if (!mlp) return TIM_ERR_ARG;
+    return run_batch(qs, nq, seed, plus, mlp, bst);
 }
 
 }  // extern "C"

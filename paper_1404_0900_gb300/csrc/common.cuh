@@ -128,6 +128,10 @@ struct tim_ctx {
     uint64_t kpt_seed = 0;
     uint64_t kpt_sets = 0, kpt_width = 0;
 
+    // pooled graph features of the learned start round (learned.cu), cached per graph
+    bool have_feat = false;
+    float feat[TIM_GRAPH_FEATURES] = {};
+
     // kernel timing of the RR sampler (events around each launch)
     tim_profile prof = {};
 
@@ -158,6 +162,24 @@ int tim_sync(tim_ctx* ctx);
 int tim_read_scalars(tim_ctx* ctx);  // copy DevScalars to h_scal and synchronise
 int tim_zero_scalars(tim_ctx* ctx);
 DevScalars* tim_dscal(tim_ctx* ctx);
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (prev >= 0 && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+// Set id of the j-th RR set of `round` in `phase` (the tag sits in bits 32..47 of j).
+static inline uint64_t make_sid(uint64_t phase, uint64_t round, uint64_t j) {
+    return (phase << 56) | (round << 48) | j;
+}
 
 // primitives (prims.cu)
 // Exclusive scan of uint32 counts into uint64 offsets out[0..count] (out[count] = total).
@@ -214,6 +236,10 @@ int tim_mark_seeds(tim_ctx* ctx, const int32_t* d_seeds, int k);
 // context's seeds_dev, host copies where host_seeds[i] is not NULL.
 int tim_greedy_batch(tim_ctx* owner, tim_ctx* const* ctxs, const int* ks, int nq,
                      int32_t* const* host_seeds, uint64_t* covered, bool use_graph);
+
+// learned.cu: start rounds i0 of Algorithm 2 predicted for ctxs[q] with k = ks[q]
+int tim_learned_start_rounds(tim_mlp* mlp, tim_ctx* const* ctxs, const int* ks, int nq,
+                             int* i0);
 
 // scalar formulas (api.cu)
 uint64_t tim_host_c_i(int64_t n, double ell, int i);

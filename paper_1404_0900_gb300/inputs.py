@@ -215,3 +215,108 @@ def random_small(n: int, m: int, seed: int) -> Graph:
         if u != v:
             pairs.add((u, v))
     return from_edges(n, sorted(pairs), name=f"rand{n}_{m}_{seed}")
+
+
+# ------------------------------------------------------- generators on the GPU
+#
+# The same graph families drawn with torch on a CUDA device, for workloads of many
+# graphs (the start-round training set) where host generation would dominate. The
+# draws come from torch's generator, so a device graph differs from the host graph of
+# the same seed; each is a fixed function of its seed on one software stack.
+
+@dataclass
+class DeviceGraph:
+    n: int
+    rowptr: "object"  # torch int64[n+1] on the device
+    dst: "object"     # torch int32[m] on the device
+    name: str = ""
+
+    @property
+    def m(self) -> int:
+        return int(self.dst.shape[0])
+
+    def to_host(self) -> Graph:
+        return Graph(n=self.n, rowptr=self.rowptr.cpu().numpy(), dst=self.dst.cpu().numpy(),
+                     name=self.name)
+
+
+def _torch_gen(seed: int, device):
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    return g
+
+
+def csr_from_pairs_device(n: int, src, dst, name: str = "") -> DeviceGraph:
+    """Device version of csr_from_pairs (self-loops and duplicates dropped)."""
+    import torch
+    keep = src != dst
+    key = torch.unique(src[keep].to(torch.int64) * n + dst[keep].to(torch.int64), sorted=True)
+    s = key // n
+    d = (key % n).to(torch.int32)
+    rowptr = torch.zeros(n + 1, dtype=torch.int64, device=key.device)
+    rowptr[1:] = torch.cumsum(torch.bincount(s, minlength=n), 0)
+    return DeviceGraph(n=n, rowptr=rowptr, dst=d.contiguous(), name=name)
+
+
+def rmat_device(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19,
+                c: float = 0.19, seed: int = 1, device="cuda") -> DeviceGraph:
+    """R-MAT as in rmat(), drawn on the device (16-bit quadrant draws per level)."""
+    import torch
+    n = 1 << scale
+    draws = edge_factor * n
+    gen = _torch_gen(seed, device)
+    cut = [int(round(v * 65536)) for v in (a, a + b, a + b + c)]
+    lut = torch.zeros(65536, dtype=torch.int64, device=device)
+    lut[cut[0]:cut[1]] = 1
+    lut[cut[1]:cut[2]] = 2
+    lut[cut[2]:] = 3
+    src = torch.zeros(draws, dtype=torch.int64, device=device)
+    dst = torch.zeros(draws, dtype=torch.int64, device=device)
+    for _ in range(scale):
+        q = lut[torch.randint(0, 65536, (draws,), generator=gen, device=device)]
+        src = (src << 1) | (q >> 1)
+        dst = (dst << 1) | (q & 1)
+    return csr_from_pairs_device(n, src, dst, name=f"rmat{scale}_dev")
+
+
+def chung_lu_device(n: int, m_draws: int, gamma: float = 2.1, seed: int = 1,
+                    device="cuda") -> DeviceGraph:
+    """Directed Chung-Lu power-law graph from m_draws edge draws (node weights
+    (i+1)^(-1/(gamma-1)), destinations on a seeded permutation of the ids); self-loops
+    and duplicates dropped, so m is below m_draws."""
+    import torch
+    gen = _torch_gen(seed, device)
+    w = (torch.arange(n, dtype=torch.float64, device=device) + 1.0) ** (-1.0 / (gamma - 1.0))
+    cdf = torch.cumsum(w, 0)
+    cdf /= cdf[-1].clone()
+    perm = torch.randperm(n, generator=gen, device=device)
+    u = torch.rand(m_draws, generator=gen, device=device, dtype=torch.float64)
+    s = torch.searchsorted(cdf, u, right=True).clamp_(max=n - 1)
+    u = torch.rand(m_draws, generator=gen, device=device, dtype=torch.float64)
+    d = perm[torch.searchsorted(cdf, u, right=True).clamp_(max=n - 1)]
+    return csr_from_pairs_device(n, s, d, name=f"chunglu{n}_dev")
+
+
+def weighted_cascade_device(g: DeviceGraph):
+    """p(u, v) = 1 / indeg(v) as a device float32 tensor."""
+    import torch
+    indeg = torch.bincount(g.dst.to(torch.int64), minlength=g.n).to(torch.float64)
+    return (1.0 / indeg[g.dst.to(torch.int64)]).to(torch.float32)
+
+
+def trivalency_device(g: DeviceGraph, seed: int = 1):
+    import torch
+    gen = _torch_gen(seed, g.dst.device)
+    vals = torch.tensor([0.1, 0.01, 0.001], dtype=torch.float32, device=g.dst.device)
+    return vals[torch.randint(0, 3, (g.m,), generator=gen, device=g.dst.device)]
+
+
+def lt_random_normalised_device(g: DeviceGraph, seed: int = 1):
+    """Uniform [0, 1) in-weights normalised to sum to one per node."""
+    import torch
+    gen = _torch_gen(seed, g.dst.device)
+    r = torch.rand(g.m, generator=gen, device=g.dst.device, dtype=torch.float64)
+    d = g.dst.to(torch.int64)
+    tot = torch.zeros(g.n, dtype=torch.float64, device=g.dst.device).index_add_(0, d, r)
+    return (r / tot[d]).to(torch.float32)

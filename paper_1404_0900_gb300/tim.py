@@ -39,6 +39,7 @@ class tim_stats(C.Structure):
         ("width_total", C.c_uint64), ("width_select", C.c_uint64),
         ("ms_kpt", C.c_double), ("ms_refine", C.c_double), ("ms_select_sample", C.c_double),
         ("ms_select_greedy", C.c_double), ("ms_total", C.c_double),
+        ("kpt_sets", C.c_uint64), ("kpt_predicted_round", C.c_int), ("kpt_accepted", C.c_int),
     ]
 
     def as_dict(self) -> dict:
@@ -73,7 +74,8 @@ class tim_query(C.Structure):
 class tim_batch_stats(C.Structure):
     _fields_ = [("queries", C.c_int), ("kpt_launch_rounds", C.c_int), ("sets_total", C.c_uint64),
                 ("ms_kpt", C.c_double), ("ms_refine", C.c_double), ("ms_select_sample", C.c_double),
-                ("ms_select_greedy", C.c_double), ("ms_total", C.c_double)]
+                ("ms_select_greedy", C.c_double), ("ms_total", C.c_double),
+                ("learned_accepted", C.c_int), ("ms_predict", C.c_double)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -118,7 +120,24 @@ _SIGS = {
     "tim_autotune": (C.c_int, [_P, C.c_uint64, C.c_uint64, _P]),
     "tim_node_select_noalloc": (C.c_int, [C.c_int, _P, C.c_int64, C.c_uint64, _P, _P, C.c_int,
                                           _P, _P]),
+    "tim_graph_features": (C.c_int, [_P, _P]),
+    "tim_mlp_create": (C.c_int, [C.POINTER(_P), _P, C.c_int]),
+    "tim_mlp_destroy": (C.c_int, [_P]),
+    "tim_mlp_param_count": (C.c_uint64, [_P]),
+    "tim_mlp_set_params": (C.c_int, [_P, _P, C.c_uint64]),
+    "tim_mlp_get_params": (C.c_int, [_P, _P, C.c_uint64]),
+    "tim_mlp_set_scaling": (C.c_int, [_P, _P, _P, C.c_float, C.c_float]),
+    "tim_mlp_grad": (C.c_int, [_P, _P, _P, C.c_uint64, _P, _P]),
+    "tim_mlp_train": (C.c_int, [_P, _P, _P, C.c_uint64, C.c_int, C.c_float, _P]),
+    "tim_mlp_predict": (C.c_int, [_P, _P, C.c_uint64, _P]),
+    "tim_kpt_estimate_learned": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_uint64, _P, _P, _P,
+                                           _P]),
+    "tim_run_learned": (C.c_int, [_P, _P, C.c_int, C.c_double, C.c_double, C.c_uint64, _P, _P,
+                                  _P]),
+    "tim_run_batch_learned": (C.c_int, [_P, C.c_int, C.c_uint64, C.c_int, _P, _P]),
 }
+
+TIM_GRAPH_FEATURES, TIM_START_FEATURES, TIM_MLP_HIDDEN, TIM_MLP_MAX_IN = 8, 12, 64, 32
 
 
 def library_path() -> str:
@@ -307,9 +326,10 @@ def tim_set_chunk(ctx, sets: int):
     _check(ctx, lib().tim_set_chunk(ctx, sets))
 
 
-def tim_run_batch(queries, seed: int, plus: bool = True):
+def tim_run_batch(queries, seed: int, plus: bool = True, mlp=None):
     """queries: list of dicts {ctx, k, eps, ell, tag}. Returns (list of (seeds, covered
-    fraction, stats dict), batch stats dict)."""
+    fraction, stats dict), batch stats dict). With `mlp` (a tim_mlp handle), Algorithm 2
+    starts from learned rounds (tim_run_batch_learned)."""
     nq = len(queries)
     arr = (tim_query * nq)()
     seeds = []
@@ -324,7 +344,12 @@ def tim_run_batch(queries, seed: int, plus: bool = True):
         arr[i].seeds = s.ctypes.data_as(_P)
     bst = tim_batch_stats()
     ctx0 = queries[0]["ctx"] if nq else None
-    _check(ctx0, lib().tim_run_batch(C.cast(arr, _P), nq, seed, 1 if plus else 0, C.byref(bst)))
+    if mlp is None:
+        _check(ctx0, lib().tim_run_batch(C.cast(arr, _P), nq, seed, 1 if plus else 0,
+                                         C.byref(bst)))
+    else:
+        _check(ctx0, lib().tim_run_batch_learned(C.cast(arr, _P), nq, seed, 1 if plus else 0, mlp,
+                                                 C.byref(bst)))
     out = [(seeds[i], arr[i].covered_fraction, arr[i].stats.as_dict()) for i in range(nq)]
     return out, bst.as_dict()
 
@@ -343,6 +368,86 @@ def tim_get_profile(ctx, reset: bool = False) -> dict:
     p = tim_profile()
     _check(ctx, lib().tim_get_profile(ctx, C.byref(p), 1 if reset else 0))
     return p.as_dict()
+
+
+def tim_graph_features(ctx) -> np.ndarray:
+    out = np.zeros(TIM_GRAPH_FEATURES, dtype=np.float32)
+    _check(ctx, lib().tim_graph_features(ctx, _ptr(out)))
+    return out
+
+
+def tim_mlp_create(ctx, d_in: int = TIM_START_FEATURES):
+    h = _P()
+    _check(ctx, lib().tim_mlp_create(C.byref(h), ctx, d_in))
+    return h
+
+
+def tim_mlp_destroy(mlp):
+    lib().tim_mlp_destroy(mlp)
+
+
+def tim_mlp_param_count(mlp) -> int:
+    return int(lib().tim_mlp_param_count(mlp))
+
+
+def tim_mlp_set_params(ctx, mlp, params):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(ctx, lib().tim_mlp_set_params(mlp, _ptr(p), p.size))
+
+
+def tim_mlp_get_params(ctx, mlp) -> np.ndarray:
+    p = np.zeros(tim_mlp_param_count(mlp), dtype=np.float32)
+    _check(ctx, lib().tim_mlp_get_params(mlp, _ptr(p), p.size))
+    return p
+
+
+def tim_mlp_set_scaling(ctx, mlp, in_mu, in_isd, out_mu: float, out_sd: float):
+    mu = np.ascontiguousarray(in_mu, dtype=np.float32)
+    isd = np.ascontiguousarray(in_isd, dtype=np.float32)
+    _check(ctx, lib().tim_mlp_set_scaling(mlp, _ptr(mu), _ptr(isd), out_mu, out_sd))
+
+
+def tim_mlp_grad(ctx, mlp, x, y) -> tuple[float, np.ndarray]:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    loss = C.c_float()
+    g = np.zeros(tim_mlp_param_count(mlp), dtype=np.float32)
+    _check(ctx, lib().tim_mlp_grad(mlp, _ptr(x), _ptr(y), y.shape[0], C.byref(loss), _ptr(g)))
+    return float(loss.value), g
+
+
+def tim_mlp_train(ctx, mlp, x, y, steps: int, lr: float) -> np.ndarray:
+    """Full-batch Adam on the device; returns the loss before each step."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.ascontiguousarray(y, dtype=np.float32)
+    hist = np.zeros(max(steps, 1), dtype=np.float32)
+    _check(ctx, lib().tim_mlp_train(mlp, _ptr(x), _ptr(y), y.shape[0], steps, lr, _ptr(hist)))
+    return hist[:steps]
+
+
+def tim_mlp_predict(ctx, mlp, x) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    out = np.zeros(x.shape[0], dtype=np.float32)
+    _check(ctx, lib().tim_mlp_predict(mlp, _ptr(x), x.shape[0], _ptr(out)))
+    return out
+
+
+def tim_kpt_estimate_learned(ctx, mlp, k: int, ell: float, seed: int):
+    """Returns (KPT*, stopping round, predicted start round, accepted)."""
+    kpt, rnd, pred, acc = C.c_double(), C.c_int(), C.c_int(), C.c_int()
+    _check(ctx, lib().tim_kpt_estimate_learned(ctx, mlp, k, ell, seed, C.byref(kpt), C.byref(rnd),
+                                               C.byref(pred), C.byref(acc)))
+    return kpt.value, rnd.value, pred.value, bool(acc.value)
+
+
+def tim_run_learned(ctx, mlp, k: int, eps: float, ell: float, seed: int):
+    """TIM+ with the learned start round. Returns (seeds, covered fraction, stats)."""
+    seeds = np.zeros(k, dtype=np.int32)
+    frac = C.c_double()
+    st = tim_stats()
+    _check(ctx, lib().tim_run_learned(ctx, mlp, k, eps, ell, seed, _ptr(seeds), C.byref(frac),
+                                      C.byref(st)))
+    return seeds, frac.value, st.as_dict()
 
 
 class Engine:
