@@ -26,7 +26,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_1404_0900_gb300 import inputs  # noqa: E402
+from paper_1404_0900_gb300 import inputs, start_round  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per examined in-edge of the IC sampler passes, from the ncu
@@ -57,7 +57,10 @@ def parse_args(argv=None):
     p.add_argument("--no-batch", action="store_true",
                    help="skip the 64-query batched-vs-plain comparison")
     p.add_argument("--batch-queries", type=int, default=64)
-    p.add_argument("--mode", choices=["timplus", "sample", "batch"], default="timplus",
+    p.add_argument("--no-learned", action="store_true",
+                   help="skip the learned-start-round comparisons")
+    p.add_argument("--mode", choices=["timplus", "sample", "batch", "learned"],
+                   default="timplus",
                    help="timplus: the TIM+ step (default); sample: only RR-set generation "
                         "(tim_sample_rr of --theta NodeSelection sets), for profiling")
     p.add_argument("--theta", type=int, default=1_000_000)
@@ -341,6 +344,8 @@ def run_ours(args):
                                             n_ic=ic["sets_total"], n_lt=lt["sets_total"])
     if not args.no_batch and world == 1:
         line["batched_vs_plain"] = run_batch_compare(args)
+    if not args.no_learned and world == 1:
+        line["learned_vs_plain"] = run_learned_compare(args, g, w_ic, w_lt)
     return line
 
 
@@ -524,27 +529,133 @@ def run_batch_compare(args, reps: int = 2):
             e1.synchronize()
             return out, e0.elapsed_time(e1)
 
+        mlp = None
+        if not getattr(args, "no_learned", False) and start_round.available():
+            mlp, _ = start_round.load(engines[0].ctx)
         plain()
         tim.tim_run_batch(queries, args.seed)
-        t_plain, t_batch = [], []
+        if mlp is not None:
+            tim.tim_run_batch(queries, args.seed, mlp=mlp)
+        t_plain, t_batch, t_learn = [], [], []
         for _ in range(reps):
             p_out, tp = timed(plain)
             (b_out, bst), tb = timed(lambda: tim.tim_run_batch(queries, args.seed))
             t_plain.append(tp)
             t_batch.append(tb)
+            if mlp is not None:
+                (l_out, lst), tl = timed(lambda: tim.tim_run_batch(queries, args.seed, mlp=mlp))
+                t_learn.append(tl)
         same = all(np.array_equal(p[0], b[0]) and p[1]["theta"] == b[2]["theta"]
                    for p, b in zip(p_out, b_out))
         sets = sum(st["sets_total"] for _, st in p_out)
+        learned = None
+        if mlp is not None:
+            ident = [bool(np.array_equal(p[0], l[0])) for p, l in zip(p_out, l_out)]
+            # spread of differing seed sets: coverage of fresh RR sets (set-id phase 6)
+            rel = []
+            for i, (p, l) in enumerate(zip(p_out, l_out)):
+                if ident[i]:
+                    continue
+                ctx = queries[i]["ctx"]
+                cnt = 200_000
+                cp = tim.tim_covered_count(ctx, p[0], args.seed + 7, 6 << 56, cnt)
+                cl = tim.tim_covered_count(ctx, l[0], args.seed + 7, 6 << 56, cnt)
+                rel.append((cl - cp) / max(cp, 1))
+            tl = min(t_learn)
+            learned = {
+                "learned_batched_ms": tl, "speedup_vs_plain": min(t_plain) / tl,
+                "speedup_vs_batched": min(t_batch) / tl,
+                "accepted": lst["learned_accepted"], "fallback_rate":
+                    1.0 - lst["learned_accepted"] / len(specs),
+                "seeds_identical_to_plain": int(sum(ident)),
+                "spread_rel_diff_of_differing": rel,
+                "kpt_launch_rounds": {"batched": bst["kpt_launch_rounds"],
+                                      "learned_batched": lst["kpt_launch_rounds"]},
+                "phase_ms": {k: lst[k] for k in ("ms_kpt", "ms_predict", "ms_refine",
+                                                 "ms_select_sample", "ms_select_greedy")},
+                "kpt_rr_sets": {"batched": sum(b[2]["kpt_sets"] for b in b_out),
+                                "learned_batched": sum(x[2]["kpt_sets"] for x in l_out)},
+            }
+            tim.tim_mlp_destroy(mlp)
     finally:
         for e in engines:
             e.close()
     tp, tb = min(t_plain), min(t_batch)
-    return {"queries": len(specs), "scales": "R-MAT U{12..20}", "plain_ms": tp,
-            "batched_ms": tb, "speedup": tp / tb, "seeds_identical": bool(same),
-            "rr_sets": sets, "batched_rr_sets_per_s": sets / (tb / 1e3),
-            "batched_phase_ms": {k: bst[k] for k in ("ms_kpt", "ms_refine", "ms_select_sample",
-                                                     "ms_select_greedy")},
-            "autotune": tuning}
+    out = {"queries": len(specs), "scales": "R-MAT U{12..20}", "plain_ms": tp,
+           "batched_ms": tb, "speedup": tp / tb, "seeds_identical": bool(same),
+           "rr_sets": sets, "batched_rr_sets_per_s": sets / (tb / 1e3),
+           "batched_phase_ms": {k: bst[k] for k in ("ms_kpt", "ms_refine", "ms_select_sample",
+                                                    "ms_select_greedy")},
+           "autotune": tuning}
+    if learned is not None:
+        out["learned"] = learned
+    return out
+
+
+def run_learned_compare(args, g20=None, w_ic=None, w_lt=None, reps: int = 2):
+    """Plain TIM+ against TIM+ from the learned start round on held-out graphs (the
+    network was trained on device-drawn graphs of scales 12-18): the host R-MAT scale-20
+    graph of the main workload and a device-drawn R-MAT scale-22 graph (seed 2022), IC
+    weighted cascade and LT 1/indeg each, k = 50, eps = 0.1. Reports device times, the
+    predicted and plain stopping rounds, acceptance (fallback rate) and the spread of
+    both seed sets estimated on 10^6 fresh RR sets (set-id phase 6)."""
+    import torch
+
+    from paper_1404_0900_gb300 import tim
+    if not start_round.available():
+        return {"unavailable": "no trained start-round network in the package"}
+    if g20 is None:
+        g20 = inputs.rmat(20, seed=1)
+        w_ic, w_lt = inputs.weighted_cascade(g20), inputs.lt_inverse_indegree(g20)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    k, eps, ell, seed = 50, 0.1, 1.0, args.seed
+    cases = []
+    with tim.Engine(0, stream) as eng:
+        mlp, rec = start_round.load(eng.ctx)
+        try:
+            g22 = inputs.rmat_device(22, seed=2022)
+            w22 = inputs.weighted_cascade_device(g22)  # IC 1/indeg; LT 1/indeg is the same
+            graphs = [("rmat20", g20.n, g20.m, torch.from_numpy(g20.rowptr).cuda(),
+                       torch.from_numpy(g20.dst).cuda(),
+                       {0: torch.from_numpy(w_ic).cuda(), 1: torch.from_numpy(w_lt).cuda()}),
+                      ("rmat22", g22.n, g22.m, g22.rowptr, g22.dst, {0: w22, 1: w22})]
+            for name, n, m, rp, dst, ws in graphs:
+                for model in (tim.TIM_IC, tim.TIM_LT):
+                    torch.cuda.synchronize()
+                    tim.tim_load_graph_device(eng.ctx, n, m, rp, dst, ws[model], model)
+                    tim.tim_autotune(eng.ctx, 500_000, seed)
+                    tim.tim_run(eng.ctx, k, eps, ell, seed)
+                    tim.tim_run_learned(eng.ctx, mlp, k, eps, ell, seed)
+                    tp, tl = [], []
+                    for _ in range(reps):
+                        ps, _, pst = tim.tim_run(eng.ctx, k, eps, ell, seed)
+                        ls, _, lst = tim.tim_run_learned(eng.ctx, mlp, k, eps, ell, seed)
+                        tp.append(pst)
+                        tl.append(lst)
+                    bp = min(tp, key=lambda s: s["ms_total"])
+                    bl = min(tl, key=lambda s: s["ms_total"])
+                    cnt = 1_000_000
+                    cp = tim.tim_covered_count(eng.ctx, ps, seed + 7, 6 << 56, cnt)
+                    cl = tim.tim_covered_count(eng.ctx, ls, seed + 7, 6 << 56, cnt)
+                    cases.append({
+                        "graph": name, "model": "IC" if model == tim.TIM_IC else "LT",
+                        "n": n, "m": m,
+                        "plain_ms": bp["ms_total"], "learned_ms": bl["ms_total"],
+                        "plain_kpt_ms": bp["ms_kpt"], "learned_kpt_ms": bl["ms_kpt"],
+                        "plain_round": bp["kpt_round"], "predicted_round": bl["kpt_predicted_round"],
+                        "accepted": bool(bl["kpt_accepted"]),
+                        "kpt_rr_sets": {"plain": bp["kpt_sets"], "learned": bl["kpt_sets"]},
+                        "seeds_identical": bool(np.array_equal(ps, ls)),
+                        "spread_estimate": {"plain": n * cp / cnt, "learned": n * cl / cnt},
+                    })
+        finally:
+            tim.tim_mlp_destroy(mlp)
+    acc = sum(c["accepted"] for c in cases)
+    return {"k": k, "eps": eps, "cases": cases, "fallback_rate": 1.0 - acc / len(cases),
+            "plain_ms_total": sum(c["plain_ms"] for c in cases),
+            "learned_ms_total": sum(c["learned_ms"] for c in cases),
+            "training": {key: rec.get(key) for key in ("graphs", "samples", "held_out", "seconds")}}
 
 
 def main(argv=None):
@@ -554,6 +665,9 @@ def main(argv=None):
         return
     if args.mode == "batch" and args.impl == "ours":
         print(json.dumps(run_batch_compare(args)), flush=True)
+        return
+    if args.mode == "learned" and args.impl == "ours":
+        print(json.dumps(run_learned_compare(args)), flush=True)
         return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:
