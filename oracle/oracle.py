@@ -61,6 +61,9 @@ def lib():
                                       P, P, P, P, P, P]),
             "or_greedy": (i64, [i64, i64, P, P, i32, P, P]),
             "or_covered_count": (i64, [P, P, P, i64, i64, i32, u64, u64, i64, P, i32]),
+            "or_skip_q": (u64, [u32, i32]),
+            "or_skip_bit": (i32, [u64, u64]),
+            "or_skip_live": (i64, [u64, u64, i64, i64, u32, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -98,6 +101,29 @@ def ic_word(seed: int, sid: int, j: int) -> int:
 
 def lt_word(seed: int, sid: int, v: int) -> int:
     return int(lib().or_lt_word(seed, sid, v))
+
+
+SKIP_MIN_INDEG = 1024  # IC in-lists at least this long with one shared threshold skip
+
+
+def skip_q(t: int, b: int) -> int:
+    """Q_b of the geometric-skip rule: (1 - t/2^32)^(2^b) in 0.64 fixed point."""
+    return int(lib().or_skip_q(t, b))
+
+
+def skip_bit(u: int, q: int) -> bool:
+    """Digit decision of the geometric-skip rule: U / 2^64 < Q / (2^64 + Q)."""
+    return bool(lib().or_skip_bit(u, q))
+
+
+def skip_live(seed: int, sid: int, beg: int, d: int, t: int) -> np.ndarray:
+    """Live relative positions of a d-edge in-list starting at in-CSR position beg
+    whose in-edges share threshold t, under the geometric-skip rule."""
+    out = np.zeros(max(d, 1), dtype=np.int64)
+    r = lib().or_skip_live(seed, sid, beg, d, t, _p(out))
+    if r < 0:
+        raise ValueError("invalid skip list")
+    return out[:r]
 
 
 def kappa(w: int, m: int, k: int) -> float:

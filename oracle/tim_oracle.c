@@ -27,6 +27,11 @@
  *     the out-CSR edges by destination).
  *   - IC coin: live iff x < thr, thr = floor(p * 2^32) for p < 1; p >= 1 is stored as
  *     0xFFFFFFFF and is always live.
+ *   - IC in-lists with at least SKIP_MIN_INDEG in-edges that all carry one threshold
+ *     t, 0 < t < 0xFFFFFFFF (weighted cascade gives every node such a list): instead
+ *     of one coin per in-edge, the live in-edges are found by drawing the geometric
+ *     gaps between them (see skip_iter below). Each in-edge is still live with
+ *     probability t / 2^32, independently (to within 2^-60 per gap digit).
  *   - LT pick: t_j = floor(w_j * 2^32); C_j = inclusive prefix of t over v's
  *     in-edges in in-CSR order, saturated at 2^32 - 1; the first j with x < C_j is
  *     the triggering in-edge, none if x >= C_last.
@@ -63,6 +68,8 @@ typedef unsigned __int128 u128;
 #define TAG_ROOT 0u
 #define TAG_IC 1u
 #define TAG_LT 2u
+#define TAG_SKIP 0x100u /* + digit index b, 0..31 */
+#define SKIP_MIN_INDEG 1024
 
 #define MODEL_IC 0
 #define MODEL_LT 1
@@ -219,6 +226,102 @@ static int64_t indeg(const or_graph* g, int64_t v) { return g->rowptr[v + 1] - g
 
 static int ic_live(uint32_t x, uint32_t thr) { return thr == 0xFFFFFFFFu || x < thr; }
 
+/* ------------------------------------------------ geometric skipping (IC)
+ * For an in-list of d in-edges that are each live with probability p = t / 2^32,
+ * independently, the number G of dead in-edges before the next live one is
+ * geometric: P(G >= g) = q^g with q = 1 - p. Since sum_g q^g = prod_b (1 + q^(2^b)),
+ *   P(G = g) = (1 - q) q^g = prod_b q^(2^b g_b) / (1 + q^(2^b))
+ * for the binary digits g_b of g: the digits are independent, digit b being 1 with
+ * probability rho_b = q^(2^b) / (1 + q^(2^b)), and "some digit >= B is 1", i.e.
+ * G >= 2^B, has probability q^(2^B).
+ *
+ * Fixed point: Q_b approximates q^(2^b) 2^64; Q_0 = (2^32 - t) 2^32 is exact and
+ * Q_(b+1) = floor(Q_b^2 / 2^64). A 64-bit uniform U decides digit b as
+ *   U / 2^64 < Q_b / (2^64 + Q_b)  <=>  U < Q_b  and  floor(U Q_b / 2^64) < Q_b - U,
+ * and "G >= 2^B" as U < Q_B.
+ *
+ * Gap r of a list starts at relative position pos (< d); R = d - pos remaining,
+ * B = bit length of R (so 2^B > R). Uniform U_b (b = 0 .. B) = words (2(r&1),
+ * 2(r&1)+1) (low, high) of Philox counter (sid lo, sid hi, beg + (r >> 1),
+ * TAG_SKIP + b), beg = in-CSR position of the list's first in-edge. If G >= 2^B or
+ * G >= R the list has no further live in-edge; else position pos + G is live and the
+ * next gap starts at pos + G + 1. (r <= pos < d keeps beg + (r >> 1) inside the
+ * list, so no two lists share a counter.) */
+uint64_t or_skip_q(uint32_t t, int b) {
+    uint64_t q = (uint64_t)(0x100000000ull - (uint64_t)t) << 32;
+    for (int i = 0; i < b; i++) q = (uint64_t)(((u128)q * q) >> 64);
+    return q;
+}
+
+int or_skip_bit(uint64_t u, uint64_t q) {
+    return u < q && (uint64_t)(((u128)u * q) >> 64) < q - u;
+}
+
+typedef struct {
+    uint64_t seed, sid;
+    int64_t beg, d, pos, r;
+    uint64_t q[33];
+} skip_iter;
+
+static void skip_begin(skip_iter* it, uint64_t seed, uint64_t sid, int64_t beg, int64_t d,
+                       uint32_t t) {
+    it->seed = seed;
+    it->sid = sid;
+    it->beg = beg;
+    it->d = d;
+    it->pos = 0;
+    it->r = 0;
+    it->q[0] = (uint64_t)(0x100000000ull - (uint64_t)t) << 32;
+    for (int b = 1; b < 33; b++) it->q[b] = (uint64_t)(((u128)it->q[b - 1] * it->q[b - 1]) >> 64);
+}
+
+static uint64_t skip_uniform(const skip_iter* it, int b) {
+    uint32_t w[4];
+    draw(it->seed, it->sid, (uint32_t)(it->beg + (it->r >> 1)), TAG_SKIP + (uint32_t)b, w);
+    return (it->r & 1) ? ((uint64_t)w[3] << 32 | w[2]) : ((uint64_t)w[1] << 32 | w[0]);
+}
+
+/* Next live relative position into *j; 0 when the list has no more. */
+static int skip_next(skip_iter* it, int64_t* j) {
+    if (it->pos >= it->d) return 0;
+    int64_t rem = it->d - it->pos;
+    int B = 0;
+    while (B < 63 && ((int64_t)1 << B) <= rem) B++;
+    if (skip_uniform(it, B) < it->q[B]) return 0;
+    int64_t gap = 0;
+    for (int b = 0; b < B; b++)
+        if (or_skip_bit(skip_uniform(it, b), it->q[b])) gap |= (int64_t)1 << b;
+    if (gap >= rem) return 0;
+    *j = it->pos + gap;
+    it->pos += gap + 1;
+    it->r++;
+    return 1;
+}
+
+/* Live relative positions of one skip list (tests); returns their number. */
+int64_t or_skip_live(uint64_t seed, uint64_t sid, int64_t beg, int64_t d, uint32_t t,
+                     int64_t* out) {
+    if (d < 1 || d > 0x7FFFFFFF || t == 0u || t == 0xFFFFFFFFu) return OR_ERR_ARG;
+    skip_iter it;
+    skip_begin(&it, seed, sid, beg, d, t);
+    int64_t n = 0, j;
+    while (skip_next(&it, &j)) out[n++] = j;
+    return n;
+}
+
+/* Does v's in-list take the skip rule? Then *t is its shared threshold. */
+static int skip_list(const or_graph* g, int64_t v, uint32_t* t) {
+    if (g->model != MODEL_IC) return 0;
+    int64_t a = g->rowptr[v], b = g->rowptr[v + 1];
+    if (b - a < SKIP_MIN_INDEG) return 0;
+    uint32_t t0 = g->thr[a];
+    if (t0 == 0u || t0 == 0xFFFFFFFFu) return 0;
+    for (int64_t j = a + 1; j < b; j++)
+        if (g->thr[j] != t0) return 0;
+    *t = t0;
+    return 1;
+}
+
 /* LT triggering in-edge of v for RR set sid: an in-CSR position, or -1 for none. */
 static int64_t lt_pick(const or_graph* g, uint64_t seed, uint64_t sid, int64_t v) {
     uint32_t x = or_lt_word(seed, sid, v);
@@ -240,7 +343,19 @@ static int64_t rr_bfs(const or_graph* g, uint64_t seed, uint64_t sid, int32_t* m
     while (head < tail) {
         int64_t v = members[head++];
         w += indeg(g, v);
-        if (g->model == MODEL_IC) {
+        uint32_t t;
+        if (g->model == MODEL_IC && skip_list(g, v, &t)) {
+            skip_iter it;
+            int64_t rel;
+            skip_begin(&it, seed, sid, g->rowptr[v], indeg(g, v), t);
+            while (skip_next(&it, &rel)) {
+                int32_t u = g->src[g->rowptr[v] + rel];
+                if (!mark[u]) {
+                    mark[u] = 1;
+                    members[tail++] = u;
+                }
+            }
+        } else if (g->model == MODEL_IC) {
             for (int64_t j = g->rowptr[v]; j < g->rowptr[v + 1]; j++) {
                 int32_t u = g->src[j];
                 if (mark[u]) continue;
@@ -285,7 +400,17 @@ int64_t or_rr_by_definition(const int64_t* rowptr, const int32_t* src, const uin
     }
     int64_t nl = 0;
     for (int64_t v = 0; v < n; v++) {
-        if (model == MODEL_IC) {
+        uint32_t t;
+        if (model == MODEL_IC && skip_list(&g, v, &t)) {
+            skip_iter it;
+            int64_t rel;
+            skip_begin(&it, seed, sid, rowptr[v], rowptr[v + 1] - rowptr[v], t);
+            while (skip_next(&it, &rel)) {
+                lu[nl] = src[rowptr[v] + rel];
+                lv[nl] = v;
+                nl++;
+            }
+        } else if (model == MODEL_IC) {
             for (int64_t j = rowptr[v]; j < rowptr[v + 1]; j++)
                 if (ic_live(or_ic_word(seed, sid, j), thr[j])) {
                     lu[nl] = src[j];
