@@ -103,7 +103,12 @@ def lt_word(seed: int, sid: int, v: int) -> int:
     return int(lib().or_lt_word(seed, sid, v))
 
 
-SKIP_MIN_INDEG = 1024  # IC in-lists at least this long with one shared threshold skip
+SKIP_MIN_INDEG = 32  # shortest IC in-list that can take the geometric-skip rule
+
+
+def skip_applies(d: int, t: int) -> bool:
+    """The skip rule's condition on a list of d in-edges sharing threshold t."""
+    return d >= SKIP_MIN_INDEG and t > 0 and t * (2 * d.bit_length() + 2) < (1 << 32)
 
 
 def skip_q(t: int, b: int) -> int:

@@ -27,11 +27,13 @@
  *     the out-CSR edges by destination).
  *   - IC coin: live iff x < thr, thr = floor(p * 2^32) for p < 1; p >= 1 is stored as
  *     0xFFFFFFFF and is always live.
- *   - IC in-lists with at least SKIP_MIN_INDEG in-edges that all carry one threshold
- *     t, 0 < t < 0xFFFFFFFF (weighted cascade gives every node such a list): instead
- *     of one coin per in-edge, the live in-edges are found by drawing the geometric
- *     gaps between them (see skip_iter below). Each in-edge is still live with
- *     probability t / 2^32, independently (to within 2^-60 per gap digit).
+ *   - IC in-lists of d >= SKIP_MIN_INDEG in-edges that all carry one threshold t with
+ *     0 < t and t * (2 * bitlength(d) + 2) < 2^32 (weighted cascade gives every such
+ *     node one): instead of one coin per in-edge, the live in-edges are found by
+ *     drawing the geometric gaps between them (see skip_iter below). Each in-edge is
+ *     still live with probability t / 2^32, independently (to within 2^-60 per gap
+ *     digit). The bound on t keeps the rule to lists where a few gaps replace many
+ *     coins.
  *   - LT pick: t_j = floor(w_j * 2^32); C_j = inclusive prefix of t over v's
  *     in-edges in in-CSR order, saturated at 2^32 - 1; the first j with x < C_j is
  *     the triggering in-edge, none if x >= C_last.
@@ -68,8 +70,8 @@ typedef unsigned __int128 u128;
 #define TAG_ROOT 0u
 #define TAG_IC 1u
 #define TAG_LT 2u
-#define TAG_SKIP 0x100u /* + digit index b, 0..31 */
-#define SKIP_MIN_INDEG 1024
+#define TAG_SKIP 0x100u /* + digit pair index b >> 1, 0..15 */
+#define SKIP_MIN_INDEG 32
 
 #define MODEL_IC 0
 #define MODEL_LT 1
@@ -241,12 +243,12 @@ static int ic_live(uint32_t x, uint32_t thr) { return thr == 0xFFFFFFFFu || x < 
  * and "G >= 2^B" as U < Q_B.
  *
  * Gap r of a list starts at relative position pos (< d); R = d - pos remaining,
- * B = bit length of R (so 2^B > R). Uniform U_b (b = 0 .. B) = words (2(r&1),
- * 2(r&1)+1) (low, high) of Philox counter (sid lo, sid hi, beg + (r >> 1),
- * TAG_SKIP + b), beg = in-CSR position of the list's first in-edge. If G >= 2^B or
+ * B = bit length of R (so 2^B > R). Uniform U_b (b = 0 .. B) = words (2(b&1),
+ * 2(b&1)+1) (low, high) of Philox counter (sid lo, sid hi, beg + r, TAG_SKIP +
+ * (b >> 1)), beg = in-CSR position of the list's first in-edge. If G >= 2^B or
  * G >= R the list has no further live in-edge; else position pos + G is live and the
- * next gap starts at pos + G + 1. (r <= pos < d keeps beg + (r >> 1) inside the
- * list, so no two lists share a counter.) */
+ * next gap starts at pos + G + 1. (r <= pos < d keeps beg + r inside the list, so no
+ * two lists share a counter.) */
 uint64_t or_skip_q(uint32_t t, int b) {
     uint64_t q = (uint64_t)(0x100000000ull - (uint64_t)t) << 32;
     for (int i = 0; i < b; i++) q = (uint64_t)(((u128)q * q) >> 64);
@@ -277,8 +279,8 @@ static void skip_begin(skip_iter* it, uint64_t seed, uint64_t sid, int64_t beg, 
 
 static uint64_t skip_uniform(const skip_iter* it, int b) {
     uint32_t w[4];
-    draw(it->seed, it->sid, (uint32_t)(it->beg + (it->r >> 1)), TAG_SKIP + (uint32_t)b, w);
-    return (it->r & 1) ? ((uint64_t)w[3] << 32 | w[2]) : ((uint64_t)w[1] << 32 | w[0]);
+    draw(it->seed, it->sid, (uint32_t)(it->beg + it->r), TAG_SKIP + (uint32_t)(b >> 1), w);
+    return (b & 1) ? ((uint64_t)w[3] << 32 | w[2]) : ((uint64_t)w[1] << 32 | w[0]);
 }
 
 /* Next live relative position into *j; 0 when the list has no more. */
@@ -312,10 +314,12 @@ int64_t or_skip_live(uint64_t seed, uint64_t sid, int64_t beg, int64_t d, uint32
 /* Does v's in-list take the skip rule? Then *t is its shared threshold. */
 static int skip_list(const or_graph* g, int64_t v, uint32_t* t) {
     if (g->model != MODEL_IC) return 0;
-    int64_t a = g->rowptr[v], b = g->rowptr[v + 1];
-    if (b - a < SKIP_MIN_INDEG) return 0;
+    int64_t a = g->rowptr[v], b = g->rowptr[v + 1], d = b - a;
+    if (d < SKIP_MIN_INDEG) return 0;
     uint32_t t0 = g->thr[a];
-    if (t0 == 0u || t0 == 0xFFFFFFFFu) return 0;
+    int bl = 0;
+    while (bl < 63 && ((int64_t)1 << bl) <= d) bl++;
+    if (t0 == 0u || (uint64_t)t0 * (uint64_t)(2 * bl + 2) >= 0x100000000ull) return 0;
     for (int64_t j = a + 1; j < b; j++)
         if (g->thr[j] != t0) return 0;
     *t = t0;

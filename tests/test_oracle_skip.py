@@ -1,6 +1,6 @@
-"""Pins for the geometric-skip rule of IC in-lists that share one threshold (at least
-1024 in-edges): each in-edge must be live with probability t / 2^32, independently,
-exactly as with one coin per edge.
+"""Pins for the geometric-skip rule of IC in-lists that share one threshold t (at least
+32 in-edges, t (2 bitlength(d) + 2) < 2^32): each in-edge must be live with
+probability t / 2^32, independently, exactly as with one coin per edge.
 
 - The fixed-point powers Q_b against q^(2^b) computed to 80 digits.
 - The digit decision against the exact rational comparison U (2^64 + Q) < Q 2^64.
@@ -98,8 +98,8 @@ def _python_skip(seed, sid, beg, d, t):
         B = rem.bit_length()
 
         def uni(b):
-            w = O.philox([sid & 0xFFFFFFFF, sid >> 32, beg + (r >> 1), 0x100 + b], key)
-            lo, hi = (int(w[2]), int(w[3])) if r & 1 else (int(w[0]), int(w[1]))
+            w = O.philox([sid & 0xFFFFFFFF, sid >> 32, beg + r, 0x100 + (b >> 1)], key)
+            lo, hi = (int(w[2]), int(w[3])) if b & 1 else (int(w[0]), int(w[1]))
             return hi << 32 | lo
 
         if uni(B) < qs[B]:
@@ -170,3 +170,33 @@ def test_hub_rr_sets_follow_the_binomial():
         want = math.comb(n_leaves, kk) * p ** kk * (1 - p) ** (n_leaves - kk)
         got = np.mean(sizes == kk)
         assert abs(got - want) < 5 * math.sqrt(want * (1 - want) / len(sizes)), (kk, got, want)
+
+
+def test_rule_boundaries():
+    # length and probability bounds of the rule
+    assert not O.skip_applies(31, 1000) and O.skip_applies(32, 1000)
+    assert not O.skip_applies(5000, 0)
+    for d in (32, 100, 1023, 1024, 40000):
+        bl = d.bit_length()
+        lim = ((1 << 32) - 1) // (2 * bl + 2)  # largest t with t (2 bl + 2) < 2^32
+        assert O.skip_applies(d, lim) and not O.skip_applies(d, lim + 1)
+    # weighted cascade: every in-list of 32 or more in-edges qualifies
+    for d in (32, 33, 100, 1000, 10 ** 6):
+        t = int(np.float32(1.0 / d) * np.float64(2 ** 32))
+        assert O.skip_applies(d, t)
+
+
+def test_small_lists_follow_the_rule_in_bfs():
+    # a node with 40 in-edges under weighted cascade (skip) and one with 40 in-edges at
+    # p = 0.3 (coins): both BFS and the drawn world agree, and the hub's live count
+    # over many sets matches Binomial(40, t / 2^32)
+    edges = [(i, 0) for i in range(2, 42)] + [(i, 1) for i in range(42, 82)] + [(0, 1)]
+    g = inputs.from_edges(82, edges)
+    w = inputs.weighted_cascade(g)
+    w[g.dst == 1] = np.float32(0.3)
+    og = O.load_graph(g.n, g.rowptr, g.dst, w, O.IC)
+    for j in range(400):
+        sid = O.make_sid(3, 0, j)
+        a, wa = O.rr_one(og, 6, sid)
+        b, wb = O.rr_by_definition(og, 6, sid)
+        assert np.array_equal(a, b) and wa == wb
