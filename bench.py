@@ -29,12 +29,12 @@ sys.path.insert(0, ROOT)
 from paper_1404_0900_gb300 import inputs, start_round  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) per examined in-edge of the IC sampler passes, from the ncu
+# DRAM bytes (read + write) per RR-set member of the IC sampler passes, from the ncu
 # capture of `bench.py --mode sample --scale 18 --theta 300000` (dram__bytes_read.sum +
-# dram__bytes_write.sum / examined in-edges of that launch); used to scale the traffic of
-# one full-size launch in proportion to its work. None where no capture exists for the
-# current kernel.
-DRAM_BYTES_PER_EDGE = {1: 33.64e6 / 328604055, 2: 704.2e6 / 2766776059, 3: None}
+# dram__bytes_write.sum of the launch / members it produced); used to scale the traffic
+# of one full-size launch in proportion to its work. None where no capture exists for
+# the current kernel.
+DRAM_BYTES_PER_MEMBER = {1: None, 2: None, 3: None}
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
@@ -299,8 +299,8 @@ def run_ours(args):
         peak, peak_src = FALLBACK_HBM_GBS, "fallback"
     ms_dom = p[f"pass{dom}_ms"]
     achieved = alg_bytes / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
-    ratio = DRAM_BYTES_PER_EDGE.get(dom)
-    traffic = ratio * p[f"pass{dom}_width"] / launches_dom if ratio else None
+    ratio = DRAM_BYTES_PER_MEMBER.get(dom)
+    traffic = ratio * p[f"pass{dom}_members"] / launches_dom if ratio else None
     ic = per_model[tim.TIM_IC][-1]
     lt = per_model[tim.TIM_LT][-1]
     line = {
@@ -331,8 +331,8 @@ def run_ours(args):
                      "unit": "GB/s", "frac": achieved / peak,
                      "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
                      "traffic": traffic,
-                     "traffic_note": "DRAM bytes per launch scaled by examined in-edges from "
-                                     "the R-MAT scale-18 ncu capture"},
+                     "traffic_note": "DRAM bytes per launch scaled by members from the R-MAT "
+                                     "scale-18 ncu capture (null: no capture of this kernel)"},
         "sampler_profile": {"IC": prof_ic, "LT": prof_lt},
         "autotune": tuning,
         "clocks": clk,
@@ -350,11 +350,14 @@ def run_ours(args):
 
 
 def sampler_bytes(p: dict, i: int) -> float:
-    """Algorithmic bytes of sampler pass i: 4 B threshold per examined in-edge, 4 B
-    source per live in-edge, 16 B of in-CSR offsets per member, 8 B emitted per member
-    (node and set id), 20 B of per-set records."""
-    return (4.0 * p[f"pass{i}_width"] + 4.0 * p[f"pass{i}_live"] + 24.0 * p[f"pass{i}_members"]
-            + 20.0 * p[f"pass{i}_sets"])
+    """Algorithmic bytes of IC sampler pass i: 4 B threshold per in-edge whose own
+    threshold must be read (in-lists without one shared threshold; a shared threshold
+    is one 8 B word per member), 4 B source per live in-edge, 16 B of in-CSR offsets
+    and 8 B shared-threshold word per member, 8 B emitted per member (node and set id),
+    20 B of per-set records. In-edges that no coin touches (geometric skipping) move
+    no bytes."""
+    return (4.0 * p[f"pass{i}_examined"] + 4.0 * p[f"pass{i}_live"] +
+            32.0 * p[f"pass{i}_members"] + 20.0 * p[f"pass{i}_sets"])
 
 
 # --------------------------------------------------------- the CPU oracle arm
@@ -460,7 +463,10 @@ def run_sample_only(args):
         t = prof[f"pass{i}_ms"]
         b = sampler_bytes(prof, i)
         passes[f"pass{i}"] = {"ms": t, "sets": prof[f"pass{i}_sets"],
-                              "width": prof[f"pass{i}_width"], "algorithmic_bytes": b,
+                              "width": prof[f"pass{i}_width"],
+                              "members": prof[f"pass{i}_members"],
+                              "live": prof[f"pass{i}_live"],
+                              "examined": prof[f"pass{i}_examined"], "algorithmic_bytes": b,
                               "GB/s": b / (t / 1e3) / 1e9 if t > 0 else 0.0}
     width = sum(prof[f"pass{i}_width"] for i in (1, 2, 3))
     return {"mode": "sample", "model": args.model, "scale": args.scale, "theta": args.theta,

@@ -103,7 +103,7 @@ def lt_word(seed: int, sid: int, v: int) -> int:
     return int(lib().or_lt_word(seed, sid, v))
 
 
-SKIP_MIN_INDEG = 32  # shortest IC in-list that can take the geometric-skip rule
+SKIP_MIN_INDEG = 512  # shortest IC in-list that can take the geometric-skip rule
 
 
 def skip_applies(d: int, t: int) -> bool:

@@ -71,7 +71,7 @@ typedef unsigned __int128 u128;
 #define TAG_IC 1u
 #define TAG_LT 2u
 #define TAG_SKIP 0x100u /* + digit pair index b >> 1, 0..15 */
-#define SKIP_MIN_INDEG 32
+#define SKIP_MIN_INDEG 512
 
 #define MODEL_IC 0
 #define MODEL_LT 1

@@ -34,6 +34,7 @@ struct DevScalars {
     unsigned long long width[3];   // sum of widths per tier
     unsigned long long live[3];    // live in-edges followed per tier
     unsigned long long memb[3];    // members per tier
+    unsigned long long exam[3];    // in-edges whose own threshold was read, per tier
 };
 
 enum : int {
@@ -258,6 +259,9 @@ double tim_host_lambda_prime(int64_t n, double eps_p, double ell);
 #define TIM_TAG_ROOT 0u
 #define TIM_TAG_IC 1u
 #define TIM_TAG_LT 2u
+#define TIM_TAG_SKIP 0x100u  // + gap digit pair index b >> 1, 0..15
+// shortest IC in-list sampled by geometric skipping (tim_skip_rule)
+#define TIM_SKIP_MIN_INDEG 512u
 
 // Philox round keys for one seed: key schedule k_r = k_0 + r * W, r = 0..9.
 struct PhiloxKeys {
@@ -294,6 +298,63 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
         c2 = n2;
     }
     return make_uint4(c0, c1, c2, c3);
+}
+
+// Geometric-skip rule for IC in-lists. A list of d in-edges whose in-edges all carry
+// one threshold t (per-node word nt: bit 32 set, low word t) takes the rule when
+// d >= TIM_SKIP_MIN_INDEG, t > 0 and t (2 bitlength(d) + 2) < 2^32: a few geometric
+// gaps then replace many coins. Each in-edge is still live with probability t / 2^32,
+// independently, as with one coin per edge.
+//   The gap G (dead in-edges before the next live one) has P(G >= g) = q^g, q = 1 - p.
+// Since sum_g q^g = prod_b (1 + q^(2^b)), the binary digits of G are independent,
+// digit b being 1 with probability q^(2^b) / (1 + q^(2^b)), and G >= 2^B has
+// probability q^(2^B). With Q_b ~ q^(2^b) 2^64 (Q_0 = (2^32 - t) 2^32 exactly,
+// Q_(b+1) = floor(Q_b^2 / 2^64)) a 64-bit uniform U decides digit b as
+//   U (2^64 + Q_b) < Q_b 2^64  <=>  U < Q_b and floor(U Q_b / 2^64) < Q_b - U,
+// and G >= 2^B (B = bit length of the R in-edges left, so 2^B > R) as U < Q_B.
+// U for digit b of gap r = words (2(b&1), 2(b&1)+1) of Philox counter (sid lo,
+// sid hi, beg + r, TIM_TAG_SKIP + (b >> 1)); beg = in-CSR position of the list's
+// first in-edge (r <= pos < d keeps beg + r inside the list). G >= R or G >= 2^B ends
+// the list; otherwise position pos + G is live and the next gap starts after it.
+__device__ __forceinline__ bool tim_skip_rule(unsigned long long nt, unsigned long long d) {
+    const uint32_t t = (uint32_t)nt;
+    if (!(nt >> 32) || t == 0u || d < TIM_SKIP_MIN_INDEG) return false;
+    const int bl = 64 - __clzll((long long)d);
+    return (unsigned long long)t * (unsigned long long)(2 * bl + 2) < 0x100000000ull;
+}
+
+__device__ __forceinline__ bool skip_digit(unsigned long long U, unsigned long long Q) {
+    return U < Q && __umul64hi(U, Q) < Q - U;
+}
+
+// Live in-edges of a list under the rule, warp-cooperatively: lane b decides digit b
+// of each gap, one ballot gives G. visit(j) runs on every lane with the same in-CSR position j of each live
+// in-edge, in increasing order, and returns true to stop early. All 32 lanes must call
+// it with the same arguments.
+template <class Visit>
+__device__ __forceinline__ void skip_live_warp(uint32_t s0, uint32_t s1, const PhiloxKeys& K,
+                                               uint32_t beg, uint32_t d, uint32_t t, int lane,
+                                               Visit&& visit) {
+    const int bmax = 32 - __clz((int)d);
+    unsigned long long Q = (unsigned long long)(0x100000000ull - (unsigned long long)t) << 32;
+    for (int b = 0; b < bmax && b < lane; b++) Q = __umul64hi(Q, Q);
+    uint32_t pos = 0;
+    for (uint32_t r = 0; pos < d; r++) {
+        const uint32_t rem = d - pos;
+        const int B = 32 - __clz((int)rem);
+        unsigned long long U = 0;
+        if (lane <= B) {
+            const uint4 x = philox4x32_10(s0, s1, beg + r, TIM_TAG_SKIP + (uint32_t)(lane >> 1), K);
+            U = (lane & 1) ? (((unsigned long long)x.w << 32) | x.z)
+                           : (((unsigned long long)x.y << 32) | x.x);
+        }
+        const bool digit = lane < B && skip_digit(U, Q);
+        const bool over = lane == B && U < Q;
+        const uint32_t G = __ballot_sync(0xffffffffu, digit);
+        if (__any_sync(0xffffffffu, over) || G >= rem) break;
+        if (visit(beg + pos + G)) break;
+        pos += G + 1u;
+    }
 }
 
 // Uniform root: floor(x * n / 2^64) with x the first two words of the ROOT draw.

@@ -215,7 +215,8 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                                        uint32_t* queue, uint16_t* slot, int* ctl,
                                        unsigned long long budget, int wt, int team,
                                        unsigned long long* width_out,
-                                       unsigned long long* live_out) {
+                                       unsigned long long* live_out,
+                                       unsigned long long* exam_out) {
     const int lane = threadIdx.x & 31;
     volatile int* vctl = ctl;
     const bool cover = a.flags & SAMPLE_COVER;
@@ -229,7 +230,7 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
         ctl[1] = (cover && marked(a.seed_mark, root)) ? ST_COVERED : 0;
     }
     team_sync<T>(team);
-    unsigned long long width = 0, live = 0;
+    unsigned long long width = 0, live = 0, work = 0, exam = 0;
     if (MODEL == TIM_IC) {
         const uint32_t s0 = (uint32_t)sid, s1 = (uint32_t)(sid >> 32);
         const uint4* thr4 = reinterpret_cast<const uint4*>(a.thr);
@@ -248,18 +249,33 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
             if (stat || head >= tail) break;
             const int nb = min(32, tail - head);
             uint64_t beg = 0, end = 0;
+            // a node's in-edges often share one threshold (weighted cascade: p = 1/indeg);
+            // then no threshold is loaded, t = 0 needs no coins, t = 2^32-1 (p >= 1)
+            // makes every in-edge live without a draw, and a long list is sampled by
+            // geometric skipping
+            unsigned long long nt = 0;
             if (lane < nb) {
                 const uint32_t v = queue[head + lane];
                 beg = __ldg(a.rowptr + v);
                 end = __ldg(a.rowptr + v + 1);
+                nt = __ldg(a.node_thr + v);
             }
+            const bool skip_list = lane < nb && tim_skip_rule(nt, end - beg);
             const unsigned long long dw = warp_sum_u64(end - beg);
-            if (width + dw > budget) {
+            // the budget counts in-edges that take a coin; a skipped list counts as at
+            // most 64
+            const unsigned long long dx =
+                warp_sum_u64(skip_list ? min(end - beg, (uint64_t)64) : end - beg);
+            if (work + dx > budget) {
                 // too heavy for this tier: list the set for the next one
                 if (wt == 0 && lane == 0) ctl[1] |= ST_OVERFLOW;
                 break;
             }
+            work += dx;
             width += dw;
+            // in-lists without a shared threshold read one threshold per in-edge
+            const unsigned long long dt = warp_sum_u64((nt >> 32) ? 0ull : end - beg);
+            if (wt == 0 && lane == 0) exam += dt;
             // 32-bit in-CSR positions (m < 2^32)
             const uint32_t b32 = (uint32_t)beg, e32 = (uint32_t)end;
             const uint32_t ng = e32 > b32 ? ((e32 - 1) >> 2) - (b32 >> 2) + 1 : 0u;
@@ -267,11 +283,6 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
             int flags = 0;
             // hubs first: the whole team strides over one in-list at a time, two groups in
             // flight per lane; only the in-list's first and last group need a range mask
-            // a node's in-edges often share one threshold (weighted cascade: p = 1/indeg);
-            // then no threshold is loaded, t = 0 needs no coins and t = 2^32-1 (p >= 1)
-            // makes every in-edge live without a draw
-            unsigned long long nt = 0;
-            if (lane < nb) nt = __ldg(a.node_thr + queue[head + lane]);
             uint32_t bigmask = __ballot_sync(0xffffffffu, big);
             while (bigmask && !(flags & 3)) {
                 const int b = __ffs(bigmask) - 1;
@@ -282,6 +293,29 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                 const bool shared = (bt >> 32) != 0;
                 const uint32_t t = (uint32_t)bt;
                 if (shared && t == 0u) continue;
+                if (tim_skip_rule(bt, be - bb)) {
+                    // geometric skipping: one step per live in-edge, by the first warp
+                    if (wt == 0) {
+                        int f = 0;
+                        skip_live_warp(s0, s1, K, bb, be - bb, t, lane, [&](uint32_t j) {
+                            if (lane == 0) {
+                                live++;
+                                const uint32_t u = __ldg(a.src + j);
+                                const int r = set_insert<C>(hash, queue, slot, ctl, u);
+                                if (r == INS_FULL) {
+                                    f |= 1;
+                                } else if (r == INS_NEW && cover && marked(a.seed_mark, u)) {
+                                    atomicOr(&ctl[1], ST_COVERED);
+                                    f |= 2;
+                                }
+                            }
+                            f = __shfl_sync(0xffffffffu, f, 0);
+                            return (f & 3) != 0;
+                        });
+                        flags |= f;
+                    }
+                    continue;
+                }
                 const uint32_t gfirst = bb >> 2, glast = (be - 1) >> 2;
                 for (uint32_t gb = gfirst + (uint32_t)(wt * 32); gb <= glast; gb += 64u * T) {
                     const uint32_t g0 = gb + lane, g1 = gb + 32u * T + lane;
@@ -317,7 +351,7 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                 flags = __reduce_or_sync(0xffffffffu, flags);
             }
             // the rest, flattened over the lanes: lane -> (owner node, group)
-            const uint32_t ngs = big ? 0u : ng;
+            const uint32_t ngs = big ? 0u : ng;  // lists under the skip rule are big
             uint32_t incl = ngs;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -387,6 +421,7 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
     team_sync<T>(team);
     *width_out = width;
     *live_out += live;
+    *exam_out += exam;
     return T == 1 ? __shfl_sync(0xffffffffu, vctl[1], 0) : vctl[1];
 }
 
@@ -420,7 +455,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) rr_team_kernel(SampleArgs a) {
         TIER == 1 ? a.count : (uint64_t)min(((volatile unsigned*)&a.ds->cnt1)[0], a.list_cap);
     uint32_t* out_list = TIER == 1 ? a.list1 : a.list2;
     unsigned* out_cnt = TIER == 1 ? &a.ds->cnt1 : &a.ds->cnt2;
-    unsigned long long k_lo = 0, k_hi = 0, wsum = 0, cov = 0, live = 0, memb = 0;
+    unsigned long long k_lo = 0, k_hi = 0, wsum = 0, cov = 0, live = 0, memb = 0, exam = 0;
     const bool emit = a.flags & SAMPLE_EMIT, kap = a.flags & SAMPLE_KAPPA;
     const bool leader = wt == 0 && lane == 0;
     for (;;) {
@@ -440,7 +475,8 @@ __global__ void __launch_bounds__(WARPS * 32, 4) rr_team_kernel(SampleArgs a) {
             const uint64_t j = TIER == 1 ? it : a.list1[it];
             unsigned long long width;
             const int st = team_rr<MODEL, C, T, SampleArgs>(a, a.K, a.sid0 + j, hash, queue, slot,
-                                                            ctl, budget, wt, team, &width, &live);
+                                                            ctl, budget, wt, team, &width, &live,
+                                                            &exam);
             const int tail = min(T == 1 ? __shfl_sync(0xffffffffu, ((volatile int*)ctl)[0], 0)
                                         : ((volatile int*)ctl)[0],
                                  C::Q);
@@ -497,6 +533,7 @@ __global__ void __launch_bounds__(WARPS * 32, 4) rr_team_kernel(SampleArgs a) {
     }
     live = warp_sum_u64(live);
     if (lane == 0 && live) atomicAdd(&a.ds->live[TIER - 1], live);
+    if (lane == 0 && exam) atomicAdd(&a.ds->exam[TIER - 1], exam);
     if (leader) {
         if (kap) atomic_add_u128(&a.ds->ksum_lo, &a.ds->ksum_hi, k_lo, k_hi);
         if (wsum) {
@@ -714,7 +751,7 @@ struct QArgs {
 constexpr int MAXQ = 256;  // queries per multi-query launch
 
 struct QAcc {
-    unsigned long long k_lo, k_hi, wsum, cov, live, memb;
+    unsigned long long k_lo, k_hi, wsum, cov, live, memb, exam;
 };
 
 template <int TIER>
@@ -730,8 +767,9 @@ __device__ __forceinline__ void flush_acc(const QueryDesc* qd, int qi, QAcc& acc
         if (acc.cov) atomicAdd(&ds->covered, acc.cov);
         if (lv) atomicAdd(&ds->live[TIER - 1], lv);
         if (acc.memb) atomicAdd(&ds->memb[TIER - 1], acc.memb);
+        if (acc.exam) atomicAdd(&ds->exam[TIER - 1], acc.exam);
     }
-    acc = QAcc{0, 0, 0, 0, 0, 0};
+    acc = QAcc{0, 0, 0, 0, 0, 0, 0};
 }
 
 // TIER 1: shared-memory sets of every query (global set index across queries); TIER 2:
@@ -764,7 +802,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
     uint2* out_list = TIER == 1 ? ma.list1 : ma.list2;
     unsigned* out_cnt = TIER == 1 ? &ma.cnt[0] : &ma.cnt[1];
     const bool leader = wt == 0 && lane == 0;
-    QAcc acc{0, 0, 0, 0, 0, 0};
+    QAcc acc{0, 0, 0, 0, 0, 0, 0};
     int cur_q = -1;
     for (;;) {
         unsigned long long i0 = 0;
@@ -811,10 +849,12 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
             int st;
             if (model == TIM_IC)
                 st = team_rr<TIM_IC, C, T, QArgs>(qa, ma.K, d.sid0 + j, hash, queue, slot, ctl,
-                                                  budget, wt, team, &width, &acc.live);
+                                                  budget, wt, team, &width, &acc.live,
+                                                  &acc.exam);
             else
                 st = team_rr<TIM_LT, C, T, QArgs>(qa, ma.K, d.sid0 + j, hash, queue, slot, ctl,
-                                                  budget, wt, team, &width, &acc.live);
+                                                  budget, wt, team, &width, &acc.live,
+                                                  &acc.exam);
             const int tail = min(T == 1 ? __shfl_sync(0xffffffffu, ((volatile int*)ctl)[0], 0)
                                         : ((volatile int*)ctl)[0],
                                  C::Q);
@@ -1049,6 +1089,7 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
             uint64_t* W[3] = {&P.pass1_width, &P.pass2_width, &P.pass3_width};
             uint64_t* V[3] = {&P.pass1_live, &P.pass2_live, &P.pass3_live};
             uint64_t* M[3] = {&P.pass1_members, &P.pass2_members, &P.pass3_members};
+            uint64_t* X[3] = {&P.pass1_examined, &P.pass2_examined, &P.pass3_examined};
             for (int i = 0; i < 3; i++) {
                 *L[i] += 1;
                 *T[i] += t[i];
@@ -1056,6 +1097,7 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
                 *W[i] += h.width[i];
                 *V[i] += h.live[i];
                 *M[i] += h.memb[i];
+                *X[i] += h.exam[i];
             }
         }
         if (res) {

@@ -7,7 +7,10 @@
 // together, one BFS level per launch sequence:
 //   - the level's frontier is a list of (slot, node) items (nodes with in-edges only);
 //   - each item's in-list is cut into 4-aligned groups of in-CSR positions and an
-//     exclusive scan over the items gives every group a global index;
+//     exclusive scan over the items gives every group a global index (an in-list
+//     under the geometric-skip rule of common.cuh gets one placeholder group, since
+//     the group-to-item mapping needs every item to own a group; one warp per such
+//     item draws its live in-edges in bulk_skip_kernel);
 //   - warps take contiguous ranges of 32 groups, so a hub's in-list is spread over the
 //     whole GPU; each lane draws one Philox block (4 coin words, keyed on set id and
 //     in-CSR position, as in the first pass) and loads 4 thresholds with one 16-byte
@@ -36,6 +39,7 @@ struct BulkArgs {
     const uint64_t* rowptr;
     const uint32_t* src;
     const uint32_t* thr;
+    const unsigned long long* node_thr;  // per-node shared threshold (bit 32: shared)
     uint64_t n, m;
     PhiloxKeys K;
     uint64_t sid0;
@@ -103,12 +107,19 @@ __global__ void bulk_init_kernel(BulkArgs a) {
     }
 }
 
+// Does in-list [beg, end) with per-node threshold word nt take the skip rule?
+__device__ __forceinline__ bool skip_rule(unsigned long long nt, uint64_t beg, uint64_t end) {
+    return tim_skip_rule(nt, end - beg);
+}
+
 __global__ void bulk_ng_kernel(BulkArgs a, uint32_t* ng) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.lvl_n;
          i += (uint64_t)gridDim.x * blockDim.x) {
         const uint32_t v = a.F[a.lvl_lo + i].y;
         const uint64_t beg = a.rowptr[v], end = a.rowptr[v + 1];
-        ng[i] = (uint32_t)(((end - 1) >> 2) - (beg >> 2) + 1);  // end > beg for frontier items
+        ng[i] = skip_rule(a.node_thr[v], beg, end)
+                    ? 1u  // placeholder, ignored by bulk_expand_kernel
+                    : (uint32_t)(((end - 1) >> 2) - (beg >> 2) + 1);  // end > beg here
     }
 }
 
@@ -183,6 +194,7 @@ __global__ void __launch_bounds__(256) bulk_expand_kernel(BulkArgs a) {
                 beg = __ldg(a.rowptr + v);
                 end = __ldg(a.rowptr + v + 1);
                 g = (beg >> 2) + (t - gstart);
+                work = !skip_rule(__ldg(a.node_thr + v), beg, end);
             }
         }
         uint4 x = make_uint4(0, 0, 0, 0), tv = make_uint4(0, 0, 0, 0);
@@ -223,6 +235,54 @@ __global__ void __launch_bounds__(256) bulk_expand_kernel(BulkArgs a) {
         }
         i0 = __shfl_sync(0xffffffffu, i, 31);
         live_acc += nlive;
+    }
+    live_acc = __reduce_add_sync(0xffffffffu, live_acc);
+    if (lane == 0 && live_acc) atomicAdd(&a.bs->live, (unsigned long long)live_acc);
+}
+
+// The level's items under the skip rule: one warp per item draws the live in-edges
+// by geometric skipping and handles each like bulk_expand_kernel does.
+__global__ void __launch_bounds__(256) bulk_skip_kernel(BulkArgs a) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const bool cover = a.flags & SAMPLE_COVER;
+    uint32_t live_acc = 0;
+    for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < a.lvl_n;
+         i += nw) {
+        const uint2 it = a.F[a.lvl_lo + i];
+        const uint32_t s = it.x, v = it.y;
+        const uint64_t beg = __ldg(a.rowptr + v), end = __ldg(a.rowptr + v + 1);
+        const unsigned long long nt = __ldg(a.node_thr + v);
+        if (!skip_rule(nt, beg, end)) continue;
+        if (cover && *(volatile uint32_t*)&a.slot_flag[s]) continue;
+        const uint64_t sid = a.sid0 + __ldg(a.list + a.base + s);
+        skip_live_warp((uint32_t)sid, (uint32_t)(sid >> 32), a.K, (uint32_t)beg,
+                       (uint32_t)(end - beg), (uint32_t)nt, lane, [&](uint32_t p) {
+                           bool fresh = false;
+                           uint32_t u = 0;
+                           uint64_t ub = 0, ue = 0;
+                           if (lane == 0) {
+                               live_acc++;
+                               u = __ldg(a.src + p);
+                               const uint32_t b = 1u << (u & 31);
+                               const uint32_t old =
+                                   atomicOr(&a.bitmap[(uint64_t)s * a.words + (u >> 5)], b);
+                               fresh = !(old & b);
+                               if (fresh) {
+                                   ub = __ldg(a.rowptr + u);
+                                   ue = __ldg(a.rowptr + u + 1);
+                                   atomicAdd(&a.slot_width[s], ue - ub);
+                                   atomicAdd(&a.slot_cnt[s], 1u);
+                                   if (cover && marked(a.seed_mark, u)) a.slot_flag[s] = 1u;
+                               }
+                           }
+                           warp_append(fresh, s, u, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2,
+                                       lane);
+                           const bool push = fresh && ue > ub && !(cover && a.slot_flag[s]);
+                           warp_append(push, s, u, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1,
+                                       lane);
+                           return false;
+                       });
     }
     live_acc = __reduce_add_sync(0xffffffffu, live_acc);
     if (lane == 0 && live_acc) atomicAdd(&a.bs->live, (unsigned long long)live_acc);
@@ -316,6 +376,7 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
     a.rowptr = (const uint64_t*)ctx->rowptr.p;
     a.src = (const uint32_t*)ctx->src.p;
     a.thr = (const uint32_t*)ctx->thr.p;
+    a.node_thr = (const unsigned long long*)ctx->node_thr.p;
     a.n = n;
     a.m = (uint64_t)ctx->m;
     a.K = tim_philox_keys(req.seed);
@@ -374,6 +435,8 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
                                         (uint64_t*)ctx->bulk_gp.p, a.lvl_n));
             bulk_expand_kernel<<<GX * 4, 256, 0, ctx->stream>>>(a);
             LAUNCH_CHECK(ctx, "bulk_expand_kernel");
+            bulk_skip_kernel<<<GX * 2, 256, 0, ctx->stream>>>(a);
+            LAUNCH_CHECK(ctx, "bulk_skip_kernel");
             CUDA_TRY(ctx, cudaMemcpyAsync(&hb, a.bs, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream));
             TIM_TRY(tim_sync(ctx));
             if (hb.err) overflow = true;

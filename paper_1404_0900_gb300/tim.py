@@ -59,6 +59,8 @@ class tim_profile(C.Structure):
         ("pass3_launches", C.c_uint64), ("pass3_ms", C.c_double),
         ("pass3_sets", C.c_uint64), ("pass3_width", C.c_uint64), ("pass3_live", C.c_uint64),
         ("pass3_members", C.c_uint64),
+        ("pass1_examined", C.c_uint64), ("pass2_examined", C.c_uint64),
+        ("pass3_examined", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:

@@ -277,3 +277,50 @@ def test_autotune_keeps_results(eng):
     tim.tim_set_width_budget(eng.ctx, 16384)
     tim.tim_set_team_size(eng.ctx, 0)
     tim.tim_set_chunk(eng.ctx, 2)
+
+
+def _hub_graph(n, m_background, hub_degrees, seed):
+    """Random background graph plus hubs 0, 1, ... with the given in-degrees (their
+    in-lists then fall under the geometric-skip rule when they share a threshold)."""
+    rng = np.random.default_rng(seed)
+    src = [rng.integers(0, n, m_background)]
+    dst = [rng.integers(len(hub_degrees), n, m_background)]  # hubs get exactly their degree
+    for h, d in enumerate(hub_degrees):
+        src.append(rng.choice(np.arange(len(hub_degrees), n), size=d, replace=False))
+        dst.append(np.full(d, h))
+        # out-edges, so that RR sets often reach the hub
+        src.append(np.full(300, h))
+        dst.append(rng.choice(np.arange(len(hub_degrees), n), size=300, replace=False))
+    return inputs.csr_from_pairs(n, np.concatenate(src), np.concatenate(dst), name="hubs")
+
+
+@pytest.mark.parametrize("weights", ["wc", "p0.002", "p0.3_heavy", "mixed"])
+@pytest.mark.parametrize("budget,team", [(16384, 0), (64, 1), (0, 8), (1 << 40, 0)])
+def test_skip_lists_bit_exact_in_every_pass(eng, weights, budget, team):
+    if weights == "p0.3_heavy":  # sets beyond the pass-2 queue: the batched third pass
+        g = _hub_graph(20000, 100000, [1024, 1500, 3000, 5000], seed=1)
+        w = inputs.constant(g, 0.3)
+        count = 600
+    else:
+        g = _hub_graph(12000, 60000, [511, 512, 1500, 3000, 9000], seed=2)
+        if weights == "wc":
+            w = inputs.weighted_cascade(g)
+        elif weights == "p0.002":
+            w = inputs.constant(g, 0.002)
+        else:  # hub 2's in-list gets one different probability: per-edge coins there
+            w = inputs.weighted_cascade(g)
+            w[np.flatnonzero(g.dst == 2)[7]] = np.float32(0.25)
+        count = 20000
+    og = _load(eng, g, w, O.IC)
+    tim.tim_set_width_budget(eng.ctx, budget)
+    tim.tim_set_team_size(eng.ctx, team)
+    try:
+        _compare_store(eng, og, 5, O.make_sid(3, 0, 0), count)
+        k = O.kappa_sum(og, 10, 5, O.make_sid(1, 3, 0), count)
+        assert tim.tim_kappa_sum(eng.ctx, 10, 5, O.make_sid(1, 3, 0), count) == k
+        seeds = np.array([0, 1, 7, 11], dtype=np.int32)
+        assert tim.tim_covered_count(eng.ctx, seeds, 5, 77, count) == \
+            O.covered_count(og, 5, 77, count, seeds)
+    finally:
+        tim.tim_set_width_budget(eng.ctx, 16384)
+        tim.tim_set_team_size(eng.ctx, 0)

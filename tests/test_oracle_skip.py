@@ -1,5 +1,5 @@
 """Pins for the geometric-skip rule of IC in-lists that share one threshold t (at least
-32 in-edges, t (2 bitlength(d) + 2) < 2^32): each in-edge must be live with
+512 in-edges, t (2 bitlength(d) + 2) < 2^32): each in-edge must be live with
 probability t / 2^32, independently, exactly as with one coin per edge.
 
 - The fixed-point powers Q_b against q^(2^b) computed to 80 digits.
@@ -174,24 +174,24 @@ def test_hub_rr_sets_follow_the_binomial():
 
 def test_rule_boundaries():
     # length and probability bounds of the rule
-    assert not O.skip_applies(31, 1000) and O.skip_applies(32, 1000)
+    assert not O.skip_applies(511, 1000) and O.skip_applies(512, 1000)
     assert not O.skip_applies(5000, 0)
-    for d in (32, 100, 1023, 1024, 40000):
+    for d in (512, 1000, 1023, 1024, 40000):
         bl = d.bit_length()
         lim = ((1 << 32) - 1) // (2 * bl + 2)  # largest t with t (2 bl + 2) < 2^32
         assert O.skip_applies(d, lim) and not O.skip_applies(d, lim + 1)
     # weighted cascade: every in-list of 32 or more in-edges qualifies
-    for d in (32, 33, 100, 1000, 10 ** 6):
+    for d in (512, 513, 1000, 4096, 10 ** 6):
         t = int(np.float32(1.0 / d) * np.float64(2 ** 32))
         assert O.skip_applies(d, t)
 
 
-def test_small_lists_follow_the_rule_in_bfs():
-    # a node with 40 in-edges under weighted cascade (skip) and one with 40 in-edges at
-    # p = 0.3 (coins): both BFS and the drawn world agree, and the hub's live count
-    # over many sets matches Binomial(40, t / 2^32)
-    edges = [(i, 0) for i in range(2, 42)] + [(i, 1) for i in range(42, 82)] + [(0, 1)]
-    g = inputs.from_edges(82, edges)
+def test_lists_at_the_length_bound_follow_the_rule_in_bfs():
+    # nodes with 511 and 512 in-edges under weighted cascade (coins, then skip) and one
+    # with 600 in-edges at p = 0.3 (coins): BFS and the drawn world agree
+    edges = [(i, 0) for i in range(3, 515)] + [(i, 1) for i in range(515, 1115)] + \
+        [(i, 2) for i in range(1115, 1626)] + [(0, 1), (2, 0)]
+    g = inputs.from_edges(1626, edges)
     w = inputs.weighted_cascade(g)
     w[g.dst == 1] = np.float32(0.3)
     og = O.load_graph(g.n, g.rowptr, g.dst, w, O.IC)
