@@ -318,6 +318,8 @@ def run_ours(args):
         "data": "synthetic (seeded R-MAT, no dataset)",
         "config": config_dict(args, g, world),
         "gteps_width": widths / (total_ms / 1e3) / 1e9,
+        "gteps_examined": sum(prof_ic[f"pass{i}_examined"] + prof_lt[f"pass{i}_examined"]
+                              for i in (1, 2, 3)) / (total_ms / 1e3) / 1e9,
         "tim_plus_ms": {"IC": statistics.mean(s["ms_total"] for s in per_model[tim.TIM_IC]),
                         "LT": statistics.mean(s["ms_total"] for s in per_model[tim.TIM_LT])},
         "phases_ms_IC": {k: ic[k] for k in ("ms_kpt", "ms_refine", "ms_select_sample",
@@ -350,14 +352,12 @@ def run_ours(args):
 
 
 def sampler_bytes(p: dict, i: int) -> float:
-    """Algorithmic bytes of IC sampler pass i: 4 B threshold per in-edge whose own
-    threshold must be read (in-lists without one shared threshold; a shared threshold
-    is one 8 B word per member), 4 B source per live in-edge, 16 B of in-CSR offsets
-    and 8 B shared-threshold word per member, 8 B emitted per member (node and set id),
-    20 B of per-set records. In-edges that no coin touches (geometric skipping) move
-    no bytes."""
-    return (4.0 * p[f"pass{i}_examined"] + 4.0 * p[f"pass{i}_live"] +
-            32.0 * p[f"pass{i}_members"] + 20.0 * p[f"pass{i}_sets"])
+    """Algorithmic bytes of IC sampler pass i, per RR set R: 8 (|R| + 1) B of in-CSR
+    offsets, 8 B (source and threshold) per examined in-edge, 4 |R| B emitted, 8 B of
+    set offsets. Examined in-edges: all in-edges of lists outside the geometric-skip
+    rule plus the live ones the rule finds (in-edges it skips are not touched)."""
+    return (8.0 * (p[f"pass{i}_members"] + p[f"pass{i}_sets"]) + 8.0 * p[f"pass{i}_examined"]
+            + 4.0 * p[f"pass{i}_members"] + 8.0 * p[f"pass{i}_sets"])
 
 
 # --------------------------------------------------------- the CPU oracle arm

@@ -144,6 +144,25 @@ __global__ void uniform_thr_kernel(const uint64_t* __restrict__ rowptr, int64_t 
     }
 }
 
+// LT: do all in-edges of v carry the same t = floor(b(e) 2^32) < 2^32? Then the
+// triggering pick of Section 6 is a division (see lt_pick in sample.cu). One warp per
+// node; low word t, bit 32 set when shared (empty in-lists get 0).
+__global__ void lt_uniform_kernel(const uint64_t* __restrict__ rowptr, int64_t n,
+                                  const unsigned long long* __restrict__ lt_t,
+                                  unsigned long long* __restrict__ node_thr) {
+    const int lane = threadIdx.x & 31;
+    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = warp; v < n; v += nwarps) {
+        const uint64_t a = rowptr[v], b = rowptr[v + 1];
+        const unsigned long long t0 = b > a ? lt_t[a] : 0ull;
+        bool same = b > a && t0 <= 0xFFFFFFFFull;
+        for (uint64_t j = a + lane; j < b && same; j += 32) same = lt_t[j] == t0;
+        same = __all_sync(0xffffffffu, same);
+        if (lane == 0) node_thr[v] = same ? ((1ull << 32) | t0) : 0ull;
+    }
+}
+
 }  // namespace
 
 int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
@@ -210,12 +229,21 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
                 ctx->launches++;
             }
         }
+        if ((rc = tim_ensure(ctx, ctx->node_thr, (size_t)(n + 1) * 8))) break;
         if (model == TIM_IC) {
-            if ((rc = tim_ensure(ctx, ctx->node_thr, (size_t)(n + 1) * 8))) break;
             uniform_thr_kernel<<<G, T, 0, ctx->stream>>>(
                 (const uint64_t*)ctx->rowptr.p, n, (const uint32_t*)ctx->thr.p,
                 (unsigned long long*)ctx->node_thr.p);
             ctx->launches++;
+        } else if (m > 0) {
+            lt_uniform_kernel<<<G, T, 0, ctx->stream>>>(
+                (const uint64_t*)ctx->rowptr.p, n, (const unsigned long long*)lt_t.p,
+                (unsigned long long*)ctx->node_thr.p);
+            ctx->launches++;
+        } else {
+            if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(ctx->node_thr.p, 0, (size_t)(n + 1) * 8,
+                                                          ctx->stream), "memset")))
+                break;
         }
         if ((rc = tim_cuda_check(ctx, cudaGetLastError(), "graph kernels"))) break;
         if ((rc = tim_read_scalars(ctx))) break;

@@ -145,6 +145,32 @@ __device__ __forceinline__ uint64_t warp_lt_search(const uint32_t* __restrict__ 
     return b ? lo + (uint64_t)(__ffs(b) - 1) : hi;
 }
 
+// LT triggering pick when all in-edges of v carry the same t = floor(b 2^32) (per-node
+// word nt: bit 32 set, low word t): the cumulative thresholds are C_j = min((j + 1) t,
+// 2^32 - 1), so the first j with x < C_j is floor(x / t) when that is below d and
+// x < 2^32 - 1 (C never exceeds 2^32 - 1), and there is none otherwise -- the same
+// in-edge as the search over C. Returns the in-CSR position, or end for none.
+__device__ __forceinline__ uint64_t lt_uniform_pick(unsigned long long nt, uint64_t beg,
+                                                    uint64_t end, uint32_t x) {
+    const uint32_t t = (uint32_t)nt;
+    if (t == 0u || x == 0xFFFFFFFFu) return end;
+    const uint64_t q = x / t;
+    return q < end - beg ? beg + q : end;
+}
+
+// First position j in [lo, hi) with thr[j] > x, by one thread.
+__device__ __forceinline__ uint64_t lane_lt_search(const uint32_t* __restrict__ thr, uint64_t lo,
+                                                   uint64_t hi, uint32_t x) {
+    for (int it = 0; it < 40 && lo < hi; it++) {
+        const uint64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(thr + mid) > x)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
 // ------------------------------------------------------------ tiers 1 and 2
 
 // Barrier over the T warps of a team (T = 1: the warp itself). Named barrier ids
@@ -273,8 +299,9 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
             }
             work += dx;
             width += dw;
-            // in-lists without a shared threshold read one threshold per in-edge
-            const unsigned long long dt = warp_sum_u64((nt >> 32) ? 0ull : end - beg);
+            // examined in-edges: every in-edge of a list outside the skip rule (the live
+            // ones the rule finds are added as they are found)
+            const unsigned long long dt = warp_sum_u64(skip_list ? 0ull : end - beg);
             if (wt == 0 && lane == 0) exam += dt;
             // 32-bit in-CSR positions (m < 2^32)
             const uint32_t b32 = (uint32_t)beg, e32 = (uint32_t)end;
@@ -300,6 +327,7 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                         skip_live_warp(s0, s1, K, bb, be - bb, t, lane, [&](uint32_t j) {
                             if (lane == 0) {
                                 live++;
+                                exam++;
                                 const uint32_t u = __ldg(a.src + j);
                                 const int r = set_insert<C>(hash, queue, slot, ctl, u);
                                 if (r == INS_FULL) {
@@ -403,7 +431,9 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
             if (beg == end) break;
             const uint32_t x =
                 philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32), v, TIM_TAG_LT, K).x;
-            const uint64_t j = warp_lt_search(a.thr, beg, end, x, lane);
+            const unsigned long long nt = __ldg(a.node_thr + v);
+            const uint64_t j = (nt >> 32) ? lt_uniform_pick(nt, beg, end, x)
+                                          : warp_lt_search(a.thr, beg, end, x, lane);
             if (j >= end) break;
             const uint32_t u = __ldg(a.src + j);
             int fresh = 0;
@@ -545,6 +575,193 @@ __global__ void __launch_bounds__(WARPS * 32, 4) rr_team_kernel(SampleArgs a) {
     }
 }
 
+// ------------------------------------------------- tier 1 for LT: a chain per lane
+//
+// An LT RR set is a chain (Section 4.2: each node keeps at most one live in-edge), so
+// its walk has no parallelism of its own: every thread walks one chain. The members
+// sit in the thread's column of a shared-memory array (element k at k * LT_THREADS +
+// tid, so the warp's accesses hit distinct banks); a 256-bit Bloom filter in registers
+// screens the revisit test, which scans the column only on a filter hit. Chains longer
+// than LT_LQ go to tier 2 (list1). Idle lanes claim sets together (one atomic per
+// warp) at the top of every step, and finished lanes reserve store space together, so
+// a warp keeps all 32 chains moving.
+constexpr int LT_THREADS = 128;
+constexpr int LT_LQ = 96;
+constexpr size_t LT_SMEM = (size_t)LT_LQ * LT_THREADS * sizeof(uint32_t);
+
+struct Bloom256 {
+    unsigned long long w[4];
+    __device__ void clear() { w[0] = w[1] = w[2] = w[3] = 0ull; }
+    __device__ static void bits(uint32_t u, int& b1, int& b2) {
+        const uint32_t h = u * 0x9E3779B1u;
+        b1 = (int)(h >> 24);
+        b2 = (int)((h >> 16) & 0xFFu);
+    }
+    __device__ bool test(int b) const {
+        const unsigned long long x = b < 128 ? (b < 64 ? w[0] : w[1]) : (b < 192 ? w[2] : w[3]);
+        return (x >> (b & 63)) & 1ull;
+    }
+    __device__ void set(int b) {
+        const unsigned long long m = 1ull << (b & 63);
+        if (b < 64) w[0] |= m; else if (b < 128) w[1] |= m; else if (b < 192) w[2] |= m; else w[3] |= m;
+    }
+    __device__ bool maybe(uint32_t u) const {
+        int b1, b2;
+        bits(u, b1, b2);
+        return test(b1) && test(b2);
+    }
+    __device__ void add(uint32_t u) {
+        int b1, b2;
+        bits(u, b1, b2);
+        set(b1);
+        set(b2);
+    }
+};
+
+__global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
+    extern __shared__ uint32_t lq[];
+    const int tid = threadIdx.x, lane = tid & 31;
+    uint32_t* col = lq + tid;  // member k at col[k * LT_THREADS]
+    const bool emit = a.flags & SAMPLE_EMIT, kap = a.flags & SAMPLE_KAPPA,
+               cover = a.flags & SAMPLE_COVER;
+    unsigned long long k_lo = 0, k_hi = 0, wsum = 0, cov = 0, live = 0, memb = 0;
+    bool has = false, exhausted = false;
+    uint64_t j = 0, sid = 0;
+    uint32_t v = 0;
+    int len = 0, status = 0;
+    unsigned long long width = 0;
+    Bloom256 bloom;
+    bloom.clear();
+    // bounded: every step either advances a chain (at most LT_LQ steps each) or
+    // finishes it, and every lane takes at most count sets
+    for (uint64_t guard = 0; guard < (a.count + 1) * (uint64_t)(LT_LQ + 2) + 64; guard++) {
+        // idle lanes claim the next sets, one atomic for the warp
+        const bool need = !has && !exhausted;
+        const unsigned nm = __ballot_sync(0xffffffffu, need);
+        if (nm) {
+            const int leader = __ffs(nm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(&a.ds->next_set, (unsigned long long)__popc(nm));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need) {
+                const unsigned long long mine = base + __popc(nm & ((1u << lane) - 1u));
+                if (mine < a.count) {
+                    j = mine;
+                    sid = a.sid0 + j;
+                    v = rr_root(sid, a.n, a.K);
+                    col[0] = v;
+                    len = 1;
+                    width = 0;
+                    bloom.clear();
+                    bloom.add(v);
+                    status = (cover && marked(a.seed_mark, v)) ? ST_COVERED : 0;
+                    has = true;
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, has)) break;
+        // one step of every lane's chain
+        bool fin = false, ovf = false;
+        if (has) {
+            if (status) {
+                fin = true;
+            } else {
+                const uint64_t beg = __ldg(a.rowptr + v), end = __ldg(a.rowptr + v + 1);
+                const unsigned long long nt = __ldg(a.node_thr + v);
+                width += end - beg;
+                uint64_t jj = end;
+                if (beg < end) {
+                    const uint32_t x =
+                        philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32), v, TIM_TAG_LT, a.K).x;
+                    jj = (nt >> 32) ? lt_uniform_pick(nt, beg, end, x)
+                                    : lane_lt_search(a.thr, beg, end, x);
+                }
+                if (jj >= end) {
+                    fin = true;
+                } else {
+                    const uint32_t u = __ldg(a.src + jj);
+                    live++;
+                    bool seen = false;
+                    if (bloom.maybe(u))
+                        for (int k = 0; k < len && !seen; k++) seen = col[k * LT_THREADS] == u;
+                    if (seen) {
+                        fin = true;
+                    } else if (len == LT_LQ) {
+                        fin = ovf = true;
+                    } else {
+                        col[len * LT_THREADS] = u;
+                        len++;
+                        bloom.add(u);
+                        if (cover && marked(a.seed_mark, u)) status |= ST_COVERED;
+                        v = u;
+                    }
+                }
+            }
+        }
+        if (fin && ovf) {
+            const unsigned idx = atomicAdd(&a.ds->cnt1, 1u);
+            if (idx < a.list_cap)
+                a.list1[idx] = (uint32_t)j;
+            else
+                atomicOr(&a.ds->err, TIM_DEV_ERR_OVF_LIST);
+        } else if (fin) {
+            wsum += width;
+            memb += len;
+            if (status & ST_COVERED) cov++;
+            if (kap) {
+                const unsigned long long kf = kappa_fixed(kappa_fp64(width, a.m, a.k));
+                k_lo += kf;
+                if (k_lo < kf) k_hi++;
+            }
+        }
+        // finished chains reserve their store space together
+        const bool put = emit && fin && !ovf;
+        if (__any_sync(0xffffffffu, put)) {
+            unsigned incl = put ? (unsigned)len : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const unsigned total = __shfl_sync(0xffffffffu, incl, 31);
+            unsigned long long base = 0;
+            if (lane == 0) base = atomicAdd(&a.ds->pool_used, (unsigned long long)total);
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (put) {
+                const unsigned long long st = base + incl - (unsigned)len;
+                if (st + (unsigned)len <= a.pool_cap) {
+                    for (int k = 0; k < len; k++) {
+                        a.pool[st + k] = col[k * LT_THREADS];
+                        a.pool_sid[st + k] = (uint32_t)j;
+                    }
+                    a.set_start[j] = st;
+                    a.set_len[j] = (uint32_t)len;
+                    a.set_width[j] = width;
+                } else {
+                    atomicOr(&a.ds->err, TIM_DEV_ERR_POOL);
+                }
+            }
+        }
+        if (fin) has = false;
+    }
+    live = warp_sum_u64(live);
+    wsum = warp_sum_u64(wsum);
+    memb = warp_sum_u64(memb);
+    cov = warp_sum_u64(cov);
+    if (lane == 0) {
+        if (live) atomicAdd(&a.ds->live[0], live);
+        if (wsum) {
+            atomicAdd(&a.ds->wsum, wsum);
+            atomicAdd(&a.ds->width[0], wsum);
+        }
+        if (memb) atomicAdd(&a.ds->memb[0], memb);
+        if (cov) atomicAdd(&a.ds->covered, cov);
+    }
+    if (kap && (k_lo || k_hi)) atomic_add_u128(&a.ds->ksum_lo, &a.ds->ksum_hi, k_lo, k_hi);
+}
+
 // ---------------------------------------------------------- tier 3 (LT chains)
 
 // One CTA per listed set; warp 0 walks the chain with a visited bitmap and a queue of
@@ -586,7 +803,9 @@ __global__ void __launch_bounds__(BIG_THREADS) rr_lt_chain_kernel(SampleArgs a) 
                 width += end - beg;
                 if (beg == end) break;
                 uint32_t x = draw(a, sid, v, TIM_TAG_LT).x;
-                uint64_t jj = warp_lt_search(a.thr, beg, end, x, lane);
+                const unsigned long long nt = __ldg(a.node_thr + v);
+                uint64_t jj = (nt >> 32) ? lt_uniform_pick(nt, beg, end, x)
+                                         : warp_lt_search(a.thr, beg, end, x, lane);
                 if (jj >= end) break;
                 uint32_t u = __ldg(a.src + jj);
                 int fresh = 0;
@@ -674,11 +893,17 @@ int occupancy(size_t smem) {
 }
 
 int launch_tier1(tim_ctx* ctx, const SampleArgs& a, unsigned grid, size_t smem) {
-    if (ctx->model == TIM_IC)
+    if (ctx->model == TIM_IC) {
         rr_team_kernel<TIM_IC, Tier1, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
-    else
-        rr_team_kernel<TIM_LT, Tier1, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
-    LAUNCH_CHECK(ctx, "rr_team_kernel (tier 1)");
+        LAUNCH_CHECK(ctx, "rr_team_kernel (tier 1)");
+    } else {
+        int nb = 0;
+        CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rr_lt_lane_kernel,
+                                                                    LT_THREADS, LT_SMEM));
+        const unsigned g = (unsigned)(ctx->num_sms * std::max(nb, 1));
+        rr_lt_lane_kernel<<<g, LT_THREADS, LT_SMEM, ctx->stream>>>(a);
+        LAUNCH_CHECK(ctx, "rr_lt_lane_kernel (tier 1)");
+    }
     return TIM_OK;
 }
 
