@@ -210,7 +210,7 @@ __device__ __forceinline__ uint32_t live_mask(uint4 x, uint4 t) {
 // Follow the live in-edges of group g given their mask: insert each source. Returns
 // bit 0 if the set overflowed, bit 1 if it met the seed set.
 template <class C, class A>
-__device__ __noinline__ int follow_live(const A& a, uint32_t g, uint32_t mask,
+__device__ __forceinline__ int follow_live(const A& a, uint32_t g, uint32_t mask,
                                         uint32_t* hash, uint32_t* queue, uint16_t* slot,
                                         int* ctl) {
     int f = 0;
@@ -287,11 +287,12 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                 nt = __ldg(a.node_thr + v);
             }
             const bool skip_list = lane < nb && tim_skip_rule(nt, end - beg);
-            const unsigned long long dw = warp_sum_u64(end - beg);
+            // the frontier's nodes are distinct, so these sums stay below m < 2^32
+            const unsigned long long dw = __reduce_add_sync(0xffffffffu, (unsigned)(end - beg));
             // the budget counts in-edges that take a coin; a skipped list counts as at
             // most 64
-            const unsigned long long dx =
-                warp_sum_u64(skip_list ? min(end - beg, (uint64_t)64) : end - beg);
+            const unsigned long long dx = __reduce_add_sync(
+                0xffffffffu, (unsigned)(skip_list ? min(end - beg, (uint64_t)64) : end - beg));
             if (work + dx > budget) {
                 // too heavy for this tier: list the set for the next one
                 if (wt == 0 && lane == 0) ctl[1] |= ST_OVERFLOW;
@@ -301,7 +302,8 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
             width += dw;
             // examined in-edges: every in-edge of a list outside the skip rule (the live
             // ones the rule finds are added as they are found)
-            const unsigned long long dt = warp_sum_u64(skip_list ? 0ull : end - beg);
+            const unsigned long long dt =
+                __reduce_add_sync(0xffffffffu, (unsigned)(skip_list ? 0ull : end - beg));
             if (wt == 0 && lane == 0) exam += dt;
             // 32-bit in-CSR positions (m < 2^32)
             const uint32_t b32 = (uint32_t)beg, e32 = (uint32_t)end;
@@ -458,8 +460,10 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
 // TIER 1: teams of one warp, storage in shared memory, every set index of [0, count),
 // in-edge budget (IC); listed sets go to list1. TIER 2: teams of T warps, storage in
 // the global arena, the sets of list1, no budget; listed sets go to list2.
+// Tier 1 is bound by integer arithmetic (coins), tier 2 by latency: tier 2 trades
+// registers for resident warps.
 template <int MODEL, class C, int TIER, int T>
-__global__ void __launch_bounds__(WARPS * 32, 4) rr_team_kernel(SampleArgs a) {
+__global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(SampleArgs a) {
     extern __shared__ uint32_t smem[];
     __shared__ unsigned long long s_claim[WARPS];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
