@@ -88,6 +88,7 @@ struct tim_ctx {
     DevBuf ovf_list2;   // uint32 set index
     DevBuf arena;       // tier-2 per-warp hash + queue
     bool arena_clean = false;
+    DevBuf lt_col;      // tier-1 LT: member columns, one per thread
     DevBuf big_bitmap;  // tier-3 LT: uint32[slots * words]
     DevBuf big_queue;   // tier-3 LT: uint32[slots * n]
     bool big_bitmap_clean = false;

@@ -76,6 +76,7 @@ struct SampleArgs {
     uint64_t big_words;
     unsigned long long width_budget;  // tier 1 IC: in-edges one warp may examine per set
     int chunk;                        // sets claimed per work-counter increment
+    uint32_t* lt_col;                 // tier 1 LT: per-thread member columns
 };
 
 __device__ __forceinline__ uint4 draw(const SampleArgs& a, uint64_t sid, uint32_t elem,
@@ -582,50 +583,37 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
 // ------------------------------------------------- tier 1 for LT: a chain per lane
 //
 // An LT RR set is a chain (Section 4.2: each node keeps at most one live in-edge), so
-// its walk has no parallelism of its own: every thread walks one chain. The members
-// sit in the thread's column of a shared-memory array (element k at k * LT_THREADS +
-// tid, so the warp's accesses hit distinct banks); a 256-bit Bloom filter in registers
-// screens the revisit test, which scans the column only on a filter hit. Chains longer
-// than LT_LQ go to tier 2 (list1). Idle lanes claim sets together (one atomic per
-// warp) at the top of every step, and finished lanes reserve store space together, so
-// a warp keeps all 32 chains moving.
+// its walk has no parallelism of its own: every thread walks one chain. The members go
+// to the thread's column of a global array (member k at k * lanes + thread, so a warp's
+// stores are contiguous); a 1024-bit Bloom filter per thread in shared memory screens
+// the revisit test, which scans the column only on a filter hit. Chains longer than
+// LT_CAP go to tier 2 (list1). Idle lanes claim sets together (one atomic per warp) at
+// the top of every step, and finished lanes reserve store space together, so a warp
+// keeps all 32 chains moving.
 constexpr int LT_THREADS = 128;
-constexpr int LT_LQ = 96;
-constexpr size_t LT_SMEM = (size_t)LT_LQ * LT_THREADS * sizeof(uint32_t);
+constexpr int LT_CAP = 1024;                 // members per chain in this pass
+constexpr int LT_BLOOM_WORDS = 32;           // 1024 bits per thread
+constexpr size_t LT_SMEM = (size_t)LT_BLOOM_WORDS * LT_THREADS * sizeof(uint32_t);
 
-struct Bloom256 {
-    unsigned long long w[4];
-    __device__ void clear() { w[0] = w[1] = w[2] = w[3] = 0ull; }
-    __device__ static void bits(uint32_t u, int& b1, int& b2) {
-        const uint32_t h = u * 0x9E3779B1u;
-        b1 = (int)(h >> 24);
-        b2 = (int)((h >> 16) & 0xFFu);
-    }
-    __device__ bool test(int b) const {
-        const unsigned long long x = b < 128 ? (b < 64 ? w[0] : w[1]) : (b < 192 ? w[2] : w[3]);
-        return (x >> (b & 63)) & 1ull;
-    }
-    __device__ void set(int b) {
-        const unsigned long long m = 1ull << (b & 63);
-        if (b < 64) w[0] |= m; else if (b < 128) w[1] |= m; else if (b < 192) w[2] |= m; else w[3] |= m;
-    }
-    __device__ bool maybe(uint32_t u) const {
-        int b1, b2;
-        bits(u, b1, b2);
-        return test(b1) && test(b2);
-    }
-    __device__ void add(uint32_t u) {
-        int b1, b2;
-        bits(u, b1, b2);
-        set(b1);
-        set(b2);
-    }
-};
+__device__ __forceinline__ void lt_bloom_bits(uint32_t u, uint32_t& w1, uint32_t& m1, uint32_t& w2,
+                                              uint32_t& m2) {
+    const uint32_t h = u * 0x9E3779B1u;
+    const uint32_t b1 = h >> 22, b2 = (h >> 12) & 1023u;
+    w1 = b1 >> 5;
+    m1 = 1u << (b1 & 31);
+    w2 = b2 >> 5;
+    m2 = 1u << (b2 & 31);
+}
 
 __global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
-    extern __shared__ uint32_t lq[];
+    extern __shared__ uint32_t bloom_all[];
     const int tid = threadIdx.x, lane = tid & 31;
-    uint32_t* col = lq + tid;  // member k at col[k * LT_THREADS]
+    uint32_t* bloom = bloom_all + tid;  // word w at bloom[w * LT_THREADS]
+    for (int w = 0; w < LT_BLOOM_WORDS; w++) bloom[w * LT_THREADS] = 0u;
+    const uint64_t lanes = (uint64_t)gridDim.x * LT_THREADS;
+    // member k of lane l of this warp's columns: wcol[k * lanes + l]
+    uint32_t* wcol = a.lt_col + (uint64_t)blockIdx.x * LT_THREADS + (tid & ~31);
+    uint32_t* col = wcol + lane;
     const bool emit = a.flags & SAMPLE_EMIT, kap = a.flags & SAMPLE_KAPPA,
                cover = a.flags & SAMPLE_COVER;
     unsigned long long k_lo = 0, k_hi = 0, wsum = 0, cov = 0, live = 0, memb = 0;
@@ -634,11 +622,10 @@ __global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
     uint32_t v = 0;
     int len = 0, status = 0;
     unsigned long long width = 0;
-    Bloom256 bloom;
-    bloom.clear();
-    // bounded: every step either advances a chain (at most LT_LQ steps each) or
-    // finishes it, and every lane takes at most count sets
-    for (uint64_t guard = 0; guard < (a.count + 1) * (uint64_t)(LT_LQ + 2) + 64; guard++) {
+    // bounded: every step either advances a chain (at most LT_CAP steps each) or
+    // finishes it, and the lanes take at most count sets between them
+    const uint64_t steps = (a.count + 1) * (uint64_t)(LT_CAP + 2) + 64;
+    for (uint64_t guard = 0; guard < steps; guard++) {
         // idle lanes claim the next sets, one atomic for the warp
         const bool need = !has && !exhausted;
         const unsigned nm = __ballot_sync(0xffffffffu, need);
@@ -656,8 +643,10 @@ __global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
                     col[0] = v;
                     len = 1;
                     width = 0;
-                    bloom.clear();
-                    bloom.add(v);
+                    uint32_t w1, m1, w2, m2;
+                    lt_bloom_bits(v, w1, m1, w2, m2);
+                    bloom[w1 * LT_THREADS] |= m1;
+                    bloom[w2 * LT_THREADS] |= m2;
                     status = (cover && marked(a.seed_mark, v)) ? ST_COVERED : 0;
                     has = true;
                 } else {
@@ -666,8 +655,9 @@ __global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
             }
         }
         if (!__any_sync(0xffffffffu, has)) break;
-        // one step of every lane's chain
-        bool fin = false, ovf = false;
+        // one step of every lane's chain: the next member u, if any
+        bool fin = false, cand = false;
+        uint32_t u = 0;
         if (has) {
             if (status) {
                 fin = true;
@@ -685,23 +675,42 @@ __global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
                 if (jj >= end) {
                     fin = true;
                 } else {
-                    const uint32_t u = __ldg(a.src + jj);
+                    u = __ldg(a.src + jj);
                     live++;
-                    bool seen = false;
-                    if (bloom.maybe(u))
-                        for (int k = 0; k < len && !seen; k++) seen = col[k * LT_THREADS] == u;
-                    if (seen) {
-                        fin = true;
-                    } else if (len == LT_LQ) {
-                        fin = ovf = true;
-                    } else {
-                        col[len * LT_THREADS] = u;
-                        len++;
-                        bloom.add(u);
-                        if (cover && marked(a.seed_mark, u)) status |= ST_COVERED;
-                        v = u;
-                    }
+                    cand = true;
                 }
+            }
+        }
+        // revisit test: the filter first; on a hit the whole warp scans that column
+        uint32_t w1 = 0, m1 = 0, w2 = 0, m2 = 0;
+        bool hit = false;
+        if (cand) {
+            lt_bloom_bits(u, w1, m1, w2, m2);
+            hit = (bloom[w1 * LT_THREADS] & m1) && (bloom[w2 * LT_THREADS] & m2);
+        }
+        bool seen = false;
+        for (unsigned hm = __ballot_sync(0xffffffffu, hit); hm; hm &= hm - 1) {
+            const int l = __ffs(hm) - 1;
+            const uint32_t ul = __shfl_sync(0xffffffffu, u, l);
+            const int ll = __shfl_sync(0xffffffffu, len, l);
+            bool f = false;
+            for (int k = lane; k < ll; k += 32) f |= wcol[(uint64_t)k * lanes + l] == ul;
+            f = __any_sync(0xffffffffu, f);
+            if (lane == l) seen = f;
+        }
+        bool ovf = false;
+        if (cand) {
+            if (seen) {
+                fin = true;
+            } else if (len == LT_CAP) {
+                fin = ovf = true;
+            } else {
+                col[(uint64_t)len * lanes] = u;
+                len++;
+                bloom[w1 * LT_THREADS] |= m1;
+                bloom[w2 * LT_THREADS] |= m2;
+                if (cover && marked(a.seed_mark, u)) status |= ST_COVERED;
+                v = u;
             }
         }
         if (fin && ovf) {
@@ -720,9 +729,11 @@ __global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
                 if (k_lo < kf) k_hi++;
             }
         }
-        // finished chains reserve their store space together
+        // finished chains reserve their store space together and the warp copies each
+        // one's column with all its lanes
         const bool put = emit && fin && !ovf;
-        if (__any_sync(0xffffffffu, put)) {
+        const unsigned pm = __ballot_sync(0xffffffffu, put);
+        if (pm) {
             unsigned incl = put ? (unsigned)len : 0u;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -733,13 +744,10 @@ __global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
             unsigned long long base = 0;
             if (lane == 0) base = atomicAdd(&a.ds->pool_used, (unsigned long long)total);
             base = __shfl_sync(0xffffffffu, base, 0);
+            const unsigned long long st = base + incl - (put ? (unsigned)len : 0u);
+            const bool fits = base + total <= a.pool_cap;
             if (put) {
-                const unsigned long long st = base + incl - (unsigned)len;
-                if (st + (unsigned)len <= a.pool_cap) {
-                    for (int k = 0; k < len; k++) {
-                        a.pool[st + k] = col[k * LT_THREADS];
-                        a.pool_sid[st + k] = (uint32_t)j;
-                    }
+                if (fits) {
                     a.set_start[j] = st;
                     a.set_len[j] = (uint32_t)len;
                     a.set_width[j] = width;
@@ -747,8 +755,23 @@ __global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
                     atomicOr(&a.ds->err, TIM_DEV_ERR_POOL);
                 }
             }
+            if (fits) {
+                for (unsigned m = pm; m; m &= m - 1) {
+                    const int l = __ffs(m) - 1;
+                    const unsigned long long sl = __shfl_sync(0xffffffffu, st, l);
+                    const int ll = __shfl_sync(0xffffffffu, len, l);
+                    const uint32_t jl = (uint32_t)__shfl_sync(0xffffffffu, j, l);
+                    for (int k = lane; k < ll; k += 32) {
+                        a.pool[sl + k] = wcol[(uint64_t)k * lanes + l];
+                        a.pool_sid[sl + k] = jl;
+                    }
+                }
+            }
         }
-        if (fin) has = false;
+        if (fin) {
+            for (int w = 0; w < LT_BLOOM_WORDS; w++) bloom[w * LT_THREADS] = 0u;
+            has = false;
+        }
     }
     live = warp_sum_u64(live);
     wsum = warp_sum_u64(wsum);
@@ -905,7 +928,11 @@ int launch_tier1(tim_ctx* ctx, const SampleArgs& a, unsigned grid, size_t smem) 
         CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rr_lt_lane_kernel,
                                                                     LT_THREADS, LT_SMEM));
         const unsigned g = (unsigned)(ctx->num_sms * std::max(nb, 1));
-        rr_lt_lane_kernel<<<g, LT_THREADS, LT_SMEM, ctx->stream>>>(a);
+        SampleArgs b = a;
+        TIM_TRY(tim_ensure(ctx, ctx->lt_col,
+                           (size_t)g * LT_THREADS * LT_CAP * sizeof(uint32_t)));
+        b.lt_col = (uint32_t*)ctx->lt_col.p;
+        rr_lt_lane_kernel<<<g, LT_THREADS, LT_SMEM, ctx->stream>>>(b);
         LAUNCH_CHECK(ctx, "rr_lt_lane_kernel (tier 1)");
     }
     return TIM_OK;
