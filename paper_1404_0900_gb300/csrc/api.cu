@@ -781,7 +781,7 @@ static int run_common(tim_ctx* ctx, bool plus, int k, double eps, double ell, ui
     s.sets_total = ctx->kpt_sets + s.theta_prime + theta;
     s.members_select = res.members;
     s.width_select = res.wsum;
-    s.width_total = ctx->kpt_width + (plus ? ctx->ref_width : 0) + res.wsum;
+    s.width_total = ctx->kpt_width + res.wsum;
     s.ms_kpt = elapsed_ms(ctx, 0, 1);
     s.ms_refine = elapsed_ms(ctx, 1, 2);
     s.ms_select_sample = elapsed_ms(ctx, 2, 3);
@@ -871,7 +871,7 @@ static int run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_mlp* ml
     }
     cudaEventRecord(ev[1], owner->stream);
     std::vector<double> kpt_plus(kpt), kpt_prime(nq, 0.0), eps_p(nq, 0.0);
-    std::vector<uint64_t> theta_p(nq, 0), cov_p(nq, 0), width_p(nq, 0);
+    std::vector<uint64_t> theta_p(nq, 0), cov_p(nq, 0);
     std::vector<MultiQuery> mq;
     if (plus) {
         // Algorithm 3: greedy on every query's R', then theta' fresh sets each
@@ -895,7 +895,6 @@ static int run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_mlp* ml
         TIM_TRY(tim_sample_multi(owner, mq.data(), nq, seed));
         for (int i = 0; i < nq; i++) {
             cov_p[i] = mq[i].res.covered;
-            width_p[i] = mq[i].res.wsum;
             const double f = (double)cov_p[i] / (double)theta_p[i];
             kpt_prime[i] = f * (double)qs[i].ctx->n / (1.0 + eps_p[i]);
             kpt_plus[i] = std::max(kpt_prime[i], kpt[i]);
@@ -946,7 +945,7 @@ static int run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_mlp* ml
         s.sets_total = sets[i] + theta_p[i] + theta[i];
         s.members_select = mq[i].res.members;
         s.width_select = mq[i].res.wsum;
-        s.width_total = width[i] + width_p[i] + mq[i].res.wsum;
+        s.width_total = width[i] + mq[i].res.wsum;
         qs[i].covered_fraction = theta[i] ? (double)cov[i] / (double)theta[i] : 0.0;
         sets_all += s.sets_total;
         // keep the per-context state consistent with a single run
