@@ -605,6 +605,37 @@ __device__ __forceinline__ void lt_bloom_bits(uint32_t u, uint32_t& w1, uint32_t
     m2 = 1u << (b2 & 31);
 }
 
+__device__ __forceinline__ void lane_bloom_add(uint32_t* bloom, uint32_t u) {
+    uint32_t w1, m1, w2, m2;
+    lt_bloom_bits(u, w1, m1, w2, m2);
+    bloom[w1 * LT_THREADS] |= m1;
+    bloom[w2 * LT_THREADS] |= m2;
+}
+
+__device__ __forceinline__ bool lane_bloom_test(const uint32_t* bloom, uint32_t u) {
+    uint32_t w1, m1, w2, m2;
+    lt_bloom_bits(u, w1, m1, w2, m2);
+    return (bloom[w1 * LT_THREADS] & m1) && (bloom[w2 * LT_THREADS] & m2);
+}
+
+// Revisit test of the lanes with hit set: does lane l's column (the warp's columns
+// start at wcol; member k of lane l at wcol[k * lanes + l]) hold u among its first len
+// members? All lanes scan each such column together. Warp-collective.
+__device__ __forceinline__ bool lane_cols_contain(const uint32_t* wcol, uint64_t lanes, int lane,
+                                                  bool hit, uint32_t u, int len) {
+    bool seen = false;
+    for (unsigned hm = __ballot_sync(0xffffffffu, hit); hm; hm &= hm - 1) {
+        const int l = __ffs(hm) - 1;
+        const uint32_t ul = __shfl_sync(0xffffffffu, u, l);
+        const int ll = __shfl_sync(0xffffffffu, len, l);
+        bool f = false;
+        for (int k = lane; k < ll; k += 32) f |= wcol[(uint64_t)k * lanes + l] == ul;
+        f = __any_sync(0xffffffffu, f);
+        if (lane == l) seen = f;
+    }
+    return seen;
+}
+
 __global__ void __launch_bounds__(LT_THREADS) rr_lt_lane_kernel(SampleArgs a) {
     extern __shared__ uint32_t bloom_all[];
     const int tid = threadIdx.x, lane = tid & 31;
@@ -1168,6 +1199,205 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
     flush_acc<TIER>(ma.q, cur_q, acc, lane);
 }
 
+// Tier 1 of the LT queries of a multi-query launch: one chain per thread as in
+// rr_lt_lane_kernel, over the set index space of the LT queries (lt_prefix; IC queries
+// have no sets there). Each thread keeps its query's totals and flushes them when it
+// moves to another query; store space is reserved per set; chains longer than LT_CAP
+// join the tier-2 list of the launch.
+__global__ void __launch_bounds__(LT_THREADS)
+rr_lt_lane_multi_kernel(MultiArgs ma, const unsigned long long* lt_prefix,
+                        unsigned long long* lt_next, uint32_t* lt_col) {
+    extern __shared__ uint32_t bloom_all[];
+    __shared__ unsigned long long s_prefix[MAXQ + 1];
+    const int tid = threadIdx.x, lane = tid & 31;
+    for (int i = tid; i <= ma.nq; i += blockDim.x) s_prefix[i] = lt_prefix[i];
+    uint32_t* bloom = bloom_all + tid;
+    for (int w = 0; w < LT_BLOOM_WORDS; w++) bloom[w * LT_THREADS] = 0u;
+    __syncthreads();
+    const uint64_t total = s_prefix[ma.nq];
+    const uint64_t lanes = (uint64_t)gridDim.x * LT_THREADS;
+    uint32_t* wcol = lt_col + (uint64_t)blockIdx.x * LT_THREADS + (tid & ~31);
+    uint32_t* col = wcol + lane;
+    QAcc acc{0, 0, 0, 0, 0, 0, 0};
+    int cur_q = -1;
+    bool has = false, exhausted = false;
+    int qi = -1, flags = 0, kk = 0, len = 0, status = 0;
+    uint64_t j = 0, sid = 0, n = 0, m = 0;
+    const uint64_t* rowptr = nullptr;
+    const uint32_t* src = nullptr;
+    const uint32_t* thr = nullptr;
+    const unsigned long long* node_thr = nullptr;
+    const uint32_t* seed_mark = nullptr;
+    uint32_t v = 0;
+    unsigned long long width = 0;
+    const uint64_t steps = (total + 1) * (uint64_t)(LT_CAP + 2) + 64;
+    for (uint64_t guard = 0; guard < steps; guard++) {
+        const bool need = !has && !exhausted;
+        const unsigned nm = __ballot_sync(0xffffffffu, need);
+        if (nm) {
+            const int leader = __ffs(nm) - 1;
+            unsigned long long base = 0;
+            if (lane == leader) base = atomicAdd(lt_next, (unsigned long long)__popc(nm));
+            base = __shfl_sync(0xffffffffu, base, leader);
+            if (need) {
+                const unsigned long long mine = base + __popc(nm & ((1u << lane) - 1u));
+                if (mine < total) {
+                    int lo = 0, hi = ma.nq;  // s_prefix[lo] <= mine < s_prefix[hi]
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_prefix[mid] <= mine)
+                            lo = mid;
+                        else
+                            hi = mid;
+                    }
+                    if (lo != cur_q) {
+                        if (cur_q >= 0) {
+                            DevScalars* ds = ma.q[cur_q].ds;
+                            if (acc.k_lo || acc.k_hi)
+                                atomic_add_u128(&ds->ksum_lo, &ds->ksum_hi, acc.k_lo, acc.k_hi);
+                            if (acc.wsum) {
+                                atomicAdd(&ds->wsum, acc.wsum);
+                                atomicAdd(&ds->width[0], acc.wsum);
+                            }
+                            if (acc.cov) atomicAdd(&ds->covered, acc.cov);
+                            if (acc.live) atomicAdd(&ds->live[0], acc.live);
+                            if (acc.memb) atomicAdd(&ds->memb[0], acc.memb);
+                        }
+                        acc = QAcc{0, 0, 0, 0, 0, 0, 0};
+                        cur_q = lo;
+                        const QueryDesc& d = ma.q[lo];
+                        rowptr = d.rowptr;
+                        src = d.src;
+                        thr = d.thr;
+                        node_thr = d.node_thr;
+                        seed_mark = d.seed_mark;
+                        n = d.n;
+                        m = d.m;
+                        flags = d.flags;
+                        kk = d.k;
+                    }
+                    qi = lo;
+                    j = mine - s_prefix[lo];
+                    sid = ma.q[lo].sid0 + j;
+                    v = rr_root(sid, n, ma.K);
+                    col[0] = v;
+                    len = 1;
+                    width = 0;
+                    lane_bloom_add(bloom, v);
+                    status = ((flags & SAMPLE_COVER) && marked(seed_mark, v)) ? ST_COVERED : 0;
+                    has = true;
+                } else {
+                    exhausted = true;
+                }
+            }
+        }
+        if (!__any_sync(0xffffffffu, has)) break;
+        bool fin = false, cand = false;
+        uint32_t u = 0;
+        if (has) {
+            if (status) {
+                fin = true;
+            } else {
+                const uint64_t beg = __ldg(rowptr + v), end = __ldg(rowptr + v + 1);
+                const unsigned long long nt = __ldg(node_thr + v);
+                width += end - beg;
+                uint64_t jj = end;
+                if (beg < end) {
+                    const uint32_t x =
+                        philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32), v, TIM_TAG_LT, ma.K).x;
+                    jj = (nt >> 32) ? lt_uniform_pick(nt, beg, end, x)
+                                    : lane_lt_search(thr, beg, end, x);
+                }
+                if (jj >= end) {
+                    fin = true;
+                } else {
+                    u = __ldg(src + jj);
+                    acc.live++;
+                    cand = true;
+                }
+            }
+        }
+        const bool seen =
+            lane_cols_contain(wcol, lanes, lane, cand && lane_bloom_test(bloom, u), u, len);
+        bool ovf = false;
+        if (cand) {
+            if (seen) {
+                fin = true;
+            } else if (len == LT_CAP) {
+                fin = ovf = true;
+            } else {
+                col[(uint64_t)len * lanes] = u;
+                len++;
+                lane_bloom_add(bloom, u);
+                if ((flags & SAMPLE_COVER) && marked(seed_mark, u)) status |= ST_COVERED;
+                v = u;
+            }
+        }
+        bool put = false;
+        unsigned long long st = 0;
+        uint32_t* pool = nullptr;
+        uint32_t* pool_sid = nullptr;
+        if (fin && ovf) {
+            const unsigned idx = atomicAdd(&ma.cnt[0], 1u);
+            if (idx < ma.list_cap)
+                ma.list1[idx] = make_uint2((uint32_t)qi, (uint32_t)j);
+            else
+                atomicOr(ma.err, TIM_DEV_ERR_OVF_LIST);
+        } else if (fin) {
+            acc.wsum += width;
+            acc.memb += len;
+            if (status & ST_COVERED) acc.cov++;
+            if (flags & SAMPLE_KAPPA) {
+                const unsigned long long kf = kappa_fixed(kappa_fp64(width, m, kk));
+                acc.k_lo += kf;
+                if (acc.k_lo < kf) acc.k_hi++;
+            }
+            if (flags & SAMPLE_EMIT) {
+                const QueryDesc& d = ma.q[qi];
+                st = atomicAdd(&d.ds->pool_used, (unsigned long long)len);
+                if (st + (unsigned)len <= d.pool_cap) {
+                    put = true;
+                    pool = d.pool;
+                    pool_sid = d.pool_sid;
+                    d.set_start[j] = st;
+                    d.set_len[j] = (uint32_t)len;
+                    d.set_width[j] = width;
+                } else {
+                    atomicOr(&d.ds->err, TIM_DEV_ERR_POOL);
+                }
+            }
+        }
+        // the warp copies each stored chain's column with all its lanes
+        for (unsigned pm = __ballot_sync(0xffffffffu, put); pm; pm &= pm - 1) {
+            const int l = __ffs(pm) - 1;
+            const unsigned long long sl = __shfl_sync(0xffffffffu, st, l);
+            const int ll = __shfl_sync(0xffffffffu, len, l);
+            const uint32_t jl = (uint32_t)__shfl_sync(0xffffffffu, (unsigned long long)j, l);
+            uint32_t* pl = (uint32_t*)__shfl_sync(0xffffffffu, (unsigned long long)pool, l);
+            uint32_t* psl = (uint32_t*)__shfl_sync(0xffffffffu, (unsigned long long)pool_sid, l);
+            for (int k = lane; k < ll; k += 32) {
+                pl[sl + k] = wcol[(uint64_t)k * lanes + l];
+                psl[sl + k] = jl;
+            }
+        }
+        if (fin) {
+            for (int w = 0; w < LT_BLOOM_WORDS; w++) bloom[w * LT_THREADS] = 0u;
+            has = false;
+        }
+    }
+    if (cur_q >= 0) {
+        DevScalars* ds = ma.q[cur_q].ds;
+        if (acc.k_lo || acc.k_hi) atomic_add_u128(&ds->ksum_lo, &ds->ksum_hi, acc.k_lo, acc.k_hi);
+        if (acc.wsum) {
+            atomicAdd(&ds->wsum, acc.wsum);
+            atomicAdd(&ds->width[0], acc.wsum);
+        }
+        if (acc.cov) atomicAdd(&ds->covered, acc.cov);
+        if (acc.live) atomicAdd(&ds->live[0], acc.live);
+        if (acc.memb) atomicAdd(&ds->memb[0], acc.memb);
+    }
+}
+
 int launch_multi(tim_ctx* owner, const MultiArgs& ma, int tier, int T, unsigned grid,
                  size_t smem) {
     if (tier == 1) {
@@ -1459,15 +1689,22 @@ int run_tier3(tim_ctx* ctx, cudaStream_t stream, const SampleRequest& req, DevSc
 int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
     if (nq <= 0) return TIM_OK;
     if (nq > MAXQ) return tim_fail(owner, TIM_ERR_ARG, "too many queries in one launch");
-    std::vector<unsigned long long> prefix(nq + 1, 0);
-    uint64_t total = 0;
+    // IC queries are sampled by rr_multi_kernel over their own set index space, LT
+    // queries by rr_lt_lane_multi_kernel over theirs
+    std::vector<unsigned long long> prefix(nq + 1, 0), prefix_lt(nq + 1, 0);
+    uint64_t total = 0, total_ic = 0, total_lt = 0;
     for (int i = 0; i < nq; i++) {
         tim_ctx* c = qs[i].ctx;
         if (!c || !c->have_graph) return tim_fail(owner, TIM_ERR_STATE, "query without a graph");
         if (c->device != owner->device) return tim_fail(owner, TIM_ERR_ARG, "queries on several devices");
         const uint64_t count = qs[i].req.count;
         if (count > 0xFFFFFFF0ull) return tim_fail(owner, TIM_ERR_ARG, "too many RR sets in one call");
-        prefix[i] = total;
+        prefix[i] = total_ic;
+        prefix_lt[i] = total_lt;
+        if (c->model == TIM_LT)
+            total_lt += count;
+        else
+            total_ic += count;
         total += count;
         if (qs[i].req.flags & SAMPLE_EMIT) {
             uint64_t cap_sets = 1024;
@@ -1482,13 +1719,16 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
             }
         }
     }
-    prefix[nq] = total;
+    prefix[nq] = total_ic;
+    prefix_lt[nq] = total_lt;
     if (total > 0xFFFFFFF0ull) return tim_fail(owner, TIM_ERR_ARG, "too many RR sets in one launch");
-    // owner scratch: descriptors | prefix | per-query scalars | next[2] | cnt[2] | err
+    // owner scratch: descriptors | IC prefix | per-query scalars | next[2] | cnt[2] | err |
+    // LT work counter | LT prefix
     const size_t off_prefix = ((size_t)nq * sizeof(QueryDesc) + 255) & ~size_t(255);
     const size_t off_scal = (off_prefix + (size_t)(nq + 1) * 8 + 255) & ~size_t(255);
     const size_t off_ctr = (off_scal + (size_t)nq * sizeof(DevScalars) + 255) & ~size_t(255);
-    const size_t batch_bytes = off_ctr + 64;
+    const size_t off_prefix_lt = off_ctr + 64;
+    const size_t batch_bytes = off_prefix_lt + (size_t)(nq + 1) * 8;
     TIM_TRY(tim_ensure(owner, owner->batch, batch_bytes));
     char* bb = (char*)owner->batch.p;
     QueryDesc* d_desc = (QueryDesc*)bb;
@@ -1497,6 +1737,17 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
     unsigned long long* d_next = (unsigned long long*)(bb + off_ctr);
     unsigned* d_cnt = (unsigned*)(bb + off_ctr + 16);
     int* d_err = (int*)(bb + off_ctr + 24);
+    unsigned long long* d_lt_next = (unsigned long long*)(bb + off_ctr + 32);
+    unsigned long long* d_prefix_lt = (unsigned long long*)(bb + off_prefix_lt);
+    unsigned grid_lt = 0;
+    if (total_lt > 0) {
+        int nb = 0;
+        CUDA_TRY(owner, cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                            &nb, rr_lt_lane_multi_kernel, LT_THREADS, LT_SMEM));
+        grid_lt = (unsigned)(owner->num_sms * std::max(nb, 1));
+        TIM_TRY(tim_ensure(owner, owner->lt_col,
+                           (size_t)grid_lt * LT_THREADS * LT_CAP * sizeof(uint32_t)));
+    }
     TIM_TRY(tim_ensure(owner, owner->ovf_list, (size_t)(total + 1) * sizeof(uint2)));
     TIM_TRY(tim_ensure(owner, owner->ovf_list2, (size_t)(total + 1) * sizeof(uint2)));
     // arena and occupancy as in the single-query path
@@ -1559,12 +1810,19 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
                                         cudaMemcpyHostToDevice, owner->stream));
         CUDA_TRY(owner, cudaMemcpyAsync(d_prefix, prefix.data(), (size_t)(nq + 1) * 8,
                                         cudaMemcpyHostToDevice, owner->stream));
+        CUDA_TRY(owner, cudaMemcpyAsync(d_prefix_lt, prefix_lt.data(), (size_t)(nq + 1) * 8,
+                                        cudaMemcpyHostToDevice, owner->stream));
         CUDA_TRY(owner, cudaMemsetAsync(d_scal, 0, (size_t)nq * sizeof(DevScalars), owner->stream));
         CUDA_TRY(owner, cudaMemsetAsync(d_next, 0, 64, owner->stream));
         uint64_t live3_total = 0;
         std::vector<uint64_t> live3(nq, 0);
         if (total > 0) {
-            TIM_TRY(launch_multi(owner, ma, 1, 1, grid1, smem1));
+            if (total_ic > 0) TIM_TRY(launch_multi(owner, ma, 1, 1, grid1, smem1));
+            if (total_lt > 0) {
+                rr_lt_lane_multi_kernel<<<grid_lt, LT_THREADS, LT_SMEM, owner->stream>>>(
+                    ma, d_prefix_lt, d_lt_next, (uint32_t*)owner->lt_col.p);
+                LAUNCH_CHECK(owner, "rr_lt_lane_multi_kernel (tier 1)");
+            }
             unsigned h_cnt[2] = {0, 0};
             CUDA_TRY(owner, cudaMemcpyAsync(h_cnt, d_cnt, sizeof h_cnt, cudaMemcpyDeviceToHost,
                                             owner->stream));
