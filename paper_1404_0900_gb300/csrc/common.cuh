@@ -186,6 +186,8 @@ static inline uint64_t make_sid(uint64_t phase, uint64_t round, uint64_t j) {
 // primitives (prims.cu)
 // Exclusive scan of uint32 counts into uint64 offsets out[0..count] (out[count] = total).
 int tim_scan_u32_to_u64(tim_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t count);
+// The same for uint64 counts (sums must stay below 2^64).
+int tim_scan_u64(tim_ctx* ctx, const unsigned long long* in, uint64_t* out, uint64_t count);
 // Stable LSD radix sort of (key, value) uint32 pairs by the low `bits` bits of key.
 // keys/vals are sorted in place (alternate buffers are taken from scratch).
 int tim_radix_sort_pairs(tim_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t count,

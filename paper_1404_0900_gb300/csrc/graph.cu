@@ -93,73 +93,59 @@ __global__ void check_dups_kernel(const uint32_t* __restrict__ sorted_dst,
     }
 }
 
-// LT: per node (one warp), inclusive prefix of t over the in-list, saturated, and the
-// weight-sum check.
-__global__ void lt_prefix_kernel(const uint64_t* __restrict__ rowptr, int64_t n,
-                                 const unsigned long long* __restrict__ lt_t,
-                                 const uint32_t* __restrict__ sorted_eid,
-                                 const float* __restrict__ w, uint32_t* __restrict__ thr,
-                                 int* __restrict__ err) {
-    const int lane = threadIdx.x & 31;
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp; v < n; v += nwarps) {
-        uint64_t a = rowptr[v], b = rowptr[v + 1];
-        unsigned long long carry = 0;
-        double wsum = 0.0;
-        for (uint64_t base = a; base < b; base += 32) {
-            uint64_t j = base + lane;
-            unsigned long long t = j < b ? lt_t[j] : 0ull;
-            double wj = j < b ? (double)w[sorted_eid[j]] : 0.0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                unsigned long long y = __shfl_up_sync(0xffffffffu, t, o);
-                if (lane >= o) t += y;
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) wj += __shfl_xor_sync(0xffffffffu, wj, o);
-            wsum += wj;
-            unsigned long long inc = carry + t;
-            if (j < b) thr[j] = inc > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)inc;
-            carry += __shfl_sync(0xffffffffu, t, 31);
+// LT thresholds from E, the exclusive scan of t over all in-edges: the inclusive
+// prefix of t over v's in-list at position j is E[j] + t[j] - E[beg(v)], saturated at
+// 2^32 - 1. The weight check compares v's total sum of t with floor((1 + 1e-5) 2^32)
+// (sum of floor(b 2^32) <= 2^32 sum b, so a valid in-list always passes). One thread per
+// in-edge; also marks nodes whose in-edges do not all carry the same t.
+__global__ void lt_thr_kernel(const uint64_t* __restrict__ rowptr, const uint32_t* __restrict__ dst_sorted,
+                              int64_t m, const unsigned long long* __restrict__ lt_t,
+                              const uint64_t* __restrict__ E, uint32_t* __restrict__ thr,
+                              uint8_t* __restrict__ nonuni, int* __restrict__ err) {
+    const unsigned long long bound = (unsigned long long)((1.0 + 1e-5) * 4294967296.0);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = dst_sorted[j];
+        const uint64_t beg = rowptr[v], end = rowptr[v + 1];
+        const unsigned long long c = E[j] + lt_t[j] - E[beg];
+        thr[j] = c > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)c;
+        if ((uint64_t)j + 1 == end && c > bound) atomicOr(err, TIM_DEV_ERR_WEIGHT);
+        if ((uint64_t)j > beg && lt_t[j] != lt_t[j - 1]) nonuni[v] = 1;
+    }
+}
+
+// IC: mark nodes whose in-edges do not all carry the same threshold. One thread per
+// in-edge.
+__global__ void ic_nonuniform_kernel(const uint64_t* __restrict__ rowptr,
+                                     const uint32_t* __restrict__ dst_sorted, int64_t m,
+                                     const uint32_t* __restrict__ thr,
+                                     uint8_t* __restrict__ nonuni) {
+    for (int64_t j = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = dst_sorted[j];
+        if ((uint64_t)j > rowptr[v] && thr[j] != thr[j - 1]) nonuni[v] = 1;
+    }
+}
+
+// Per-node threshold word: IC: low word = the first in-edge's threshold, bit 32 set when
+// all in-edges share it (empty in-lists included); LT: bit 32 set, low word = t, when
+// all in-edges share t < 2^32 (empty in-lists get 0).
+__global__ void node_thr_kernel(const uint64_t* __restrict__ rowptr, int64_t n, int model,
+                                const uint32_t* __restrict__ thr,
+                                const unsigned long long* __restrict__ lt_t,
+                                const uint8_t* __restrict__ nonuni,
+                                unsigned long long* __restrict__ node_thr) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t a = rowptr[v], b = rowptr[v + 1];
+        if (model == TIM_IC) {
+            const uint32_t t0 = b > a ? thr[a] : 0u;
+            node_thr[v] = (unsigned long long)t0 | (nonuni[v] ? 0ull : (1ull << 32));
+        } else {
+            const unsigned long long t0 = b > a ? lt_t[a] : 0ull;
+            const bool same = b > a && !nonuni[v] && t0 <= 0xFFFFFFFFull;
+            node_thr[v] = same ? ((1ull << 32) | t0) : 0ull;
         }
-        if (lane == 0 && wsum > 1.0 + 1e-5) atomicOr(err, TIM_DEV_ERR_WEIGHT);
-    }
-}
-
-// IC: does every in-edge of v carry the same threshold? One warp per node.
-__global__ void uniform_thr_kernel(const uint64_t* __restrict__ rowptr, int64_t n,
-                                   const uint32_t* __restrict__ thr,
-                                   unsigned long long* __restrict__ node_thr) {
-    const int lane = threadIdx.x & 31;
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp; v < n; v += nwarps) {
-        const uint64_t a = rowptr[v], b = rowptr[v + 1];
-        const uint32_t t0 = b > a ? thr[a] : 0u;
-        bool same = true;
-        for (uint64_t j = a + lane; j < b && same; j += 32) same = thr[j] == t0;
-        same = __all_sync(0xffffffffu, same);
-        if (lane == 0) node_thr[v] = (unsigned long long)t0 | (same ? (1ull << 32) : 0ull);
-    }
-}
-
-// LT: do all in-edges of v carry the same t = floor(b(e) 2^32) < 2^32? Then the
-// triggering pick of Section 6 is a division (see lt_pick in sample.cu). One warp per
-// node; low word t, bit 32 set when shared (empty in-lists get 0).
-__global__ void lt_uniform_kernel(const uint64_t* __restrict__ rowptr, int64_t n,
-                                  const unsigned long long* __restrict__ lt_t,
-                                  unsigned long long* __restrict__ node_thr) {
-    const int lane = threadIdx.x & 31;
-    int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t v = warp; v < n; v += nwarps) {
-        const uint64_t a = rowptr[v], b = rowptr[v + 1];
-        const unsigned long long t0 = b > a ? lt_t[a] : 0ull;
-        bool same = b > a && t0 <= 0xFFFFFFFFull;
-        for (uint64_t j = a + lane; j < b && same; j += 32) same = lt_t[j] == t0;
-        same = __all_sync(0xffffffffu, same);
-        if (lane == 0) node_thr[v] = same ? ((1ull << 32) | t0) : 0ull;
     }
 }
 
@@ -185,7 +171,7 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->src.p, 0, (size_t)(m + 4) * sizeof(uint32_t), ctx->stream));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->thr.p, 0, (size_t)(m + 4) * sizeof(uint32_t), ctx->stream));
 
-    DevBuf keys, vals, indeg, lt_t;
+    DevBuf keys, vals, indeg, lt_t, lt_e, nonuni;
     int rc = TIM_OK;
     do {
         if ((rc = tim_ensure(ctx, keys, (size_t)(m + 1) * sizeof(uint32_t)))) break;
@@ -222,29 +208,33 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
             check_dups_kernel<<<G, T, 0, ctx->stream>>>((const uint32_t*)keys.p,
                                                         (const uint32_t*)ctx->src.p, m, &ds->err);
             ctx->launches++;
-            if (model == TIM_LT) {
-                lt_prefix_kernel<<<G, T, 0, ctx->stream>>>(
-                    (const uint64_t*)ctx->rowptr.p, n, (const unsigned long long*)lt_t.p,
-                    (const uint32_t*)vals.p, d_w, (uint32_t*)ctx->thr.p, &ds->err);
-                ctx->launches++;
-            }
         }
-        if ((rc = tim_ensure(ctx, ctx->node_thr, (size_t)(n + 1) * 8))) break;
-        if (model == TIM_IC) {
-            uniform_thr_kernel<<<G, T, 0, ctx->stream>>>(
-                (const uint64_t*)ctx->rowptr.p, n, (const uint32_t*)ctx->thr.p,
-                (unsigned long long*)ctx->node_thr.p);
+        if ((rc = tim_ensure(ctx, nonuni, (size_t)(n + 1)))) break;
+        if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(nonuni.p, 0, (size_t)(n + 1), ctx->stream),
+                                 "memset")))
+            break;
+        if (m > 0 && model == TIM_LT) {
+            if ((rc = tim_ensure(ctx, lt_e, (size_t)(m + 1) * sizeof(uint64_t)))) break;
+            if ((rc = tim_scan_u64(ctx, (const unsigned long long*)lt_t.p, (uint64_t*)lt_e.p,
+                                   (uint64_t)m)))
+                break;
+            lt_thr_kernel<<<G, T, 0, ctx->stream>>>(
+                (const uint64_t*)ctx->rowptr.p, (const uint32_t*)keys.p, m,
+                (const unsigned long long*)lt_t.p, (const uint64_t*)lt_e.p, (uint32_t*)ctx->thr.p,
+                (uint8_t*)nonuni.p, &ds->err);
             ctx->launches++;
         } else if (m > 0) {
-            lt_uniform_kernel<<<G, T, 0, ctx->stream>>>(
-                (const uint64_t*)ctx->rowptr.p, n, (const unsigned long long*)lt_t.p,
-                (unsigned long long*)ctx->node_thr.p);
+            ic_nonuniform_kernel<<<G, T, 0, ctx->stream>>>(
+                (const uint64_t*)ctx->rowptr.p, (const uint32_t*)keys.p, m,
+                (const uint32_t*)ctx->thr.p, (uint8_t*)nonuni.p);
             ctx->launches++;
-        } else {
-            if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(ctx->node_thr.p, 0, (size_t)(n + 1) * 8,
-                                                          ctx->stream), "memset")))
-                break;
         }
+        if ((rc = tim_ensure(ctx, ctx->node_thr, (size_t)(n + 1) * 8))) break;
+        node_thr_kernel<<<G, T, 0, ctx->stream>>>(
+            (const uint64_t*)ctx->rowptr.p, n, model, (const uint32_t*)ctx->thr.p,
+            (const unsigned long long*)lt_t.p, (const uint8_t*)nonuni.p,
+            (unsigned long long*)ctx->node_thr.p);
+        ctx->launches++;
         if ((rc = tim_cuda_check(ctx, cudaGetLastError(), "graph kernels"))) break;
         if ((rc = tim_read_scalars(ctx))) break;
     } while (0);
@@ -252,6 +242,8 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
     tim_free(vals);
     tim_free(indeg);
     tim_free(lt_t);
+    tim_free(lt_e);
+    tim_free(nonuni);
     if (rc) return rc;
     if (ctx->h_scal->err & TIM_DEV_ERR_WEIGHT)
         return tim_fail(ctx, TIM_ERR_ARG, "invalid edge weights for the model");

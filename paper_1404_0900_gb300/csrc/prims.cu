@@ -40,7 +40,8 @@ __device__ unsigned long long block_excl_scan(unsigned long long v, unsigned lon
     return res;
 }
 
-__global__ void scan_reduce_kernel(const uint32_t* __restrict__ in, uint64_t count,
+template <class TIn>
+__global__ void scan_reduce_kernel(const TIn* __restrict__ in, uint64_t count,
                                    unsigned long long* __restrict__ block_sums) {
     uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
     unsigned long long s = 0;
@@ -70,21 +71,22 @@ __global__ void scan_block_sums_kernel(unsigned long long* __restrict__ sums, ui
     if (threadIdx.x == 0) *out_total = carry;
 }
 
-__global__ void scan_apply_kernel(const uint32_t* __restrict__ in, uint64_t count,
+template <class TIn>
+__global__ void scan_apply_kernel(const TIn* __restrict__ in, uint64_t count,
                                   const unsigned long long* __restrict__ block_off,
                                   uint64_t* __restrict__ out) {
     // blocked layout: thread t owns SCAN_ITEMS consecutive elements
     // padded index: one extra word per 32 keeps the blocked read free of bank conflicts
-    __shared__ uint32_t tile[SCAN_TILE + SCAN_TILE / 32];
+    __shared__ TIn tile[SCAN_TILE + SCAN_TILE / 32];
     uint64_t base = (uint64_t)blockIdx.x * SCAN_TILE;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; i++) {
         int x = i * SCAN_THREADS + threadIdx.x;
         uint64_t idx = base + (uint64_t)x;
-        tile[x + (x >> 5)] = idx < count ? in[idx] : 0u;
+        tile[x + (x >> 5)] = idx < count ? in[idx] : (TIn)0;
     }
     __syncthreads();
-    uint32_t loc[SCAN_ITEMS];
+    TIn loc[SCAN_ITEMS];
     unsigned long long s = 0;
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; i++) {
@@ -178,7 +180,8 @@ radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __res
 
 }  // namespace
 
-int tim_scan_u32_to_u64(tim_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t count) {
+template <class TIn>
+static int scan_to_u64(tim_ctx* ctx, const TIn* in, uint64_t* out, uint64_t count) {
     uint64_t nblocks = (count + SCAN_TILE - 1) / SCAN_TILE;
     if (nblocks == 0) {
         CUDA_TRY(ctx, cudaMemsetAsync(out, 0, sizeof(uint64_t), ctx->stream));
@@ -186,13 +189,22 @@ int tim_scan_u32_to_u64(tim_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_
     }
     TIM_TRY(tim_ensure(ctx, ctx->scratch_e, nblocks * sizeof(unsigned long long)));
     auto* sums = (unsigned long long*)ctx->scratch_e.p;
-    scan_reduce_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, ctx->stream>>>(in, count, sums);
+    scan_reduce_kernel<TIn><<<(unsigned)nblocks, SCAN_THREADS, 0, ctx->stream>>>(in, count, sums);
     LAUNCH_CHECK(ctx, "scan_reduce_kernel");
     scan_block_sums_kernel<<<1, 1024, 0, ctx->stream>>>(sums, nblocks, out + count);
     LAUNCH_CHECK(ctx, "scan_block_sums_kernel");
-    scan_apply_kernel<<<(unsigned)nblocks, SCAN_THREADS, 0, ctx->stream>>>(in, count, sums, out);
+    scan_apply_kernel<TIn><<<(unsigned)nblocks, SCAN_THREADS, 0, ctx->stream>>>(in, count, sums,
+                                                                               out);
     LAUNCH_CHECK(ctx, "scan_apply_kernel");
     return TIM_OK;
+}
+
+int tim_scan_u32_to_u64(tim_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t count) {
+    return scan_to_u64<uint32_t>(ctx, in, out, count);
+}
+
+int tim_scan_u64(tim_ctx* ctx, const unsigned long long* in, uint64_t* out, uint64_t count) {
+    return scan_to_u64<unsigned long long>(ctx, in, out, count);
 }
 
 int tim_radix_sort_pairs(tim_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t count, int bits) {
