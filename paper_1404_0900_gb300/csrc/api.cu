@@ -182,7 +182,7 @@ int tim_destroy(tim_ctx* ctx) {
                       &ctx->counts,   &ctx->node_off,   &ctx->cursor,    &ctx->node_sets,
                       &ctx->covered,  &ctx->chosen,     &ctx->best,      &ctx->seed_mark,
                       &ctx->seeds_dev, &ctx->ovf_list,  &ctx->big_bitmap, &ctx->big_queue,
-                      &ctx->ovf_list2, &ctx->arena,    &ctx->lt_col,
+                      &ctx->ovf_list2, &ctx->arena,    &ctx->lt_col,    &ctx->greedy_bar,
                       &ctx->scratch_a, &ctx->scratch_b, &ctx->scratch_c, &ctx->scratch_d,
                       &ctx->scratch_e, &ctx->scal,      &ctx->bulk_bitmap, &ctx->bulk_slot,
                       &ctx->bulk_F,    &ctx->bulk_M,    &ctx->bulk_ng,   &ctx->bulk_gp,

@@ -43,6 +43,7 @@ enum : int {
     TIM_DEV_ERR_GRAPH = 4,    // invalid graph (range, self-loop, duplicate)
     TIM_DEV_ERR_WEIGHT = 8,   // invalid weight
     TIM_DEV_ERR_BOUNDS = 16,  // an index check failed
+    TIM_DEV_ERR_TIMEOUT = 32, // a bounded device wait gave up
 };
 
 struct tim_ctx {
@@ -82,6 +83,7 @@ struct tim_ctx {
     DevBuf best;       // uint64[k]
     DevBuf seed_mark;  // uint32 bitmap[n/32 + 1]
     DevBuf seeds_dev;  // int32[n]
+    DevBuf greedy_bar; // grid barrier of the cooperative greedy launch
 
     // sets handed from tier 1 to tier 2 and from tier 2 to tier 3 of the sampler
     DevBuf ovf_list;    // uint32 set index

@@ -105,6 +105,112 @@ __global__ void cover_kernel(const unsigned long long* __restrict__ best,
     if (lane == 0 && fresh) atomicAdd(ncov, fresh);
 }
 
+// Barrier over all blocks of a co-resident (cooperative) launch: sense reversal on a
+// generation counter. The wait is bounded: after GRID_WAIT_LIMIT polls the block sets
+// TIM_DEV_ERR_TIMEOUT in *err and returns false (the caller then stops).
+constexpr unsigned GRID_WAIT_LIMIT = 1u << 24;
+
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+};
+
+__device__ bool grid_barrier(GridBarrier* bar, int* err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned g = ((volatile unsigned*)&bar->gen)[0];
+        if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (((volatile unsigned*)&bar->gen)[0] == g && it < GRID_WAIT_LIMIT) {
+                __nanosleep(64);
+                it++;
+            }
+            if (it >= GRID_WAIT_LIMIT) {
+                atomicOr(err, TIM_DEV_ERR_TIMEOUT);
+                ok = 0;
+            }
+        }
+        __threadfence();
+        s_ok = ok && !(((volatile int*)err)[0] & TIM_DEV_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// All k greedy rounds in one cooperative launch: per round an argmax over the counts
+// (every block reduces a slice, atomicMax into best[r]), a grid barrier, the cover step
+// of the chosen node (warps over its set list), and a second barrier.
+__global__ void __launch_bounds__(256)
+greedy_rounds_kernel(int* __restrict__ counts, uint8_t* __restrict__ chosen, uint64_t n,
+                     const uint64_t* __restrict__ node_off, const uint32_t* __restrict__ node_sets,
+                     const uint64_t* __restrict__ set_start, const uint32_t* __restrict__ set_len,
+                     const uint32_t* __restrict__ pool, uint8_t* __restrict__ covered, int k,
+                     unsigned long long* __restrict__ best, int32_t* __restrict__ seeds,
+                     unsigned long long* __restrict__ ncov, GridBarrier* bar, int* err) {
+    __shared__ unsigned long long wb[8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    unsigned long long fresh = 0;
+    for (int r = 0; r < k; r++) {
+        unsigned long long b = 0;
+        for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
+             v += (uint64_t)gridDim.x * blockDim.x) {
+            if (!((volatile uint8_t*)chosen)[v]) {
+                const unsigned long long key = greedy_key(((volatile int*)counts)[v], (uint32_t)v);
+                b = key > b ? key : b;
+            }
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+            b = y > b ? y : b;
+        }
+        if (lane == 0) wb[wid] = b;
+        __syncthreads();
+        if (wid == 0) {
+            b = lane < (int)(blockDim.x >> 5) ? wb[lane] : 0ull;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
+                b = y > b ? y : b;
+            }
+            if (lane == 0 && b) atomicMax(best + r, b);
+        }
+        if (!grid_barrier(bar, err)) return;
+        const unsigned long long key = ((volatile unsigned long long*)best)[r];
+        if (key != 0) {
+            const uint32_t v = ~(uint32_t)(key & 0xFFFFFFFFull);
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                chosen[v] = 1;
+                seeds[r] = (int32_t)v;
+            }
+            const uint64_t a = node_off[v], e = node_off[v + 1];
+            for (uint64_t i = a + warp; i < e; i += nwarps) {
+                const uint32_t s = node_sets[i];
+                if (((volatile uint8_t*)covered)[s]) continue;  // uniform across the warp
+                __syncwarp();
+                if (lane == 0) {
+                    covered[s] = 1;
+                    fresh++;
+                }
+                const uint64_t st = set_start[s];
+                const uint32_t len = set_len[s];
+                for (uint32_t t = lane; t < len; t += 32) atomicSub(&counts[pool[st + t]], 1);
+            }
+        }
+        if (!grid_barrier(bar, err)) return;
+    }
+    if (lane == 0 && fresh) atomicAdd(ncov, fresh);
+}
+
 }  // namespace
 
 int tim_build_index(tim_ctx* ctx) {
@@ -145,9 +251,47 @@ int tim_greedy(tim_ctx* ctx, int k, int32_t* host_seeds, uint64_t* covered) {
                                   ctx->stream));
     TIM_TRY(tim_zero_scalars(ctx));
     DevScalars* ds = tim_dscal(ctx);
+    auto* best = (unsigned long long*)ctx->best.p;
+    // all rounds in one cooperative launch when the device supports it
+    int coop = 0, nb = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    if (coop &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, greedy_rounds_kernel, 256, 0) ==
+            cudaSuccess &&
+        nb > 0) {
+        TIM_TRY(tim_ensure(ctx, ctx->greedy_bar, sizeof(GridBarrier)));
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->greedy_bar.p, 0, sizeof(GridBarrier), ctx->stream));
+        const unsigned grid = (unsigned)(ctx->num_sms * std::min(nb, 4));
+        int* d_counts = (int*)ctx->counts.p;
+        uint8_t* d_chosen = (uint8_t*)ctx->chosen.p;
+        uint64_t nn = n;
+        const uint64_t* d_off = (const uint64_t*)ctx->node_off.p;
+        const uint32_t* d_ns = (const uint32_t*)ctx->node_sets.p;
+        const uint64_t* d_ss = (const uint64_t*)ctx->set_start.p;
+        const uint32_t* d_sl = (const uint32_t*)ctx->set_len.p;
+        const uint32_t* d_pool = (const uint32_t*)ctx->pool.p;
+        uint8_t* d_cov = (uint8_t*)ctx->covered.p;
+        int kk = k;
+        int32_t* d_seeds = (int32_t*)ctx->seeds_dev.p;
+        unsigned long long* d_ncov = &ds->covered;
+        GridBarrier* d_bar = (GridBarrier*)ctx->greedy_bar.p;
+        int* d_err = &ds->err;
+        void* args[] = {&d_counts, &d_chosen, &nn, &d_off, &d_ns, &d_ss, &d_sl, &d_pool,
+                        &d_cov, &kk, &best, &d_seeds, &d_ncov, &d_bar, &d_err};
+        CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)greedy_rounds_kernel, dim3(grid),
+                                                  dim3(256), args, 0, ctx->stream));
+        LAUNCH_CHECK(ctx, "greedy_rounds_kernel");
+        if (host_seeds)
+            CUDA_TRY(ctx, cudaMemcpyAsync(host_seeds, ctx->seeds_dev.p, (size_t)k * sizeof(int32_t),
+                                          cudaMemcpyDeviceToHost, ctx->stream));
+        TIM_TRY(tim_read_scalars(ctx));
+        if (ctx->h_scal->err & TIM_DEV_ERR_TIMEOUT)
+            return tim_fail(ctx, TIM_ERR_TIMEOUT, "greedy grid barrier timed out");
+        if (covered) *covered = ctx->h_scal->covered;
+        return TIM_OK;
+    }
     const unsigned GA = (unsigned)(ctx->num_sms * 4);
     const unsigned GC = (unsigned)(ctx->num_sms * 2);
-    auto* best = (unsigned long long*)ctx->best.p;
     for (int r = 0; r < k; r++) {
         argmax_kernel<<<GA, 512, 0, ctx->stream>>>((const int*)ctx->counts.p,
                                                    (const uint8_t*)ctx->chosen.p, n, best + r);
