@@ -367,15 +367,20 @@ def oracle_rates(args, g, w_ic, w_lt, seconds: float, nthreads: int):
     sample sized to take about `seconds` of wall time in total."""
     from oracle import oracle as O
     rates = {}
-    for name, model, w, probe in (("IC", O.IC, w_ic, 256), ("LT", O.LT, w_lt, 4096)):
+    target = seconds / 2
+    for name, model, w, probe in (("IC", O.IC, w_ic, 1024), ("LT", O.LT, w_lt, 4096)):
         og = O.load_graph(g.n, g.rowptr, g.dst, w, model)
-        t0 = time.perf_counter()
-        O.sample(og, args.seed, O.make_sid(3, 0, 0), probe, nthreads)
-        dt = max(time.perf_counter() - t0, 1e-6)
-        count = max(probe, int(probe * (seconds / 2) / dt))
-        t0 = time.perf_counter()
-        O.sample(og, args.seed, O.make_sid(3, 0, probe), count, nthreads)
-        dt = time.perf_counter() - t0
+        O.sample(og, args.seed, O.make_sid(3, 0, 0), probe, nthreads)  # threads warm
+        # grow the sample until it takes at least half the target (at most 4 tries)
+        count, first = probe, probe
+        for _ in range(4):
+            t0 = time.perf_counter()
+            O.sample(og, args.seed, O.make_sid(3, 0, first), count, nthreads)
+            dt = max(time.perf_counter() - t0, 1e-6)
+            if dt >= 0.5 * target:
+                break
+            first += count
+            count = max(count * 2, int(count * target / dt))
         rates[name] = (count / dt, count, dt)
     return rates
 
