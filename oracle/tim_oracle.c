@@ -70,7 +70,7 @@ typedef unsigned __int128 u128;
 #define TAG_ROOT 0u
 #define TAG_IC 1u
 #define TAG_LT 2u
-#define TAG_SKIP 0x100u /* + digit pair index b >> 1, 0..15 */
+#define TAG_SKIP 0x100u /* + digit index b, 0..31 */
 #define SKIP_MIN_INDEG 512
 
 #define MODEL_IC 0
@@ -243,12 +243,12 @@ static int ic_live(uint32_t x, uint32_t thr) { return thr == 0xFFFFFFFFu || x < 
  * and "G >= 2^B" as U < Q_B.
  *
  * Gap r of a list starts at relative position pos (< d); R = d - pos remaining,
- * B = bit length of R (so 2^B > R). Uniform U_b (b = 0 .. B) = words (2(b&1),
- * 2(b&1)+1) (low, high) of Philox counter (sid lo, sid hi, beg + r, TAG_SKIP +
- * (b >> 1)), beg = in-CSR position of the list's first in-edge. If G >= 2^B or
- * G >= R the list has no further live in-edge; else position pos + G is live and the
- * next gap starts at pos + G + 1. (r <= pos < d keeps beg + r inside the list, so no
- * two lists share a counter.) */
+ * B = bit length of R (so 2^B > R). Uniform U_b (b = 0 .. B) = words (2(r&1),
+ * 2(r&1)+1) (low, high) of Philox counter (sid lo, sid hi, beg + (r >> 1), TAG_SKIP +
+ * b), beg = in-CSR position of the list's first in-edge: one draw per digit serves two
+ * consecutive gaps. If G >= 2^B or G >= R the list has no further live in-edge; else
+ * position pos + G is live and the next gap starts at pos + G + 1. (r <= pos < d keeps
+ * beg + (r >> 1) inside the list, so no two lists share a counter.) */
 uint64_t or_skip_q(uint32_t t, int b) {
     uint64_t q = (uint64_t)(0x100000000ull - (uint64_t)t) << 32;
     for (int i = 0; i < b; i++) q = (uint64_t)(((u128)q * q) >> 64);
@@ -279,8 +279,8 @@ static void skip_begin(skip_iter* it, uint64_t seed, uint64_t sid, int64_t beg, 
 
 static uint64_t skip_uniform(const skip_iter* it, int b) {
     uint32_t w[4];
-    draw(it->seed, it->sid, (uint32_t)(it->beg + it->r), TAG_SKIP + (uint32_t)(b >> 1), w);
-    return (b & 1) ? ((uint64_t)w[3] << 32 | w[2]) : ((uint64_t)w[1] << 32 | w[0]);
+    draw(it->seed, it->sid, (uint32_t)(it->beg + (it->r >> 1)), TAG_SKIP + (uint32_t)b, w);
+    return (it->r & 1) ? ((uint64_t)w[3] << 32 | w[2]) : ((uint64_t)w[1] << 32 | w[0]);
 }
 
 /* Next live relative position into *j; 0 when the list has no more. */

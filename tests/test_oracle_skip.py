@@ -98,8 +98,8 @@ def _python_skip(seed, sid, beg, d, t):
         B = rem.bit_length()
 
         def uni(b):
-            w = O.philox([sid & 0xFFFFFFFF, sid >> 32, beg + r, 0x100 + (b >> 1)], key)
-            lo, hi = (int(w[2]), int(w[3])) if b & 1 else (int(w[0]), int(w[1]))
+            w = O.philox([sid & 0xFFFFFFFF, sid >> 32, beg + (r >> 1), 0x100 + b], key)
+            lo, hi = (int(w[2]), int(w[3])) if r & 1 else (int(w[0]), int(w[1]))
             return hi << 32 | lo
 
         if uni(B) < qs[B]:
