@@ -177,7 +177,7 @@ int tim_destroy(tim_ctx* ctx) {
     DeviceGuard g(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->rowptr,   &ctx->src,        &ctx->thr,       &ctx->pool,
-                      &ctx->node_thr,
+                      &ctx->node_thr,  &ctx->qtab,
                       &ctx->pool_sid, &ctx->set_start,  &ctx->set_len,   &ctx->set_width,
                       &ctx->counts,   &ctx->node_off,   &ctx->cursor,    &ctx->node_sets,
                       &ctx->covered,  &ctx->chosen,     &ctx->best,      &ctx->seed_mark,

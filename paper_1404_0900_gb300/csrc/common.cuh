@@ -61,8 +61,10 @@ struct tim_ctx {
     DevBuf rowptr;  // uint64[n+1]
     DevBuf src;     // uint32[m + 4]
     DevBuf thr;     // uint32[m + 4] IC thresholds or LT inclusive cumulative thresholds
+    DevBuf qtab;      // IC: per skip-rule node, Q_0..Q_31 of its geometric gaps (u64[32])
     DevBuf node_thr;  // IC: uint64[n], low word = threshold shared by all in-edges of v,
-                      // bit 32 set when they do share one (empty in-lists included)
+                      // bit 32 set when they do share one (empty in-lists included),
+                      // bits 33..63 = 1 + index of the node's qtab entry (skip rule)
 
     // RR-set store
     uint64_t n_sets = 0;
@@ -264,7 +266,7 @@ double tim_host_lambda_prime(int64_t n, double eps_p, double ell);
 #define TIM_TAG_ROOT 0u
 #define TIM_TAG_IC 1u
 #define TIM_TAG_LT 2u
-#define TIM_TAG_SKIP 0x100u  // + gap digit pair index b >> 1, 0..15
+#define TIM_TAG_SKIP 0x100u  // + gap digit index b, 0..31
 // shortest IC in-list sampled by geometric skipping (tim_skip_rule)
 #define TIM_SKIP_MIN_INDEG 512u
 
@@ -317,9 +319,9 @@ __device__ __forceinline__ uint4 philox4x32_10(uint32_t c0, uint32_t c1, uint32_
 // Q_(b+1) = floor(Q_b^2 / 2^64)) a 64-bit uniform U decides digit b as
 //   U (2^64 + Q_b) < Q_b 2^64  <=>  U < Q_b and floor(U Q_b / 2^64) < Q_b - U,
 // and G >= 2^B (B = bit length of the R in-edges left, so 2^B > R) as U < Q_B.
-// U for digit b of gap r = words (2(b&1), 2(b&1)+1) of Philox counter (sid lo,
-// sid hi, beg + r, TIM_TAG_SKIP + (b >> 1)); beg = in-CSR position of the list's
-// first in-edge (r <= pos < d keeps beg + r inside the list). G >= R or G >= 2^B ends
+// U for digit b of gap r = words (2(r&1), 2(r&1)+1) of Philox counter (sid lo,
+// sid hi, beg + (r >> 1), TIM_TAG_SKIP + b); beg = in-CSR position of the list's first
+// in-edge (r <= pos < d keeps beg + (r >> 1) inside the list). G >= R or G >= 2^B ends
 // the list; otherwise position pos + G is live and the next gap starts after it.
 __device__ __forceinline__ bool tim_skip_rule(unsigned long long nt, unsigned long long d) {
     const uint32_t t = (uint32_t)nt;
@@ -332,27 +334,34 @@ __device__ __forceinline__ bool skip_digit(unsigned long long U, unsigned long l
     return U < Q && __umul64hi(U, Q) < Q - U;
 }
 
+// The gap table of a node under the rule: Q_b for b = 0..31, computed at load.
+__device__ __forceinline__ const unsigned long long* skip_table(const unsigned long long* qtab,
+                                                                unsigned long long nt) {
+    return qtab + ((nt >> 33) - 1ull) * 32ull;
+}
+
 // Live in-edges of a list under the rule, warp-cooperatively: lane b decides digit b
-// of each gap, one ballot gives G. visit(j) runs on every lane with the same in-CSR position j of each live
-// in-edge, in increasing order, and returns true to stop early. All 32 lanes must call
-// it with the same arguments.
+// of each gap (Q_b from the node's table), one ballot gives G; a lane's draw for gap 2i
+// also serves gap 2i + 1. visit(j) runs on every lane with the same in-CSR position j
+// of each live in-edge, in increasing order, and returns true to stop early. All 32
+// lanes must call it with the same arguments.
 template <class Visit>
 __device__ __forceinline__ void skip_live_warp(uint32_t s0, uint32_t s1, const PhiloxKeys& K,
-                                               uint32_t beg, uint32_t d, uint32_t t, int lane,
+                                               uint32_t beg, uint32_t d,
+                                               const unsigned long long* qtab_node, int lane,
                                                Visit&& visit) {
     const int bmax = 32 - __clz((int)d);
-    unsigned long long Q = (unsigned long long)(0x100000000ull - (unsigned long long)t) << 32;
-    for (int b = 0; b < bmax && b < lane; b++) Q = __umul64hi(Q, Q);
+    const unsigned long long Q = lane <= bmax && lane < 32 ? __ldg(qtab_node + lane) : 0ull;
+    uint4 x = make_uint4(0u, 0u, 0u, 0u);
     uint32_t pos = 0;
     for (uint32_t r = 0; pos < d; r++) {
         const uint32_t rem = d - pos;
         const int B = 32 - __clz((int)rem);
-        unsigned long long U = 0;
-        if (lane <= B) {
-            const uint4 x = philox4x32_10(s0, s1, beg + r, TIM_TAG_SKIP + (uint32_t)(lane >> 1), K);
-            U = (lane & 1) ? (((unsigned long long)x.w << 32) | x.z)
-                           : (((unsigned long long)x.y << 32) | x.x);
-        }
+        // B never grows along a list, so the lanes gap 2i + 1 needs drew for gap 2i
+        if ((r & 1u) == 0u && lane <= B)
+            x = philox4x32_10(s0, s1, beg + (r >> 1), TIM_TAG_SKIP + (uint32_t)lane, K);
+        const unsigned long long U = (r & 1u) ? (((unsigned long long)x.w << 32) | x.z)
+                                             : (((unsigned long long)x.y << 32) | x.x);
         const bool digit = lane < B && skip_digit(U, Q);
         const bool over = lane == B && U < Q;
         const uint32_t G = __ballot_sync(0xffffffffu, digit);

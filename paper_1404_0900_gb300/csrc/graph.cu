@@ -149,6 +149,28 @@ __global__ void node_thr_kernel(const uint64_t* __restrict__ rowptr, int64_t n, 
     }
 }
 
+// IC: nodes under the geometric-skip rule get a gap table Q_0..Q_31 (Q_0 = (2^32 - t)
+// 2^32, Q_(b+1) = floor(Q_b^2 / 2^64)) and 1 + its index in bits 33..63 of node_thr.
+// With tab == nullptr only counts them.
+__global__ void skip_tables_kernel(const uint64_t* __restrict__ rowptr, int64_t n,
+                                   unsigned long long* __restrict__ node_thr,
+                                   unsigned long long* __restrict__ tab, unsigned long long cap,
+                                   unsigned long long* __restrict__ counter) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const unsigned long long nt = node_thr[v];
+        if (!tim_skip_rule(nt, rowptr[v + 1] - rowptr[v])) continue;
+        const unsigned long long idx = atomicAdd(counter, 1ull);
+        if (!tab || idx >= cap) continue;
+        unsigned long long q = (0x100000000ull - (unsigned long long)(uint32_t)nt) << 32;
+        for (int b = 0; b < 32; b++) {
+            tab[idx * 32 + b] = q;
+            q = __umul64hi(q, q);
+        }
+        node_thr[v] = (nt & 0x1FFFFFFFFull) | ((idx + 1ull) << 33);
+    }
+}
+
 }  // namespace
 
 int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
@@ -235,6 +257,27 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
             (const unsigned long long*)lt_t.p, (const uint8_t*)nonuni.p,
             (unsigned long long*)ctx->node_thr.p);
         ctx->launches++;
+        if (model == TIM_IC) {
+            // count the skip-rule nodes, then give each its gap table
+            if ((rc = tim_ensure(ctx, lt_e, 2 * sizeof(unsigned long long)))) break;
+            auto* ctr = (unsigned long long*)lt_e.p;
+            if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(ctr, 0, 16, ctx->stream), "memset")))
+                break;
+            skip_tables_kernel<<<G, T, 0, ctx->stream>>>((const uint64_t*)ctx->rowptr.p, n,
+                                                          (unsigned long long*)ctx->node_thr.p,
+                                                          nullptr, 0, ctr);
+            ctx->launches++;
+            unsigned long long nskip = 0;
+            if ((rc = tim_cuda_check(ctx, cudaMemcpyAsync(&nskip, ctr, 8, cudaMemcpyDeviceToHost,
+                                                          ctx->stream), "copy")))
+                break;
+            if ((rc = tim_sync(ctx))) break;
+            if ((rc = tim_ensure(ctx, ctx->qtab, (size_t)(nskip + 1) * 32 * 8))) break;
+            skip_tables_kernel<<<G, T, 0, ctx->stream>>>(
+                (const uint64_t*)ctx->rowptr.p, n, (unsigned long long*)ctx->node_thr.p,
+                (unsigned long long*)ctx->qtab.p, nskip, ctr + 1);
+            ctx->launches++;
+        }
         if ((rc = tim_cuda_check(ctx, cudaGetLastError(), "graph kernels"))) break;
         if ((rc = tim_read_scalars(ctx))) break;
     } while (0);

@@ -55,6 +55,7 @@ struct SampleArgs {
     const uint32_t* src;
     const uint32_t* thr;
     const unsigned long long* node_thr;  // IC: per-node shared threshold (bit 32: shared)
+    const unsigned long long* qtab;      // IC: gap tables of skip-rule nodes
     uint64_t n, m;
     PhiloxKeys K;
     uint64_t sid0, count;
@@ -327,7 +328,8 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                     // geometric skipping: one step per live in-edge, by the first warp
                     if (wt == 0) {
                         int f = 0;
-                        skip_live_warp(s0, s1, K, bb, be - bb, t, lane, [&](uint32_t j) {
+                        skip_live_warp(s0, s1, K, bb, be - bb, skip_table(a.qtab, bt), lane,
+                                       [&](uint32_t j) {
                             if (lane == 0) {
                                 live++;
                                 exam++;
@@ -995,6 +997,7 @@ struct QueryDesc {
     const uint32_t* src;
     const uint32_t* thr;
     const unsigned long long* node_thr;
+    const unsigned long long* qtab;
     uint64_t n, m;
     uint64_t sid0, count;
     int model, flags, k, pad;
@@ -1030,6 +1033,7 @@ struct QArgs {
     const uint32_t* src;
     const uint32_t* thr;
     const unsigned long long* node_thr;
+    const unsigned long long* qtab;
     uint64_t n, m;
     int flags, k;
     const uint32_t* seed_mark;
@@ -1128,7 +1132,8 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
                 cur_q = qi;
             }
             const QueryDesc& d = ma.q[qi];
-            const QArgs qa{d.rowptr, d.src, d.thr, d.node_thr, d.n, d.m, d.flags, d.k, d.seed_mark};
+            const QArgs qa{d.rowptr, d.src, d.thr, d.node_thr, d.qtab,
+                           d.n,      d.m,   d.flags, d.k,     d.seed_mark};
             const int model = d.model;
             const unsigned long long budget =
                 (TIER == 1 && model == TIM_IC) ? d.width_budget : ~0ull;
@@ -1492,6 +1497,7 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
     a.src = (const uint32_t*)ctx->src.p;
     a.thr = (const uint32_t*)ctx->thr.p;
     a.node_thr = (const unsigned long long*)ctx->node_thr.p;
+    a.qtab = (const unsigned long long*)ctx->qtab.p;
     a.n = (uint64_t)ctx->n;
     a.m = (uint64_t)ctx->m;
     a.K = tim_philox_keys(req.seed);
@@ -1787,6 +1793,7 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
             d.src = (const uint32_t*)c->src.p;
             d.thr = (const uint32_t*)c->thr.p;
             d.node_thr = (const unsigned long long*)c->node_thr.p;
+            d.qtab = (const unsigned long long*)c->qtab.p;
             d.n = (uint64_t)c->n;
             d.m = (uint64_t)c->m;
             d.sid0 = r.sid0;

@@ -40,6 +40,7 @@ struct BulkArgs {
     const uint32_t* src;
     const uint32_t* thr;
     const unsigned long long* node_thr;  // per-node shared threshold (bit 32: shared)
+    const unsigned long long* qtab;      // gap tables of skip-rule nodes
     uint64_t n, m;
     PhiloxKeys K;
     uint64_t sid0;
@@ -257,7 +258,7 @@ __global__ void __launch_bounds__(256) bulk_skip_kernel(BulkArgs a) {
         if (cover && *(volatile uint32_t*)&a.slot_flag[s]) continue;
         const uint64_t sid = a.sid0 + __ldg(a.list + a.base + s);
         skip_live_warp((uint32_t)sid, (uint32_t)(sid >> 32), a.K, (uint32_t)beg,
-                       (uint32_t)(end - beg), (uint32_t)nt, lane, [&](uint32_t p) {
+                       (uint32_t)(end - beg), skip_table(a.qtab, nt), lane, [&](uint32_t p) {
                            bool fresh = false;
                            uint32_t u = 0;
                            uint64_t ub = 0, ue = 0;
@@ -377,6 +378,7 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
     a.src = (const uint32_t*)ctx->src.p;
     a.thr = (const uint32_t*)ctx->thr.p;
     a.node_thr = (const unsigned long long*)ctx->node_thr.p;
+    a.qtab = (const unsigned long long*)ctx->qtab.p;
     a.n = n;
     a.m = (uint64_t)ctx->m;
     a.K = tim_philox_keys(req.seed);
