@@ -315,6 +315,7 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
             // hubs first: the whole team strides over one in-list at a time, two groups in
             // flight per lane; only the in-list's first and last group need a range mask
             uint32_t bigmask = __ballot_sync(0xffffffffu, big);
+            int hubi = 0;  // hubs under the skip rule go to the team's warps in turn
             while (bigmask && !(flags & 3)) {
                 const int b = __ffs(bigmask) - 1;
                 bigmask &= bigmask - 1;
@@ -325,8 +326,8 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                 const uint32_t t = (uint32_t)bt;
                 if (shared && t == 0u) continue;
                 if (tim_skip_rule(bt, be - bb)) {
-                    // geometric skipping: one step per live in-edge, by the first warp
-                    if (wt == 0) {
+                    // geometric skipping: one step per live in-edge, by one warp of the team
+                    if (hubi++ % T == wt) {
                         int f = 0;
                         skip_live_warp(s0, s1, K, bb, be - bb, skip_table(a.qtab, bt), lane,
                                        [&](uint32_t j) {
