@@ -177,7 +177,8 @@ int tim_destroy(tim_ctx* ctx) {
     DeviceGuard g(ctx->device);
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->rowptr,   &ctx->src,        &ctx->thr,       &ctx->pool,
-                      &ctx->node_thr,  &ctx->qtab,
+                      &ctx->node_thr,  &ctx->qtab,      &ctx->ld_keys,   &ctx->ld_vals,
+                      &ctx->ld_indeg,  &ctx->ld_lt_t,   &ctx->ld_lt_e,   &ctx->ld_nonuni,
                       &ctx->pool_sid, &ctx->set_start,  &ctx->set_len,   &ctx->set_width,
                       &ctx->counts,   &ctx->node_off,   &ctx->cursor,    &ctx->node_sets,
                       &ctx->covered,  &ctx->chosen,     &ctx->best,      &ctx->seed_mark,
@@ -307,13 +308,9 @@ int tim_load_graph_device(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_o
     if (!d_out_rowptr || (m > 0 && (!d_out_dst || !d_edge_w)))
         return tim_fail(ctx, TIM_ERR_ARG, "null graph array");
     DeviceGuard g(ctx->device);
-    int rc = tim_graph_build(ctx, n, m, d_out_rowptr, d_out_dst, d_edge_w, model);
-    // the radix-sort scratch is only needed while loading
-    tim_free(ctx->scratch_a);
-    tim_free(ctx->scratch_b);
-    tim_free(ctx->scratch_c);
-    tim_free(ctx->scratch_d);
-    return rc;
+    // the build's temporaries and sort scratch stay allocated for the next load
+    // (tim_destroy frees them)
+    return tim_graph_build(ctx, n, m, d_out_rowptr, d_out_dst, d_edge_w, model);
 }
 
 int tim_load_graph(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* out_rowptr,

@@ -115,6 +115,9 @@ struct tim_ctx {
     DevBuf batch, greedy_batch;
     int last_team = 1;
 
+    // graph-load temporaries (graph.cu), kept between loads
+    DevBuf ld_keys, ld_vals, ld_indeg, ld_lt_t, ld_lt_e, ld_nonuni;
+
     // generic scratch for scans and sorts
     DevBuf scratch_a, scratch_b, scratch_c, scratch_d, scratch_e;
 

@@ -193,7 +193,13 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->src.p, 0, (size_t)(m + 4) * sizeof(uint32_t), ctx->stream));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->thr.p, 0, (size_t)(m + 4) * sizeof(uint32_t), ctx->stream));
 
-    DevBuf keys, vals, indeg, lt_t, lt_e, nonuni;
+    // temporaries of the build, kept by the context so that reloading allocates nothing
+    DevBuf& keys = ctx->ld_keys;
+    DevBuf& vals = ctx->ld_vals;
+    DevBuf& indeg = ctx->ld_indeg;
+    DevBuf& lt_t = ctx->ld_lt_t;
+    DevBuf& lt_e = ctx->ld_lt_e;
+    DevBuf& nonuni = ctx->ld_nonuni;
     int rc = TIM_OK;
     do {
         if ((rc = tim_ensure(ctx, keys, (size_t)(m + 1) * sizeof(uint32_t)))) break;
@@ -281,12 +287,6 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
         if ((rc = tim_cuda_check(ctx, cudaGetLastError(), "graph kernels"))) break;
         if ((rc = tim_read_scalars(ctx))) break;
     } while (0);
-    tim_free(keys);
-    tim_free(vals);
-    tim_free(indeg);
-    tim_free(lt_t);
-    tim_free(lt_e);
-    tim_free(nonuni);
     if (rc) return rc;
     if (ctx->h_scal->err & TIM_DEV_ERR_WEIGHT)
         return tim_fail(ctx, TIM_ERR_ARG, "invalid edge weights for the model");
