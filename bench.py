@@ -29,12 +29,13 @@ sys.path.insert(0, ROOT)
 from paper_1404_0900_gb300 import inputs, start_round  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) per RR-set member of the IC sampler passes, from the ncu
-# capture of `bench.py --mode sample --scale 18 --theta 300000` (dram__bytes_read.sum +
-# dram__bytes_write.sum of the launch / members it produced); used to scale the traffic
-# of one full-size launch in proportion to its work. None where no capture exists for
-# the current kernel.
-DRAM_BYTES_PER_MEMBER = {1: None, 2: None, 3: None}
+# DRAM bytes (read + write) per RR-set member of the IC sampler passes 1 and 2, from a
+# one-pass ncu capture of the full-size run `bench.py --steps 1 --warmup 1 --no-e2e
+# --no-cpu-baseline --no-batch --no-learned` (dram__bytes_read.sum +
+# dram__bytes_write.sum over the timed step's launches of the pass / the members that
+# pass produced in that step); the traffic of one launch is scaled from it by members.
+# None where no capture exists for the current kernel.
+DRAM_BYTES_PER_MEMBER = {1: 60.2, 2: 273.8, 3: None}
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
@@ -285,9 +286,9 @@ def run_ours(args):
     # roofline of the dominant kernel: the IC sampler pass with the most device time
     p = prof_ic
     dom = max((1, 2, 3), key=lambda i: p[f"pass{i}_ms"])
-    names = {1: "rr_warp_kernel<IC> tier 1 (shared-memory warp per set)",
-             2: "rr_warp_kernel<IC> tier 2 (global-memory warp per set)",
-             3: "bulk level-synchronous IC pass (tier 3)"}
+    names = {1: "rr_team_kernel<IC, Cap<256,9>, pass 1> (shared-memory hash, warp per set)",
+             2: "rr_team_kernel<IC, Cap<8192,14>, pass 2> (global-arena hash, team per set)",
+             3: "bulk level-synchronous IC pass (pass 3)"}
     alg_bytes = sampler_bytes(p, dom)
     launches_dom = max(p[f"pass{dom}_launches"], 1)
     per_launch_bytes = alg_bytes / launches_dom
@@ -333,8 +334,9 @@ def run_ours(args):
                      "unit": "GB/s", "frac": achieved / peak,
                      "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
                      "traffic": traffic,
-                     "traffic_note": "DRAM bytes per launch scaled by members from the R-MAT "
-                                     "scale-18 ncu capture (null: no capture of this kernel)"},
+                     "traffic_note": "DRAM bytes per launch: bytes per member from the "
+                                     "full-size one-pass ncu capture of this workload x the "
+                                     "members per launch (null: no capture of this kernel)"},
         "sampler_profile": {"IC": prof_ic, "LT": prof_lt},
         "autotune": tuning,
         "clocks": clk,

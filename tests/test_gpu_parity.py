@@ -52,6 +52,10 @@ GRAPHS = {
     "chain": lambda: (inputs.chain(3000), "p1"),
     "rmat10_tri": lambda: (inputs.rmat(10, seed=9), "tri"),
     "rmat13_mixed": lambda: (inputs.rmat(13, seed=4), "mixed"),
+    # 500 roots reach node 0, whose 6000 in-edges are all live: one frontier batch
+    # inserts 6000 members into a set whose visited hash starts small and must grow
+    "fan_p1": lambda: (inputs.from_edges(6501, [(i, 0) for i in range(1, 6001)]
+                                         + [(0, j) for j in range(6001, 6501)]), "p1"),
 }
 
 
@@ -79,7 +83,7 @@ def test_rr_sets_bit_exact(eng, name, model):
     g, kind = GRAPHS[name]()
     w = _weights(g, kind, model)
     og = _load(eng, g, w, model)
-    count = 3000 if name in ("rand_p1", "chain") else 20000
+    count = 3000 if name in ("rand_p1", "chain", "fan_p1") else 20000
     _compare_store(eng, og, 11, O.make_sid(3, 0, 0), count)
     # a second seed and a set-id range that does not start at zero
     _compare_store(eng, og, 12345678901, (5 << 40) + 17, 777)
