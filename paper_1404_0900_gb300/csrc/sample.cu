@@ -14,7 +14,8 @@
 //   outgrow the queue, or (IC) whose examined in-edges would pass a budget, is listed
 //   for tier 2. This keeps the kernel's tail short: light sets are most sets.
 // Tier 2: the same code with a 32x larger queue and hash in global memory (one arena
-//   slot per team) and no edge budget, run by teams of T warps per set: T = 1 when the
+//   slot per team; the queue tail and status stay in shared memory, since every new
+//   member takes a tail atomic) and no edge budget, run by teams of T warps per set: T = 1 when the
 //   listed sets are many (parallelism across sets fills the GPU), up to 8 when they are
 //   few (the team splits each in-list, so one heavy set does not leave the GPU idle).
 // In-lists of at least BIG_GROUPS groups (hubs) are streamed by the whole team one at
@@ -470,6 +471,7 @@ template <int MODEL, class C, int TIER, int T>
 __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(SampleArgs a) {
     extern __shared__ uint32_t smem[];
     __shared__ unsigned long long s_claim[WARPS];
+    __shared__ int s_ctl[WARPS][4];  // tier 2: a team's tail and status (shared atomics)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int wt = wid % T, team = wid / T;
     const int tl = wt * 32 + lane;  // thread index inside the team
@@ -485,7 +487,7 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
     team_sync<T>(team);
     uint32_t* queue = hash + C::H;
     uint16_t* slot = reinterpret_cast<uint16_t*>(queue + C::Q);
-    int* ctl = reinterpret_cast<int*>(queue + C::Q + C::Q / 2);
+    int* ctl = TIER == 1 ? reinterpret_cast<int*>(queue + C::Q + C::Q / 2) : s_ctl[team];
     const unsigned long long budget =
         (TIER == 1 && MODEL == TIM_IC) ? a.width_budget : ~0ull;
     unsigned long long* counter = TIER == 1 ? &a.ds->next_set : &a.ds->next2;
@@ -1071,6 +1073,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
     extern __shared__ uint32_t smem[];
     __shared__ unsigned long long s_claim[WARPS];
     __shared__ unsigned long long s_prefix[MAXQ + 1];
+    __shared__ int s_ctl[WARPS][4];  // tier 2: a team's tail and status (shared atomics)
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int wt = wid % T, team = wid / T;
     const int tl = wt * 32 + lane;
@@ -1087,7 +1090,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
     team_sync<T>(team);
     uint32_t* queue = hash + C::H;
     uint16_t* slot = reinterpret_cast<uint16_t*>(queue + C::Q);
-    int* ctl = reinterpret_cast<int*>(queue + C::Q + C::Q / 2);
+    int* ctl = TIER == 1 ? reinterpret_cast<int*>(queue + C::Q + C::Q / 2) : s_ctl[team];
     unsigned long long* counter = &ma.next[TIER - 1];
     const uint64_t items = TIER == 1 ? s_prefix[ma.nq]
                                      : (uint64_t)min(((volatile unsigned*)ma.cnt)[0], ma.list_cap);
