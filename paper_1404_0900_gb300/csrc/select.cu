@@ -16,11 +16,22 @@
 
 namespace {
 
+// Both index kernels take four members per thread and step (16-byte loads of the pool,
+// which is 16-byte aligned): four independent atomics per thread are in flight at once.
 __global__ void count_members_kernel(const uint32_t* __restrict__ pool, uint64_t members,
                                      uint32_t* __restrict__ cnt) {
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < members;
-         p += (uint64_t)gridDim.x * blockDim.x)
-        atomicAdd(&cnt[pool[p]], 1u);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t quads = members >> 2;
+    const uint4* pool4 = reinterpret_cast<const uint4*>(pool);
+    for (uint64_t q = tid; q < quads; q += stride) {
+        const uint4 u = __ldg(pool4 + q);
+        atomicAdd(&cnt[u.x], 1u);
+        atomicAdd(&cnt[u.y], 1u);
+        atomicAdd(&cnt[u.z], 1u);
+        atomicAdd(&cnt[u.w], 1u);
+    }
+    for (uint64_t p = (quads << 2) + tid; p < members; p += stride) atomicAdd(&cnt[pool[p]], 1u);
 }
 
 __global__ void scatter_sets_kernel(const uint32_t* __restrict__ pool,
@@ -28,10 +39,26 @@ __global__ void scatter_sets_kernel(const uint32_t* __restrict__ pool,
                                     const uint64_t* __restrict__ node_off,
                                     uint32_t* __restrict__ cursor,
                                     uint32_t* __restrict__ node_sets) {
-    for (uint64_t p = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; p < members;
-         p += (uint64_t)gridDim.x * blockDim.x) {
-        uint32_t u = pool[p];
-        uint32_t slot = atomicAdd(&cursor[u], 1u);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const uint64_t quads = members >> 2;
+    const uint4* pool4 = reinterpret_cast<const uint4*>(pool);
+    const uint4* sid4 = reinterpret_cast<const uint4*>(pool_sid);
+    for (uint64_t q = tid; q < quads; q += stride) {
+        const uint4 u = __ldg(pool4 + q);
+        const uint4 j = __ldg(sid4 + q);
+        const uint32_t c0 = atomicAdd(&cursor[u.x], 1u), c1 = atomicAdd(&cursor[u.y], 1u);
+        const uint32_t c2 = atomicAdd(&cursor[u.z], 1u), c3 = atomicAdd(&cursor[u.w], 1u);
+        const uint64_t o0 = __ldg(node_off + u.x), o1 = __ldg(node_off + u.y);
+        const uint64_t o2 = __ldg(node_off + u.z), o3 = __ldg(node_off + u.w);
+        node_sets[o0 + c0] = j.x;
+        node_sets[o1 + c1] = j.y;
+        node_sets[o2 + c2] = j.z;
+        node_sets[o3 + c3] = j.w;
+    }
+    for (uint64_t p = (quads << 2) + tid; p < members; p += stride) {
+        const uint32_t u = pool[p];
+        const uint32_t slot = atomicAdd(&cursor[u], 1u);
         node_sets[node_off[u] + slot] = pool_sid[p];
     }
 }
