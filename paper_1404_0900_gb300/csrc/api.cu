@@ -234,7 +234,7 @@ int tim_autotune(tim_ctx* ctx, uint64_t sample_sets, uint64_t seed, tim_tuning* 
     if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
     if (sample_sets == 0) return tim_fail(ctx, TIM_ERR_ARG, "sample_sets must be > 0");
     DeviceGuard g(ctx->device);
-    const uint64_t budgets_ic[] = {4096, 16384, 65536};
+    const uint64_t budgets_ic[] = {512, 1024, 2048, 4096, 16384};
     const uint64_t budgets_lt[] = {16384};
     // pass-2 team size stays automatic: it is chosen per call from the number of sets
     // handed over, which a fixed calibration size cannot stand in for
@@ -242,7 +242,7 @@ int tim_autotune(tim_ctx* ctx, uint64_t sample_sets, uint64_t seed, tim_tuning* 
     const int chunks[] = {1, 2, 4};
     const bool ic = ctx->model == TIM_IC;
     const uint64_t* budgets = ic ? budgets_ic : budgets_lt;
-    const int nbud = ic ? 3 : 1;
+    const int nbud = ic ? 5 : 1;
     const int nteam = 1;
     const tim_profile saved_prof = ctx->prof;
     SampleRequest req;
