@@ -60,10 +60,12 @@ def parse_args(argv=None):
     p.add_argument("--batch-queries", type=int, default=64)
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-start-round comparisons")
-    p.add_argument("--mode", choices=["timplus", "sample", "batch", "learned"],
+    p.add_argument("--mode", choices=["timplus", "sample", "batch", "learned", "c3"],
                    default="timplus",
                    help="timplus: the TIM+ step (default); sample: only RR-set generation "
-                        "(tim_sample_rr of --theta NodeSelection sets), for profiling")
+                        "(tim_sample_rr of --theta NodeSelection sets), for profiling; "
+                        "c3: TIM+ on the 41.6M-node / 1.4B-edge Chung-Lu graph, IC "
+                        "trivalency, k=50, eps=0.2")
     p.add_argument("--theta", type=int, default=1_000_000)
     p.add_argument("--model", choices=["ic", "lt"], default="ic")
     return p.parse_args(argv)
@@ -482,6 +484,68 @@ def run_sample_only(args):
             "GTEPS (in-edges examined)": width / (ms / 1e3) / 1e9, "passes": passes}
 
 
+def run_c3(args):
+    """TIM+ on the largest configuration: directed Chung-Lu, 41.6M nodes, 1.4B edges,
+    exponent 2.1, IC trivalency (p per edge from {0.1, 0.01, 0.001}), k = 50, eps = 0.2,
+    l = 1, drawn and loaded on the device. --steps runs after --warmup, each timed by
+    CUDA events on the library's stream (the graph, 11 GB as G^T, is far larger than L2)."""
+    import torch
+
+    from paper_1404_0900_gb300 import tim
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    k, eps = 50, 0.2
+    t0 = time.perf_counter()
+    g = inputs.chung_lu_c3_device(seed=1)
+    w = inputs.trivalency_device(g, seed=2)
+    torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
+    n, m = g.n, g.m
+    with tim.Engine(0, stream) as eng:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tim.tim_load_graph_device(eng.ctx, g.n, g.m, g.rowptr, g.dst, w, tim.TIM_IC)
+        e1.record(stream)
+        e1.synchronize()
+        load_ms = e0.elapsed_time(e1)
+        del g, w
+        torch.cuda.empty_cache()
+        tuning = tim.tim_autotune(eng.ctx, 200_000, args.seed)
+        for _ in range(args.warmup):
+            tim.tim_run(eng.ctx, k, eps, args.ell, args.seed)
+        clocks = ClockSampler(0)
+        clocks.start()
+        runs = []
+        launches0 = tim.tim_launch_count(eng.ctx)
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            seeds, frac, st = tim.tim_run(eng.ctx, k, eps, args.ell, args.seed)
+            e1.record(stream)
+            e1.synchronize()
+            runs.append((e0.elapsed_time(e1), st))
+        launches = tim.tim_launch_count(eng.ctx) - launches0
+        clk = clocks.stop()
+    ms = sum(r[0] for r in runs)
+    st = runs[-1][1]
+    return {"mode": "c3", "metric": "RR sets/s (TIM+ end to end, IC trivalency)",
+            "value": sum(r[1]["sets_total"] for r in runs) / (ms / 1e3), "unit": "RR sets/s",
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "data": "synthetic (seeded Chung-Lu, no dataset)",
+            "config": {"workload": "TIM+ on a directed Chung-Lu graph (exponent 2.1), IC "
+                                   "trivalency {0.1, 0.01, 0.001}, k=50, eps=0.2, l=1",
+                       "n": n, "m": m, "k": k, "eps": eps, "ell": args.ell,
+                       "l2": "inputs larger than L2"},
+            "phases_ms": {x: st[x] for x in ("ms_kpt", "ms_refine", "ms_select_sample",
+                                             "ms_select_greedy")},
+            "kpt_round": st["kpt_round"], "kpt_star": st["kpt_star"], "kpt_plus": st["kpt_plus"],
+            "theta": st["theta"], "sets_total": st["sets_total"],
+            "members_select": st["members_select"], "width_total": st["width_total"],
+            "generate_s": gen_s, "load_ms": load_ms, "autotune": tuning, "clocks": clk,
+            "gpu_launches": launches}
+
+
 def batch_specs(nq: int):
     """The batched workload: query q has an R-MAT graph of scale U{12..20} (graph seed
     q + 1), k ~ U{1..50}, eps from {0.1, 0.2, 0.3, 0.5}; even q use IC weighted cascade,
@@ -681,6 +745,9 @@ def main(argv=None):
         return
     if args.mode == "learned" and args.impl == "ours":
         print(json.dumps(run_learned_compare(args)), flush=True)
+        return
+    if args.mode == "c3" and args.impl == "ours":
+        print(json.dumps(run_c3(args)), flush=True)
         return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

@@ -247,11 +247,24 @@ def _torch_gen(seed: int, device):
     return g
 
 
-def csr_from_pairs_device(n: int, src, dst, name: str = "") -> DeviceGraph:
-    """Device version of csr_from_pairs (self-loops and duplicates dropped)."""
+def csr_from_pairs_device(n: int, src, dst, name: str = "", m_exact: int | None = None,
+                          gen=None) -> DeviceGraph:
+    """Device version of csr_from_pairs (self-loops and duplicates dropped). With m_exact,
+    a uniform random subset of exactly m_exact of the distinct edges is kept (drawn
+    with `gen`); fewer distinct edges than that is an error."""
     import torch
     keep = src != dst
     key = torch.unique(src[keep].to(torch.int64) * n + dst[keep].to(torch.int64), sorted=True)
+    del keep
+    if m_exact is not None:
+        if key.numel() < m_exact:
+            raise ValueError(f"only {key.numel()} distinct edges, {m_exact} asked for")
+        # the m_exact smallest of one uniform key per edge (a sort, not a permutation)
+        r = torch.rand(key.numel(), generator=gen, device=key.device, dtype=torch.float64)
+        pick = torch.argsort(r)[:m_exact]
+        del r
+        key = key[torch.sort(pick).values]
+        del pick
     s = key // n
     d = (key % n).to(torch.int32)
     rowptr = torch.zeros(n + 1, dtype=torch.int64, device=key.device)
@@ -281,21 +294,33 @@ def rmat_device(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0
 
 
 def chung_lu_device(n: int, m_draws: int, gamma: float = 2.1, seed: int = 1,
-                    device="cuda") -> DeviceGraph:
+                    device="cuda", m_exact: int | None = None) -> DeviceGraph:
     """Directed Chung-Lu power-law graph from m_draws edge draws (node weights
     (i+1)^(-1/(gamma-1)), destinations on a seeded permutation of the ids); self-loops
-    and duplicates dropped, so m is below m_draws."""
+    and duplicates dropped, so m is below m_draws (or exactly m_exact: a uniform subset
+    of the distinct edges)."""
     import torch
     gen = _torch_gen(seed, device)
     w = (torch.arange(n, dtype=torch.float64, device=device) + 1.0) ** (-1.0 / (gamma - 1.0))
     cdf = torch.cumsum(w, 0)
+    del w
     cdf /= cdf[-1].clone()
     perm = torch.randperm(n, generator=gen, device=device)
     u = torch.rand(m_draws, generator=gen, device=device, dtype=torch.float64)
     s = torch.searchsorted(cdf, u, right=True).clamp_(max=n - 1)
     u = torch.rand(m_draws, generator=gen, device=device, dtype=torch.float64)
     d = perm[torch.searchsorted(cdf, u, right=True).clamp_(max=n - 1)]
-    return csr_from_pairs_device(n, s, d, name=f"chunglu{n}_dev")
+    del u, perm, cdf
+    return csr_from_pairs_device(n, s, d, name=f"chunglu{n}_dev", m_exact=m_exact, gen=gen)
+
+
+# The largest configuration: a Chung-Lu graph of Twitter's size (Section 7, Table 2):
+# 41.6M nodes, 1.4B edges, exponent 2.1. 1.75B draws leave about 1.44B distinct edges.
+C3_N, C3_M, C3_DRAWS = 41_600_000, 1_400_000_000, 1_750_000_000
+
+
+def chung_lu_c3_device(seed: int = 1, device="cuda") -> DeviceGraph:
+    return chung_lu_device(C3_N, C3_DRAWS, 2.1, seed=seed, device=device, m_exact=C3_M)
 
 
 def weighted_cascade_device(g: DeviceGraph):
