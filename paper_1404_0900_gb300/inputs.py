@@ -261,7 +261,7 @@ def csr_from_pairs_device(n: int, src, dst, name: str = "", m_exact: int | None 
             raise ValueError(f"only {key.numel()} distinct edges, {m_exact} asked for")
         # the m_exact smallest of one uniform key per edge (a sort, not a permutation)
         r = torch.rand(key.numel(), generator=gen, device=key.device, dtype=torch.float64)
-        pick = torch.argsort(r)[:m_exact]
+        pick = torch.argsort(r, stable=True)[:m_exact]
         del r
         key = key[torch.sort(pick).values]
         del pick
@@ -301,11 +301,16 @@ def chung_lu_device(n: int, m_draws: int, gamma: float = 2.1, seed: int = 1,
     of the distinct edges)."""
     import torch
     gen = _torch_gen(seed, device)
-    w = (torch.arange(n, dtype=torch.float64, device=device) + 1.0) ** (-1.0 / (gamma - 1.0))
-    cdf = torch.cumsum(w, 0)
+    # the weight CDF on the host: a device float scan may round differently run to run
+    w = (np.arange(n, dtype=np.float64) + 1.0) ** (-1.0 / (gamma - 1.0))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+    cdf = torch.from_numpy(cdf).to(device)
     del w
-    cdf /= cdf[-1].clone()
-    perm = torch.randperm(n, generator=gen, device=device)
+    # a seeded permutation: the stable order of one uniform key per id (reproducible
+    # whatever the device's sort does with equal keys)
+    perm = torch.argsort(torch.rand(n, generator=gen, device=device, dtype=torch.float64),
+                         stable=True)
     u = torch.rand(m_draws, generator=gen, device=device, dtype=torch.float64)
     s = torch.searchsorted(cdf, u, right=True).clamp_(max=n - 1)
     u = torch.rand(m_draws, generator=gen, device=device, dtype=torch.float64)
@@ -338,10 +343,12 @@ def trivalency_device(g: DeviceGraph, seed: int = 1):
 
 
 def lt_random_normalised_device(g: DeviceGraph, seed: int = 1):
-    """Uniform [0, 1) in-weights normalised to sum to one per node."""
+    """Uniform random in-weights normalised to sum to one per node. The draws are
+    integers in [1, 2^40) so that the per-node sums are exact whatever order the device
+    adds them in (reproducible weights)."""
     import torch
     gen = _torch_gen(seed, g.dst.device)
-    r = torch.rand(g.m, generator=gen, device=g.dst.device, dtype=torch.float64)
+    r = torch.randint(1, 1 << 40, (g.m,), generator=gen, device=g.dst.device, dtype=torch.int64)
     d = g.dst.to(torch.int64)
-    tot = torch.zeros(g.n, dtype=torch.float64, device=g.dst.device).index_add_(0, d, r)
-    return (r / tot[d]).to(torch.float32)
+    tot = torch.zeros(g.n, dtype=torch.int64, device=g.dst.device).index_add_(0, d, r)
+    return (r.to(torch.float64) / tot[d].to(torch.float64)).to(torch.float32)
