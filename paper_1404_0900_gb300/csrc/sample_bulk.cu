@@ -143,20 +143,87 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t s, uint32_t u,
     }
 }
 
+// Appends of one block staged in shared memory: a warp reserves buffer space with a
+// shared atomic, and the block reserves the global range once, at its end (a list's
+// global counter is one address for the whole GPU: one atomic per warp and step there
+// serialises). Appends that do not fit go to the global list directly.
+constexpr unsigned STAGE = 1024;
+struct Stage {
+    uint2 f[STAGE];
+    uint2 m[STAGE];
+    unsigned nf, nm;
+    unsigned long long gf, gm;
+};
+
+__device__ __forceinline__ void staged_append(bool pred, uint32_t s, uint32_t u, uint2* buf,
+                                              unsigned* used, unsigned long long* counter,
+                                              uint2* list, uint64_t cap, int* err, int errbit,
+                                              int lane) {
+    const uint32_t bal = __ballot_sync(0xffffffffu, pred);
+    if (!bal) return;
+    const int leader = __ffs(bal) - 1;
+    unsigned base = 0;
+    if (lane == leader) base = atomicAdd(used, (unsigned)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    const unsigned r = __popc(bal & ((1u << lane) - 1u));
+    const bool staged = pred && base + r < STAGE;
+    if (staged) buf[base + r] = make_uint2(s, u);
+    warp_append(pred && !staged, s, u, counter, list, cap, err, errbit, lane);
+}
+
+// Copy a block's staged appends to one reserved range of each global list.
+__device__ __forceinline__ void stage_flush(Stage& st, const BulkArgs& a) {
+    __syncthreads();
+    const unsigned nf = min(st.nf, STAGE), nm = min(st.nm, STAGE);
+    if (threadIdx.x == 0) {
+        st.gf = nf ? atomicAdd(&a.bs->f_count, (unsigned long long)nf) : 0ull;
+        st.gm = nm ? atomicAdd(&a.bs->m_count, (unsigned long long)nm) : 0ull;
+    }
+    __syncthreads();
+    for (unsigned i = threadIdx.x; i < nf; i += blockDim.x) {
+        if (st.gf + i < a.fcap)
+            a.F[st.gf + i] = st.f[i];
+        else
+            atomicOr(&a.bs->err, 1);
+    }
+    for (unsigned i = threadIdx.x; i < nm; i += blockDim.x) {
+        if (st.gm + i < a.mcap)
+            a.M[st.gm + i] = st.m[i];
+        else
+            atomicOr(&a.bs->err, 2);
+    }
+}
+
+// Add a fresh member's in-degree and count to its set, one atomic per set and warp.
+__device__ __forceinline__ void slot_add(bool fresh, uint32_t s, uint64_t deg, const BulkArgs& a,
+                                         int lane) {
+    const uint32_t fm = __ballot_sync(0xffffffffu, fresh);
+    if (!fresh) return;
+    const uint32_t grp = __match_any_sync(fm, s);
+    // the group's members are distinct nodes of one set: their in-degrees sum below m
+    const unsigned dsum = __reduce_add_sync(grp, (unsigned)deg);
+    if (lane == __ffs(grp) - 1) {
+        atomicAdd(&a.slot_width[s], (unsigned long long)dsum);
+        atomicAdd(&a.slot_cnt[s], (unsigned)__popc(grp));
+    }
+}
+
 __global__ void __launch_bounds__(256) bulk_expand_kernel(BulkArgs a) {
+    __shared__ Stage st;
+    if (threadIdx.x == 0) st.nf = st.nm = 0;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const uint64_t G = a.gp[a.lvl_n];
     const uint64_t nchunks = (G + 31) >> 5;
     const uint64_t wid = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t per = (nchunks + nw - 1) / nw;
-    const uint64_t c0 = wid * per;
+    const uint64_t c0 = min(wid * per, nchunks);
     const uint64_t c1 = min(c0 + per, nchunks);
-    if (c0 >= c1) return;
     const bool cover = a.flags & SAMPLE_COVER;
     // item holding group 32 * c0: the last i with gp[i] <= 32 * c0
-    uint64_t i0;
-    {
+    uint64_t i0 = 0;
+    if (c0 < c1) {
         uint64_t lo = 0, hi = a.lvl_n;  // gp[lo] <= x < gp[hi]
         const uint64_t x = c0 << 5;
         while (hi - lo > 1) {
@@ -224,21 +291,23 @@ __global__ void __launch_bounds__(256) bulk_expand_kernel(BulkArgs a) {
                     if (fresh) {
                         ub = __ldg(a.rowptr + u);
                         ue = __ldg(a.rowptr + u + 1);
-                        atomicAdd(&a.slot_width[s], ue - ub);
-                        atomicAdd(&a.slot_cnt[s], 1u);
                         if (cover && marked(a.seed_mark, u)) a.slot_flag[s] = 1u;
                     }
                 }
             }
-            warp_append(fresh, s, u, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2, lane);
+            slot_add(fresh, s, ue - ub, a, lane);
+            staged_append(fresh, s, u, st.m, &st.nm, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2,
+                          lane);
             const bool push = fresh && ue > ub && !(cover && a.slot_flag[s]);
-            warp_append(push, s, u, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1, lane);
+            staged_append(push, s, u, st.f, &st.nf, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1,
+                          lane);
         }
         i0 = __shfl_sync(0xffffffffu, i, 31);
         live_acc += nlive;
     }
     live_acc = __reduce_add_sync(0xffffffffu, live_acc);
     if (lane == 0 && live_acc) atomicAdd(&a.bs->live, (unsigned long long)live_acc);
+    stage_flush(st, a);
 }
 
 // The level's items under the skip rule: one warp per item draws the live in-edges
@@ -328,14 +397,23 @@ __global__ void bulk_finalize_kernel(BulkArgs a) {
 
 // Copy members into the store (emit) and clear the visited bits, one member each.
 __global__ void bulk_emit_clear_kernel(BulkArgs a, unsigned long long mcount, int emit) {
+    const int lane = threadIdx.x & 31;
     for (uint64_t e = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; e < mcount;
          e += (uint64_t)gridDim.x * blockDim.x) {
         const uint2 it = a.M[e];
         if (emit) {
+            // one cursor atomic per set and warp (staged appends keep a set's members
+            // together)
+            const uint32_t grp = __match_any_sync(__activemask(), it.x);
+            const int leader = __ffs(grp) - 1;
             const unsigned long long st = a.slot_start[it.x];
             const uint32_t cnt = a.slot_cnt[it.x];
+            uint32_t base = 0;
+            if (lane == leader && st + cnt <= a.pool_cap)
+                base = atomicAdd(&a.slot_cursor[it.x], (unsigned)__popc(grp));
+            base = __shfl_sync(grp, base, leader);
             if (st + cnt <= a.pool_cap) {
-                const uint32_t pos = atomicAdd(&a.slot_cursor[it.x], 1u);
+                const uint32_t pos = base + __popc(grp & ((1u << lane) - 1u));
                 a.pool[st + pos] = it.y;
                 a.pool_sid[st + pos] = a.list[a.base + it.x];
             }
