@@ -30,12 +30,12 @@ from paper_1404_0900_gb300 import inputs, start_round  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # DRAM bytes (read + write) per RR-set member of the IC sampler passes 1 and 2, from a
-# one-pass ncu capture of the full-size run `bench.py --steps 1 --warmup 1 --no-e2e
-# --no-cpu-baseline --no-batch --no-learned` (dram__bytes_read.sum +
-# dram__bytes_write.sum over the timed step's launches of the pass / the members that
-# pass produced in that step); the traffic of one launch is scaled from it by members.
-# None where no capture exists for the current kernel.
-DRAM_BYTES_PER_MEMBER = {1: 60.2, 2: 273.8, 3: None}
+# one-pass ncu capture (`-k regex:rr_team_kernel`) of the full-size run `bench.py
+# --steps 1 --warmup 1 --no-e2e --no-cpu-baseline --no-batch --no-learned`
+# (dram__bytes_read.sum + dram__bytes_write.sum over the timed step's launches of the
+# pass / the members that pass produced in that step); the traffic of one launch is
+# scaled from it by members. None where no capture exists for the current kernel.
+DRAM_BYTES_PER_MEMBER = {1: 70.5, 2: 275.1, 3: None}
 FALLBACK_HBM_GBS = 6800.0
 L2_FLUSH_BYTES = 512 << 20
 
