@@ -11,6 +11,7 @@ paper's algorithms together in the paper's order:
   node_selection  -- Algorithm 1 (Section 3.1), theta from Eq. 4 / Eq. 5
   tim_plus        -- TIM+ (Section 4.1): Algorithm 2 -> 3 -> theta -> Algorithm 1
   tim             -- TIM (Section 3.3): Algorithm 2 -> theta -> Algorithm 1
+  spread_mc       -- forward Monte-Carlo estimate of E[I(S)] (Section 2.1; Section 7)
 """
 from __future__ import annotations
 
@@ -64,6 +65,10 @@ def lib():
             "or_skip_q": (u64, [u32, i32]),
             "or_skip_bit": (i32, [u64, u64]),
             "or_skip_live": (i64, [u64, u64, i64, i64, u32, P]),
+            "or_out_positions": (i32, [i64, i64, P, P, P, P, P]),
+            "or_cascade_one": (i64, [P, P, P, i64, i64, i32, P, P, P, u64, u64, P, i32, P]),
+            "or_spread_mc": (i64, [P, P, P, i64, i64, i32, P, P, P, u64, u64, i64, P, i32, P,
+                                   i32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -177,9 +182,23 @@ class OracleGraph:
     src: np.ndarray  # int32[m]
     thr: np.ndarray  # uint32[m]
     in_w: np.ndarray  # float32[m]
+    out: tuple | None = None  # (out_rowptr, out_pos, pos_dst), built on first use
 
     def indeg(self) -> np.ndarray:
         return np.diff(self.rowptr)
+
+    def out_positions(self):
+        """G as an out-CSR of in-CSR positions, and each position's destination."""
+        if self.out is None:
+            orow = np.zeros(self.n + 1, dtype=np.int64)
+            opos = np.zeros(max(self.m, 1), dtype=np.int64)
+            pdst = np.zeros(max(self.m, 1), dtype=np.int32)
+            rc = lib().or_out_positions(self.n, self.m, _p(self.rowptr), _p(self.src), _p(orow),
+                                        _p(opos), _p(pdst))
+            if rc != 0:
+                raise MemoryError
+            self.out = (orow, opos, pdst)
+        return self.out
 
     def args(self):
         return (_p(self.rowptr), _p(self.src), _p(self.thr), self.n, self.m, self.model)
@@ -281,6 +300,41 @@ def covered_count(g: OracleGraph, seed: int, sid0: int, count: int, seeds,
     if r < 0:
         raise MemoryError
     return int(r)
+
+
+# ------------------------------------------------------ forward Monte Carlo
+
+def _seed_array(g: OracleGraph, seeds) -> np.ndarray:
+    s = np.ascontiguousarray(seeds, dtype=np.int32)
+    if s.size and (s.min() < 0 or s.max() >= g.n):
+        raise ValueError("seed out of range")
+    return s if s.size else np.zeros(1, dtype=np.int32)
+
+
+def cascade_one(g: OracleGraph, seeds, seed: int, sid: int) -> np.ndarray:
+    """The nodes activated from `seeds` in the world of set id sid (sorted)."""
+    orow, opos, pdst = g.out_positions()
+    s = _seed_array(g, seeds)
+    buf = np.zeros(g.n + 1, dtype=np.int32)
+    cnt = lib().or_cascade_one(*g.args(), _p(orow), _p(opos), _p(pdst), seed, sid, _p(s),
+                               len(seeds), _p(buf))
+    if cnt < 0:
+        raise ValueError(f"cascade failed ({cnt})")
+    return np.sort(buf[:cnt])
+
+
+def spread_mc(g: OracleGraph, seeds, count: int, seed: int, sid0: int, nthreads: int = 0):
+    """Forward Monte-Carlo spread (Section 2.1): activated-node counts of cascades sid0 ..
+    sid0 + count - 1 (int64[count]) and their exact total; total / count estimates
+    E[I(S)]."""
+    orow, opos, pdst = g.out_positions()
+    s = _seed_array(g, seeds)
+    counts = np.zeros(max(count, 1), dtype=np.int64)
+    tot = lib().or_spread_mc(*g.args(), _p(orow), _p(opos), _p(pdst), seed, sid0, count, _p(s),
+                             len(seeds), _p(counts), nthreads)
+    if tot < 0:
+        raise ValueError(f"spread failed ({tot})")
+    return counts[:count], int(tot)
 
 
 # --------------------------------------------------------------- Algorithm 2

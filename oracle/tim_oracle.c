@@ -803,3 +803,117 @@ int64_t or_covered_count(const int64_t* rowptr, const int32_t* src, const uint32
     }
     return fail ? OR_ERR_OOM : cov;
 }
+
+/* ------------------------------------------------ forward Monte-Carlo spread
+ * Section 2.1 (the Monte Carlo estimate of E[I(S)] of Kempe et al.): draw a random
+ * graph g -- every edge kept with its propagation probability -- and count the nodes
+ * of g reachable from S; the average over independent draws estimates E[I(S)]
+ * (Section 7 averages 10^5 of them). Triggering form (Section 4.2): every node keeps
+ * the in-edges of its sampled triggering set, and the nodes reachable from S over
+ * kept edges are the activated ones.
+ *
+ * Cascade c draws the world of set id sid = sid0 + c with the keys of the RR sets:
+ * the IC in-edge at in-CSR position j is kept iff ic_live(or_ic_word(sid, j), thr_j)
+ * -- one coin per in-edge, also in the lists that RR sampling treats by geometric
+ * skipping -- and under LT node v keeps the in-edge lt_pick(sid, v). So where no list
+ * is skipped, the RR set of sid is exactly the set of nodes that reach its root in
+ * the world of the cascade with the same sid.
+ *
+ * The walk needs G itself: or_out_positions lists, for every node u, the in-CSR
+ * positions of its out-edges (ascending), and the destination of every position. */
+int or_out_positions(int64_t n, int64_t m, const int64_t* rowptr, const int32_t* src,
+                     int64_t* out_rowptr, int64_t* out_pos, int32_t* pos_dst) {
+    int64_t* cur = (int64_t*)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!cur) return OR_ERR_OOM;
+    for (int64_t v = 0; v <= n; v++) out_rowptr[v] = 0;
+    for (int64_t j = 0; j < m; j++) out_rowptr[src[j] + 1]++;
+    for (int64_t v = 0; v < n; v++) out_rowptr[v + 1] += out_rowptr[v];
+    for (int64_t v = 0; v < n; v++)
+        for (int64_t j = rowptr[v]; j < rowptr[v + 1]; j++) {
+            pos_dst[j] = (int32_t)v;
+            int64_t u = src[j];
+            out_pos[out_rowptr[u] + cur[u]++] = j;
+        }
+    free(cur);
+    return OR_OK;
+}
+
+/* One cascade: the nodes reachable from the distinct seeds in the world of sid, in
+ * queue[] (BFS order); mark[] is all-zero on entry and on exit. Returns their count. */
+static int64_t cascade(const or_graph* g, const int64_t* out_rowptr, const int64_t* out_pos,
+                       const int32_t* pos_dst, uint64_t seed, uint64_t sid, const int32_t* seeds,
+                       int k, int32_t* queue, uint8_t* mark) {
+    int64_t tail = 0;
+    for (int i = 0; i < k; i++)
+        if (!mark[seeds[i]]) {
+            mark[seeds[i]] = 1;
+            queue[tail++] = seeds[i];
+        }
+    for (int64_t head = 0; head < tail; head++) {
+        int64_t u = queue[head];
+        for (int64_t e = out_rowptr[u]; e < out_rowptr[u + 1]; e++) {
+            int64_t j = out_pos[e];
+            int32_t v = pos_dst[j];
+            if (mark[v]) continue;
+            int kept = g->model == MODEL_IC ? ic_live(or_ic_word(seed, sid, j), g->thr[j])
+                                            : lt_pick(g, seed, sid, v) == j;
+            if (kept) {
+                mark[v] = 1;
+                queue[tail++] = v;
+            }
+        }
+    }
+    for (int64_t i = 0; i < tail; i++) mark[queue[i]] = 0;
+    return tail;
+}
+
+/* The activated nodes of one cascade (sid) into members[] (capacity n); returns their
+ * count. */
+int64_t or_cascade_one(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
+                       int64_t m, int model, const int64_t* out_rowptr, const int64_t* out_pos,
+                       const int32_t* pos_dst, uint64_t seed, uint64_t sid, const int32_t* seeds,
+                       int k, int32_t* members) {
+    or_graph g = {n, m, rowptr, src, thr, model};
+    for (int i = 0; i < k; i++)
+        if (seeds[i] < 0 || seeds[i] >= n) return OR_ERR_ARG;
+    uint8_t* mark = (uint8_t*)calloc((size_t)n, 1);
+    if (!mark) return OR_ERR_OOM;
+    int64_t cnt = cascade(&g, out_rowptr, out_pos, pos_dst, seed, sid, seeds, k, members, mark);
+    free(mark);
+    return cnt;
+}
+
+/* Cascades sid0 .. sid0+count-1: counts[c] = activated nodes of cascade c. Returns
+ * the total over all cascades (an exact integer; the estimate of E[I(S)] is
+ * total / count) or an error code. */
+int64_t or_spread_mc(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
+                     int64_t m, int model, const int64_t* out_rowptr, const int64_t* out_pos,
+                     const int32_t* pos_dst, uint64_t seed, uint64_t sid0, int64_t count,
+                     const int32_t* seeds, int k, int64_t* counts, int nthreads) {
+    or_graph g = {n, m, rowptr, src, thr, model};
+    for (int i = 0; i < k; i++)
+        if (seeds[i] < 0 || seeds[i] >= n) return OR_ERR_ARG;
+    nthreads = set_threads(nthreads);
+    int64_t total = 0;
+    int fail = 0;
+#pragma omp parallel num_threads(nthreads) reduction(+ : total)
+    {
+        uint8_t* mark = (uint8_t*)calloc((size_t)n, 1);
+        int32_t* queue = (int32_t*)malloc(sizeof(int32_t) * ((size_t)n + 1));
+        if (!mark || !queue) {
+#pragma omp atomic write
+            fail = 1;
+        }
+#pragma omp for schedule(dynamic, 16)
+        for (int64_t c = 0; c < count; c++) {
+            if (!mark || !queue) continue;
+            int64_t a = cascade(&g, out_rowptr, out_pos, pos_dst, seed, sid0 + (uint64_t)c, seeds,
+                                k, queue, mark);
+            counts[c] = a;
+            total += a;
+        }
+        free(mark);
+        free(queue);
+    }
+    return fail ? OR_ERR_OOM : total;
+}
