@@ -60,13 +60,15 @@ def parse_args(argv=None):
     p.add_argument("--batch-queries", type=int, default=64)
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-start-round comparisons")
-    p.add_argument("--mode", choices=["timplus", "sample", "batch", "learned", "c3"],
+    p.add_argument("--mode", choices=["timplus", "sample", "batch", "learned", "c3", "spread"],
                    default="timplus",
                    help="timplus: the TIM+ step (default); sample: only RR-set generation "
                         "(tim_sample_rr of --theta NodeSelection sets), for profiling; "
                         "c3: TIM+ on the 41.6M-node / 1.4B-edge Chung-Lu graph, IC "
-                        "trivalency, k=50, eps=0.2")
+                        "trivalency, k=50, eps=0.2; spread: forward Monte-Carlo spread "
+                        "of TIM+'s seeds (--cascades) against the RR estimate")
     p.add_argument("--theta", type=int, default=1_000_000)
+    p.add_argument("--cascades", type=int, default=10_000)
     p.add_argument("--model", choices=["ic", "lt"], default="ic")
     return p.parse_args(argv)
 
@@ -546,6 +548,53 @@ def run_c3(args):
             "gpu_launches": launches}
 
 
+def run_spread(args):
+    """Forward Monte-Carlo spread (Section 2.1; Section 7 averages 10^5 cascades) of the
+    seeds TIM+ returns on the bench graph, IC and LT: --cascades cascades per timed run,
+    CUDA events on the library's stream; the mean against the RR-set estimate n * F_R(S)
+    of the same run (Corollary 1)."""
+    import torch
+
+    from paper_1404_0900_gb300 import tim
+    g = inputs.rmat(args.scale, seed=1)
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    out = {"mode": "spread", "scale": args.scale, "k": args.k, "eps": args.eps,
+           "cascades": args.cascades, "steps": args.steps, "warmup": args.warmup,
+           "models": {}}
+    sid0 = 7 << 56
+    for name, model, w in (("IC", tim.TIM_IC, inputs.weighted_cascade(g)),
+                           ("LT", tim.TIM_LT, inputs.lt_inverse_indegree(g))):
+        with tim.Engine(0, stream) as eng:
+            tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, model)
+            seeds, frac, st = tim.tim_run(eng.ctx, args.k, args.eps, args.ell, args.seed)
+            for _ in range(max(args.warmup, 1)):
+                tim.tim_spread_mc(eng.ctx, seeds, args.cascades, args.seed, sid0)
+            ms = 0.0
+            totals = []
+            for s in range(args.steps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                mean, total, counts = tim.tim_spread_mc(eng.ctx, seeds, args.cascades, args.seed,
+                                                        sid0 + s * args.cascades,
+                                                        want_counts=True)
+                e1.record(stream)
+                e1.synchronize()
+                ms += e0.elapsed_time(e1)
+                totals.append(counts.astype(np.float64))
+            allc = np.concatenate(totals)
+            rr = g.n * frac
+            out["models"][name] = {
+                "cascades_per_s": args.cascades * args.steps / (ms / 1e3),
+                "activated_per_s": float(allc.sum()) / (ms / 1e3),
+                "ms_per_run": ms / args.steps, "spread_mc": float(allc.mean()),
+                "spread_mc_stderr": float(allc.std() / np.sqrt(allc.size)),
+                "spread_rr": rr, "rel_diff": float(allc.mean()) / rr - 1.0,
+                "theta": st["theta"]}
+    return out
+
+
 def batch_specs(nq: int):
     """The batched workload: query q has an R-MAT graph of scale U{12..20} (graph seed
     q + 1), k ~ U{1..50}, eps from {0.1, 0.2, 0.3, 0.5}; even q use IC weighted cascade,
@@ -748,6 +797,9 @@ def main(argv=None):
         return
     if args.mode == "c3" and args.impl == "ours":
         print(json.dumps(run_c3(args)), flush=True)
+        return
+    if args.mode == "spread" and args.impl == "ours":
+        print(json.dumps(run_spread(args)), flush=True)
         return
     line = run_reference(args) if args.impl == "reference" else run_ours(args)
     if line is not None:

@@ -187,7 +187,9 @@ int tim_destroy(tim_ctx* ctx) {
                       &ctx->scratch_a, &ctx->scratch_b, &ctx->scratch_c, &ctx->scratch_d,
                       &ctx->scratch_e, &ctx->scal,      &ctx->bulk_bitmap, &ctx->bulk_slot,
                       &ctx->bulk_F,    &ctx->bulk_M,    &ctx->bulk_ng,   &ctx->bulk_gp,
-                      &ctx->bulk_scal, &ctx->batch,     &ctx->greedy_batch};
+                      &ctx->bulk_scal, &ctx->batch,     &ctx->greedy_batch,
+                      &ctx->out_rowptr, &ctx->out_rec,  &ctx->mc_bitmap, &ctx->mc_queue,
+                      &ctx->mc_counts, &ctx->mc_seeds,  &ctx->mc_scal};
     for (DevBuf* b : bufs) tim_free(*b);
     if (ctx->h_scal) cudaFreeHost(ctx->h_scal);
     for (int i = 0; i < 8; i++)

@@ -118,6 +118,12 @@ struct tim_ctx {
     // graph-load temporaries (graph.cu), kept between loads
     DevBuf ld_keys, ld_vals, ld_indeg, ld_lt_t, ld_lt_e, ld_nonuni;
 
+    // forward cascades (spread.cu): G as out-records {in-CSR position, destination},
+    // built from G^T on first use; per-block visited bitmaps (kept all-zero between
+    // calls) and queues; cascade counts, seeds, counters
+    DevBuf out_rowptr, out_rec, mc_bitmap, mc_queue, mc_counts, mc_seeds, mc_scal;
+    bool have_out = false, mc_clean = false;
+
     // generic scratch for scans and sorts
     DevBuf scratch_a, scratch_b, scratch_c, scratch_d, scratch_e;
 
@@ -375,6 +381,32 @@ __device__ __forceinline__ void skip_live_warp(uint32_t s0, uint32_t s1, const P
 }
 
 // Uniform root: floor(x * n / 2^64) with x the first two words of the ROOT draw.
+// LT triggering pick when all in-edges of v carry the same t = floor(b 2^32) (per-node
+// word nt: bit 32 set, low word t): the cumulative thresholds are C_j = min((j + 1) t,
+// 2^32 - 1), so the first j with x < C_j is floor(x / t) when that is below d and
+// x < 2^32 - 1 (C never exceeds 2^32 - 1), and there is none otherwise -- the same
+// in-edge as the search over C. Returns the in-CSR position, or end for none.
+__device__ __forceinline__ uint64_t lt_uniform_pick(unsigned long long nt, uint64_t beg,
+                                                    uint64_t end, uint32_t x) {
+    const uint32_t t = (uint32_t)nt;
+    if (t == 0u || x == 0xFFFFFFFFu) return end;
+    const uint64_t q = x / t;
+    return q < end - beg ? beg + q : end;
+}
+
+// First position j in [lo, hi) with thr[j] > x, by one thread.
+__device__ __forceinline__ uint64_t lane_lt_search(const uint32_t* __restrict__ thr, uint64_t lo,
+                                                   uint64_t hi, uint32_t x) {
+    for (int it = 0; it < 40 && lo < hi; it++) {
+        const uint64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(thr + mid) > x)
+            hi = mid;
+        else
+            lo = mid + 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ uint32_t rr_root(uint64_t sid, uint64_t n, const PhiloxKeys& K) {
     uint4 w = philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32), 0u, TIM_TAG_ROOT, K);
     unsigned long long x = ((unsigned long long)w.y << 32) | w.x;

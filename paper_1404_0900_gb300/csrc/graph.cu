@@ -181,6 +181,7 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
     ctx->have_graph = false;
     ctx->have_kpt = false;
     ctx->have_feat = false;
+    ctx->have_out = false;
     ctx->n_sets = ctx->members = 0;
     TIM_TRY(tim_zero_scalars(ctx));
     DevScalars* ds = tim_dscal(ctx);

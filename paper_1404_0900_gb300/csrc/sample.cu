@@ -148,32 +148,6 @@ __device__ __forceinline__ uint64_t warp_lt_search(const uint32_t* __restrict__ 
     return b ? lo + (uint64_t)(__ffs(b) - 1) : hi;
 }
 
-// LT triggering pick when all in-edges of v carry the same t = floor(b 2^32) (per-node
-// word nt: bit 32 set, low word t): the cumulative thresholds are C_j = min((j + 1) t,
-// 2^32 - 1), so the first j with x < C_j is floor(x / t) when that is below d and
-// x < 2^32 - 1 (C never exceeds 2^32 - 1), and there is none otherwise -- the same
-// in-edge as the search over C. Returns the in-CSR position, or end for none.
-__device__ __forceinline__ uint64_t lt_uniform_pick(unsigned long long nt, uint64_t beg,
-                                                    uint64_t end, uint32_t x) {
-    const uint32_t t = (uint32_t)nt;
-    if (t == 0u || x == 0xFFFFFFFFu) return end;
-    const uint64_t q = x / t;
-    return q < end - beg ? beg + q : end;
-}
-
-// First position j in [lo, hi) with thr[j] > x, by one thread.
-__device__ __forceinline__ uint64_t lane_lt_search(const uint32_t* __restrict__ thr, uint64_t lo,
-                                                   uint64_t hi, uint32_t x) {
-    for (int it = 0; it < 40 && lo < hi; it++) {
-        const uint64_t mid = lo + ((hi - lo) >> 1);
-        if (__ldg(thr + mid) > x)
-            hi = mid;
-        else
-            lo = mid + 1;
-    }
-    return lo;
-}
-
 // ------------------------------------------------------------ tiers 1 and 2
 
 // Barrier over the T warps of a team (T = 1: the warp itself). Named barrier ids

@@ -16,6 +16,8 @@ from . import build as _build
 
 TIM_IC, TIM_LT = 0, 1
 TIM_OK = 0
+TIM_ERR_ARG, TIM_ERR_OOM, TIM_ERR_OVERFLOW = -1, -2, -3
+TIM_ERR_TIMEOUT, TIM_ERR_CUDA, TIM_ERR_STATE = -4, -5, -6
 
 STATUS = {0: "TIM_OK", -1: "TIM_ERR_ARG", -2: "TIM_ERR_OOM", -3: "TIM_ERR_OVERFLOW",
           -4: "TIM_ERR_TIMEOUT", -5: "TIM_ERR_CUDA", -6: "TIM_ERR_STATE"}
@@ -113,6 +115,8 @@ _SIGS = {
                           C.c_uint64]),
     "tim_run_tim": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_uint64, _P, _P, _P]),
     "tim_launch_count": (C.c_uint64, [_P]),
+    "tim_spread_mc": (C.c_int, [_P, _P, C.c_int, C.c_uint64, C.c_uint64, C.c_uint64, _P, _P,
+                                _P]),
     "tim_get_profile": (C.c_int, [_P, _P, C.c_int]),
     "tim_set_width_budget": (C.c_int, [_P, C.c_uint64]),
     "tim_set_team_size": (C.c_int, [_P, C.c_int]),
@@ -314,6 +318,19 @@ def tim_node_select_noalloc(device: int, stream, n: int, n_sets: int, d_off, d_m
 
 def tim_launch_count(ctx) -> int:
     return int(lib().tim_launch_count(ctx))
+
+
+def tim_spread_mc(ctx, seeds, count: int, seed: int, first_set_id: int,
+                  want_counts: bool = False):
+    """Forward Monte-Carlo spread of `seeds` over `count` cascades (set ids first_set_id
+    + c). Returns (mean, total, per-cascade counts as uint32 or None)."""
+    s = np.ascontiguousarray(seeds, dtype=np.int32)
+    total, mean = C.c_uint64(), C.c_double()
+    counts = np.zeros(max(count, 1), dtype=np.uint32) if want_counts else None
+    _check(ctx, lib().tim_spread_mc(ctx, _ptr(s) if s.size else None, int(s.size), count, seed,
+                                    first_set_id, C.byref(total), C.byref(mean),
+                                    _ptr(counts) if want_counts else None))
+    return mean.value, total.value, (counts[:count] if want_counts else None)
 
 
 def tim_set_width_budget(ctx, budget: int):
