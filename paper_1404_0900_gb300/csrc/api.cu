@@ -179,6 +179,7 @@ int tim_destroy(tim_ctx* ctx) {
     DevBuf* bufs[] = {&ctx->rowptr,   &ctx->src,        &ctx->thr,       &ctx->pool,
                       &ctx->node_thr,  &ctx->qtab,      &ctx->ld_keys,   &ctx->ld_vals,
                       &ctx->ld_indeg,  &ctx->ld_lt_t,   &ctx->ld_lt_e,   &ctx->ld_nonuni,
+                      &ctx->ld_srcof,
                       &ctx->pool_sid, &ctx->set_start,  &ctx->set_len,   &ctx->set_width,
                       &ctx->counts,   &ctx->node_off,   &ctx->cursor,    &ctx->node_sets,
                       &ctx->covered,  &ctx->chosen,     &ctx->best,      &ctx->seed_mark,

@@ -116,7 +116,7 @@ struct tim_ctx {
     int last_team = 1;
 
     // graph-load temporaries (graph.cu), kept between loads
-    DevBuf ld_keys, ld_vals, ld_indeg, ld_lt_t, ld_lt_e, ld_nonuni;
+    DevBuf ld_keys, ld_vals, ld_indeg, ld_lt_t, ld_lt_e, ld_nonuni, ld_srcof;
 
     // forward cascades (spread.cu): G as out-records {in-CSR position, destination},
     // built from G^T on first use; per-block visited bitmaps (kept all-zero between

@@ -24,9 +24,15 @@ __global__ void check_rowptr_kernel(const int64_t* __restrict__ rowptr, int64_t 
     }
 }
 
-__global__ void keys_iota_kernel(const int32_t* __restrict__ dst, int64_t m, int64_t n,
+// Sort input (destination, edge id) per out-CSR edge, and the source of every edge: one
+// warp per source node u strides over its out-edges. The offsets are checked by
+// check_rowptr_kernel only at the end of the load, so they are clamped to [0, m) here
+// (an invalid graph is rejected; its sources are never used).
+__global__ void keys_iota_kernel(const int64_t* __restrict__ rowptr,
+                                 const int32_t* __restrict__ dst, int64_t n, int64_t m,
                                  uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                 uint32_t* __restrict__ indeg, int* __restrict__ err) {
+                                 uint32_t* __restrict__ srcof, uint32_t* __restrict__ indeg,
+                                 int* __restrict__ err) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         int32_t v = dst[e];
@@ -38,23 +44,16 @@ __global__ void keys_iota_kernel(const int32_t* __restrict__ dst, int64_t m, int
         vals[e] = (uint32_t)e;
         atomicAdd(&indeg[v], 1u);
     }
-}
-
-// Source of out-CSR edge e: the u with rowptr[u] <= e < rowptr[u+1].
-__device__ __forceinline__ uint32_t source_of(const int64_t* __restrict__ rowptr, int64_t n,
-                                              int64_t e) {
-    int64_t lo = 0, hi = n;  // answer in [lo, hi)
-    while (hi - lo > 1) {
-        int64_t mid = (lo + hi) >> 1;
-        if (rowptr[mid] <= e)
-            lo = mid;
-        else
-            hi = mid;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
+        const int64_t b = min(max(rowptr[u], (int64_t)0), m);
+        const int64_t f = min(max(rowptr[u + 1], b), m);
+        for (int64_t e = b + lane; e < f; e += 32) srcof[e] = (uint32_t)u;
     }
-    return (uint32_t)lo;
 }
 
-__global__ void fill_in_edges_kernel(const int64_t* __restrict__ out_rowptr, int64_t n, int64_t m,
+__global__ void fill_in_edges_kernel(const uint32_t* __restrict__ srcof, int64_t n, int64_t m,
                                      const uint32_t* __restrict__ sorted_dst,
                                      const uint32_t* __restrict__ sorted_eid,
                                      const float* __restrict__ w, int model,
@@ -65,7 +64,11 @@ __global__ void fill_in_edges_kernel(const int64_t* __restrict__ out_rowptr, int
          pos += (int64_t)gridDim.x * blockDim.x) {
         uint32_t e = sorted_eid[pos];
         uint32_t v = sorted_dst[pos];
-        uint32_t u = source_of(out_rowptr, n, (int64_t)e);
+        uint32_t u = srcof[e];
+        if (u >= (uint64_t)n) {  // offsets that miss this edge (an invalid graph)
+            atomicOr(err, TIM_DEV_ERR_GRAPH);
+            u = 0;
+        }
         if (u == v) atomicOr(err, TIM_DEV_ERR_GRAPH);
         src[pos] = u;
         float p = w[e];
@@ -201,11 +204,13 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
     DevBuf& lt_t = ctx->ld_lt_t;
     DevBuf& lt_e = ctx->ld_lt_e;
     DevBuf& nonuni = ctx->ld_nonuni;
+    DevBuf& srcof = ctx->ld_srcof;
     int rc = TIM_OK;
     do {
         if ((rc = tim_ensure(ctx, keys, (size_t)(m + 1) * sizeof(uint32_t)))) break;
         if ((rc = tim_ensure(ctx, vals, (size_t)(m + 1) * sizeof(uint32_t)))) break;
         if ((rc = tim_ensure(ctx, indeg, (size_t)(n + 1) * sizeof(uint32_t)))) break;
+        if ((rc = tim_ensure(ctx, srcof, (size_t)(m + 1) * sizeof(uint32_t)))) break;
         if (model == TIM_LT &&
             (rc = tim_ensure(ctx, lt_t, (size_t)(m + 1) * sizeof(unsigned long long))))
             break;
@@ -215,9 +220,9 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
         check_rowptr_kernel<<<G, T, 0, ctx->stream>>>(d_rowptr, n, m, &ds->err);
         ctx->launches++;
         if (m > 0) {
-            keys_iota_kernel<<<G, T, 0, ctx->stream>>>(d_dst, m, n, (uint32_t*)keys.p,
-                                                       (uint32_t*)vals.p, (uint32_t*)indeg.p,
-                                                       &ds->err);
+            keys_iota_kernel<<<G, T, 0, ctx->stream>>>(d_rowptr, d_dst, n, m, (uint32_t*)keys.p,
+                                                       (uint32_t*)vals.p, (uint32_t*)srcof.p,
+                                                       (uint32_t*)indeg.p, &ds->err);
             ctx->launches++;
             int bits = 0;
             while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
@@ -230,7 +235,8 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
             break;
         if (m > 0) {
             fill_in_edges_kernel<<<G, T, 0, ctx->stream>>>(
-                d_rowptr, n, m, (const uint32_t*)keys.p, (const uint32_t*)vals.p, d_w, model,
+                (const uint32_t*)srcof.p, n, m, (const uint32_t*)keys.p, (const uint32_t*)vals.p, d_w,
+                model,
                 (uint32_t*)ctx->src.p, (uint32_t*)ctx->thr.p, (unsigned long long*)lt_t.p,
                 &ds->err);
             ctx->launches++;
