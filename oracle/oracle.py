@@ -278,7 +278,7 @@ def kappa_sum(g: OracleGraph, k: int, seed: int, sid0: int, count: int, nthreads
 
 
 def greedy(n: int, off, mem, k: int):
-    """Greedy max coverage (Algorithm 1 lines 3-7): (seeds, covered count,
+    """Greedy max coverage (the selection of Algorithm 1): (seeds, covered count,
     first-round coverage counts)."""
     off = np.ascontiguousarray(off, dtype=np.int64)
     mem = np.ascontiguousarray(mem, dtype=np.int32)
@@ -407,22 +407,22 @@ class RefineResult:
 
 def refine_kpt(g: OracleGraph, k: int, ell: float, eps: float, seed: int, kpt: KptResult,
                nthreads: int = 0, tag: int = 0) -> RefineResult:
-    # line 1: R' = the RR sets of the last iteration of Algorithm 2
+    # R' = the RR sets of the last iteration of Algorithm 2
     if kpt.last_round > 0:
         off, mem, _ = sample(g, seed, make_sid(PHASE_KPT, kpt.last_round, tag << 32), kpt.last_c,
                              nthreads)
     else:
         off, mem = np.zeros(1, dtype=np.int64), np.zeros(0, dtype=np.int32)
-    # lines 2-6: greedy on R'
+    # greedy on R'
     seeds_p, _, _ = greedy(g.n, off, mem, k)
-    # lines 7-8
+    # eps' and theta'
     ep = eps_prime(eps, k, ell)
     lp = lam_prime(g.n, ep, ell)
     theta_p = int(math.ceil(lp / kpt.kpt_star))
-    # lines 9-10: fraction of theta' fresh RR sets covered by S'_k
+    # fraction of theta' fresh RR sets covered by S'_k
     cov = covered_count(g, seed, make_sid(PHASE_REFINE, 0, tag << 32), theta_p, seeds_p, nthreads)
     f = cov / theta_p
-    # lines 11-12
+    # KPT' and KPT+
     kpt_prime = f * g.n / (1.0 + ep)
     return RefineResult(kpt_plus=max(kpt_prime, kpt.kpt_star), kpt_prime=kpt_prime,
                         eps_prime=ep, theta_prime=theta_p, covered=cov, seeds_prime=seeds_p)

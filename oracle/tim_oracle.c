@@ -531,7 +531,7 @@ static int set_threads(int nthreads) {
 }
 
 /* Generate RR sets with ids sids(j) = sid0 + j, j in [0, count) (Algorithm 1,
- * lines 1-2). Writes a CSR-of-sets (off[count+1], mem) and optional widths.
+ * its sampling step). Writes a CSR-of-sets (off[count+1], mem) and optional widths.
  * Returns the total member count; if it exceeds mem_cap nothing is copied into mem
  * and the caller retries with a bigger buffer. Sets are independent, so chunks of
  * set ids may run on several host threads; the result does not depend on it. */
@@ -727,7 +727,7 @@ int or_kpt_estimate(const int64_t* rowptr, const int32_t* src, const uint32_t* t
 }
 
 /* ------------------------------------------------ greedy maximum coverage */
-/* The greedy of Algorithm 1 (lines 3-7) over a CSR-of-sets, written naively: every
+/* The greedy of Algorithm 1 over a CSR-of-sets, written naively: every
  * round recounts, for every node, the sets not yet covered that contain it, picks
  * the node with the largest count (ties: smallest id; chosen nodes excluded) and
  * marks the sets it covers. Returns the number of covered sets. */
@@ -771,7 +771,7 @@ int64_t or_greedy(int64_t n, int64_t n_sets, const int64_t* off, const int32_t* 
 }
 
 /* Number of RR sets sid0 .. sid0+count-1 that intersect the node set `in_s`
- * (n bytes, 1 = member): the covered count of Algorithm 3, line 10. */
+ * (n bytes, 1 = member): the covered count of Algorithm 3. */
 int64_t or_covered_count(const int64_t* rowptr, const int32_t* src, const uint32_t* thr,
                          int64_t n, int64_t m, int model, uint64_t seed, uint64_t sid0,
                          int64_t count, const uint8_t* in_s, int nthreads) {

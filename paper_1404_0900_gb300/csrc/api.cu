@@ -651,15 +651,15 @@ int tim_refine_kpt(tim_ctx* ctx, int k, double ell, double eps, uint64_t seed, d
     if (k < 1 || k > ctx->n || !(eps > 0.0) || !(ell > 0.0))
         return tim_fail(ctx, TIM_ERR_ARG, "need 1 <= k <= n, eps > 0, l > 0");
     DeviceGuard g(ctx->device);
-    // lines 1-6: greedy on R' (the store holds the last round of Algorithm 2)
+    // greedy on R' (the store holds the last round of Algorithm 2)
     TIM_TRY(tim_build_index(ctx));
     TIM_TRY(tim_greedy(ctx, k, nullptr, nullptr));
     TIM_TRY(tim_mark_seeds(ctx, (const int32_t*)ctx->seeds_dev.p, k));
-    // lines 7-8
+    // eps' and theta'
     const double ep = tim_host_eps_prime(eps, k, ell);
     const double lp = tim_host_lambda_prime(ctx->n, ep, ell);
     const uint64_t theta_p = (uint64_t)ceil(lp / ctx->kpt_star);
-    // lines 9-10
+    // the fraction of theta' fresh RR sets that S'_k covers
     SampleRequest req;
     req.seed = seed;
     req.sid0 = make_sid(2, 0, (uint64_t)ctx->query_tag << 32);
@@ -669,7 +669,7 @@ int tim_refine_kpt(tim_ctx* ctx, int k, double ell, double eps, uint64_t seed, d
     SampleResult res;
     TIM_TRY(tim_sample(ctx, req, &res));
     const double f = (double)res.covered / (double)theta_p;
-    // lines 11-12
+    // KPT' and KPT+
     ctx->ref_kpt_prime = f * (double)ctx->n / (1.0 + ep);
     ctx->ref_kpt_plus = std::max(ctx->ref_kpt_prime, ctx->kpt_star);
     ctx->ref_eps_prime = ep;

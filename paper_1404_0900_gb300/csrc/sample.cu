@@ -25,7 +25,7 @@
 //
 // Per set the kernels can (flags): EMIT the members into the RR-set store, sum KAPPA
 // (Eq. 6) in 2^-63 fixed point, and test COVER (does the set meet a given seed set;
-// Algorithm 3 lines 9-10; the BFS stops at the first member in the seed set).
+// the coverage test of Algorithm 3; the BFS stops at the first member in the seed set).
 #include <algorithm>
 #include <vector>
 

@@ -1,5 +1,5 @@
-// select.cu -- greedy maximum coverage over the RR-set store (Algorithm 1, lines 3-7;
-// also lines 2-6 of Algorithm 3).
+// select.cu -- greedy maximum coverage over the RR-set store (the selection of
+// Algorithm 1; also the greedy on R' of Algorithm 3).
 //
 // Index: coverage counts (how many stored sets contain each node) by a histogram over
 // the store, an exclusive scan into node offsets, and a scatter of set ids into

@@ -1,4 +1,4 @@
-"""Pins for the oracle's greedy maximum coverage (Algorithm 1, lines 3-7), RefineKPT
+"""Pins for the oracle's greedy maximum coverage (the selection of Algorithm 1), RefineKPT
 (Algorithm 3) and the TIM / TIM+ drivers (Sections 3.3 and 4.1)."""
 import itertools
 import math
