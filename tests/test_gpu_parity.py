@@ -162,6 +162,27 @@ def test_coverage_counts_and_covered_count(eng, model):
     assert c == O.covered_count(og, 21, O.make_sid(2, 0, 0), 25000, seeds[:3])
 
 
+@pytest.mark.parametrize("team", [1, 2, 4, 8])
+def test_covered_count_with_every_set_in_teams(eng, team):
+    # budget 0 hands every set, light or heavy, to the second pass, where teams of
+    # `team` warps stop each set at its first seed (Algorithm 3's coverage test)
+    g = inputs.rmat(13, seed=4)
+    w = inputs.weighted_cascade(g)
+    og = _load(eng, g, w, O.IC)
+    rng = np.random.default_rng(team)
+    try:
+        tim.tim_set_width_budget(eng.ctx, 0)
+        tim.tim_set_team_size(eng.ctx, team)
+        for seeds in ([0], rng.choice(g.n, 5, replace=False).tolist(),
+                      rng.choice(g.n, 60, replace=False).tolist()):
+            for count in (3000, 777):
+                c = tim.tim_covered_count(eng.ctx, seeds, 5, O.make_sid(2, 0, 9), count)
+                assert c == O.covered_count(og, 5, O.make_sid(2, 0, 9), count, seeds), (team, seeds)
+    finally:
+        tim.tim_set_width_budget(eng.ctx, 16384)
+        tim.tim_set_team_size(eng.ctx, 0)
+
+
 @pytest.mark.parametrize("k", [1, 3, 16])
 def test_greedy_ties_and_k_equals_n(eng, k):
     g = inputs.complete(16)
