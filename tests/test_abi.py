@@ -53,3 +53,19 @@ def test_create_fails_cleanly_without_device(monkeypatch):
         pytest.skip("a GPU is present")
     with pytest.raises(tim.TimError):
         tim.tim_create(0)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    # no fallback: without libtim.so the binding raises instead of computing anything
+    monkeypatch.setattr(B, "LIB", "/nonexistent/libtim.so")
+    monkeypatch.setattr(tim, "_lib", None)
+    with pytest.raises(OSError):
+        tim.lib(build_if_missing=False)
+
+
+def test_product_package_never_imports_the_oracle():
+    pkg = os.path.dirname(os.path.abspath(tim.__file__))
+    for name in os.listdir(pkg):
+        if name.endswith(".py"):
+            text = open(os.path.join(pkg, name)).read()
+            assert "import oracle" not in text and "from oracle" not in text, name
