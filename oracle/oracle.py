@@ -48,6 +48,10 @@ def lib():
             "or_lt_thresholds": (i32, [i64, P, P, P]),
             "or_rr_by_definition": (i64, [P, P, P, i64, i64, i32, u64, u64, P, P]),
             "or_rr_one": (i64, [P, P, P, i64, i64, i32, u64, u64, P, P]),
+            "or_rr_one_mode": (i64, [P, P, P, i64, i64, i32, i32, u64, u64, P, P]),
+            "or_rr_by_definition_mode": (i64, [P, P, P, i64, i64, i32, i32, u64, u64, P, P]),
+            "or_sample_mode": (i64, [P, P, P, i64, i64, i32, i32, u64, u64, i64, P, P, i64, P,
+                                     i32]),
             "or_kappa": (dbl, [i64, i64, i32]),
             "or_kappa_fixed": (u64, [dbl]),
             "or_sample": (i64, [P, P, P, i64, i64, i32, u64, u64, i64, P, P, i64, P, i32]),
@@ -229,35 +233,39 @@ def load_graph(n: int, rowptr, dst, weight, model: int) -> OracleGraph:
 
 # ------------------------------------------------------------------- RR sets
 
-def rr_one(g: OracleGraph, seed: int, sid: int):
-    """One RR set by randomised BFS: (sorted members, width)."""
+def rr_one(g: OracleGraph, seed: int, sid: int, per_edge: bool = False):
+    """One RR set by randomised BFS: (sorted members, width). per_edge: one coin per
+    in-edge in every list, without the geometric-skip rule (Section 3.1 as printed;
+    for statistical checks of the rule only)."""
     buf = np.zeros(g.n, dtype=np.int32)
     w = np.zeros(1, dtype=np.int64)
-    cnt = lib().or_rr_one(*g.args(), seed, sid, _p(buf), _p(w))
+    cnt = lib().or_rr_one_mode(*g.args(), int(per_edge), seed, sid, _p(buf), _p(w))
     if cnt < 0:
         raise MemoryError
     return np.sort(buf[:cnt]), int(w[0])
 
 
-def rr_by_definition(g: OracleGraph, seed: int, sid: int):
+def rr_by_definition(g: OracleGraph, seed: int, sid: int, per_edge: bool = False):
     """The same RR set from Definitions 1-2 (whole random graph drawn first)."""
     buf = np.zeros(g.n, dtype=np.int32)
     w = np.zeros(1, dtype=np.int64)
-    cnt = lib().or_rr_by_definition(*g.args(), seed, sid, _p(buf), _p(w))
+    cnt = lib().or_rr_by_definition_mode(*g.args(), int(per_edge), seed, sid, _p(buf), _p(w))
     if cnt < 0:
         raise MemoryError
     return buf[:cnt].copy(), int(w[0])
 
 
-def sample(g: OracleGraph, seed: int, sid0: int, count: int, nthreads: int = 0):
-    """RR sets sid0 .. sid0+count-1 as (off int64[count+1], mem int32, widths int64)."""
+def sample(g: OracleGraph, seed: int, sid0: int, count: int, nthreads: int = 0,
+           per_edge: bool = False):
+    """RR sets sid0 .. sid0+count-1 as (off int64[count+1], mem int32, widths int64).
+    per_edge: see rr_one."""
     off = np.zeros(count + 1, dtype=np.int64)
     widths = np.zeros(max(count, 1), dtype=np.int64)
     cap = max(16, count * 8)
     while True:
         mem = np.zeros(cap, dtype=np.int32)
-        tot = lib().or_sample(*g.args(), seed, sid0, count, _p(off), _p(mem), cap, _p(widths),
-                              nthreads)
+        tot = lib().or_sample_mode(*g.args(), int(per_edge), seed, sid0, count, _p(off), _p(mem),
+                                   cap, _p(widths), nthreads)
         if tot < 0:
             raise MemoryError
         if tot <= cap:

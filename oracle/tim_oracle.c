@@ -33,7 +33,11 @@
  *     drawing the geometric gaps between them (see skip_iter below). Each in-edge is
  *     still live with probability t / 2^32, independently (to within 2^-60 per gap
  *     digit). The bound on t keeps the rule to lists where a few gaps replace many
- *     coins.
+ *     coins. This rule and its random-number layout are frozen: the law of the
+ *     sets it gives is checked against the per-edge mode (one coin per in-edge in
+ *     every list, Section 3.1 as printed; or_sample_mode with per_edge = 1) by
+ *     whole-graph statistics, and any change to either lands in an oracle-only change
+ *     with its pins before a kernel follows it.
  *   - LT pick: t_j = floor(w_j * 2^32); C_j = inclusive prefix of t over v's
  *     in-edges in in-CSR order, saturated at 2^32 - 1; the first j with x < C_j is
  *     the triggering in-edge, none if x >= C_last.
@@ -222,6 +226,7 @@ typedef struct {
     const int32_t* src;    /* in-CSR sources, m */
     const uint32_t* thr;   /* IC thresholds or LT cumulative thresholds, m */
     int model;
+    int per_edge; /* 1: one coin per in-edge in every IC list (no geometric skipping) */
 } or_graph;
 
 static int64_t indeg(const or_graph* g, int64_t v) { return g->rowptr[v + 1] - g->rowptr[v]; }
@@ -311,9 +316,12 @@ int64_t or_skip_live(uint64_t seed, uint64_t sid, int64_t beg, int64_t d, uint32
     return n;
 }
 
-/* Does v's in-list take the skip rule? Then *t is its shared threshold. */
+/* Does v's in-list take the skip rule? Then *t is its shared threshold. In the
+ * per-edge mode no list does: every in-edge draws its own coin, as Section 3.1 states
+ * the procedure. That mode exists only to check, by statistics over whole graphs, that
+ * the skip rule gives RR sets of the same law; it is never compared with the GPU. */
 static int skip_list(const or_graph* g, int64_t v, uint32_t* t) {
-    if (g->model != MODEL_IC) return 0;
+    if (g->model != MODEL_IC || g->per_edge) return 0;
     int64_t a = g->rowptr[v], b = g->rowptr[v + 1], d = b - a;
     if (d < SKIP_MIN_INDEG) return 0;
     uint32_t t0 = g->thr[a];
@@ -389,10 +397,11 @@ static int64_t rr_bfs(const or_graph* g, uint64_t seed, uint64_t sid, int32_t* m
  * as a plain edge list, then take the closure "u can reach the root in g" by
  * repeated passes over that list until nothing changes. Independent of any search
  * order. Returns |R|; members are written in ascending id order. */
-int64_t or_rr_by_definition(const int64_t* rowptr, const int32_t* src, const uint32_t* thr,
-                            int64_t n, int64_t m, int model, uint64_t seed, uint64_t sid,
-                            int32_t* members, int64_t* width) {
-    or_graph g = {n, m, rowptr, src, thr, model};
+int64_t or_rr_by_definition_mode(const int64_t* rowptr, const int32_t* src,
+                                 const uint32_t* thr, int64_t n, int64_t m, int model,
+                                 int per_edge, uint64_t seed, uint64_t sid, int32_t* members,
+                                 int64_t* width) {
+    or_graph g = {n, m, rowptr, src, thr, model, per_edge};
     int64_t* lu = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
     int64_t* lv = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
     uint8_t* in_r = (uint8_t*)calloc((size_t)n, 1);
@@ -405,7 +414,7 @@ int64_t or_rr_by_definition(const int64_t* rowptr, const int32_t* src, const uin
     int64_t nl = 0;
     for (int64_t v = 0; v < n; v++) {
         uint32_t t;
-        if (model == MODEL_IC && skip_list(&g, v, &t)) {
+        if (skip_list(&g, v, &t)) {
             skip_iter it;
             int64_t rel;
             skip_begin(&it, seed, sid, rowptr[v], rowptr[v + 1] - rowptr[v], t);
@@ -453,16 +462,28 @@ int64_t or_rr_by_definition(const int64_t* rowptr, const int32_t* src, const uin
     return cnt;
 }
 
-/* One RR set by BFS, exported for single-set checks. */
-int64_t or_rr_one(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
-                  int64_t m, int model, uint64_t seed, uint64_t sid, int32_t* members,
-                  int64_t* width) {
-    or_graph g = {n, m, rowptr, src, thr, model};
+int64_t or_rr_by_definition(const int64_t* rowptr, const int32_t* src, const uint32_t* thr,
+                            int64_t n, int64_t m, int model, uint64_t seed, uint64_t sid,
+                            int32_t* members, int64_t* width) {
+    return or_rr_by_definition_mode(rowptr, src, thr, n, m, model, 0, seed, sid, members, width);
+}
+
+/* One RR set by BFS, exported for single-set checks (per_edge: see skip_list). */
+int64_t or_rr_one_mode(const int64_t* rowptr, const int32_t* src, const uint32_t* thr,
+                       int64_t n, int64_t m, int model, int per_edge, uint64_t seed,
+                       uint64_t sid, int32_t* members, int64_t* width) {
+    or_graph g = {n, m, rowptr, src, thr, model, per_edge};
     uint8_t* mark = (uint8_t*)calloc((size_t)n, 1);
     if (!mark) return OR_ERR_OOM;
     int64_t r = rr_bfs(&g, seed, sid, members, mark, width);
     free(mark);
     return r;
+}
+
+int64_t or_rr_one(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
+                  int64_t m, int model, uint64_t seed, uint64_t sid, int32_t* members,
+                  int64_t* width) {
+    return or_rr_one_mode(rowptr, src, thr, n, m, model, 0, seed, sid, members, width);
 }
 
 /* ---------------------------------------------------------- kappa, Eq. 6 */
@@ -535,10 +556,11 @@ static int set_threads(int nthreads) {
  * Returns the total member count; if it exceeds mem_cap nothing is copied into mem
  * and the caller retries with a bigger buffer. Sets are independent, so chunks of
  * set ids may run on several host threads; the result does not depend on it. */
-int64_t or_sample(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
-                  int64_t m, int model, uint64_t seed, uint64_t sid0, int64_t count,
-                  int64_t* off, int32_t* mem, int64_t mem_cap, int64_t* widths, int nthreads) {
-    or_graph g = {n, m, rowptr, src, thr, model};
+int64_t or_sample_mode(const int64_t* rowptr, const int32_t* src, const uint32_t* thr,
+                       int64_t n, int64_t m, int model, int per_edge, uint64_t seed,
+                       uint64_t sid0, int64_t count, int64_t* off, int32_t* mem,
+                       int64_t mem_cap, int64_t* widths, int nthreads) {
+    or_graph g = {n, m, rowptr, src, thr, model, per_edge};
     if (count < 0) return OR_ERR_ARG;
     off[0] = 0;
     if (count == 0) return 0;
@@ -605,6 +627,13 @@ int64_t or_sample(const int64_t* rowptr, const int32_t* src, const uint32_t* thr
     }
     free(bufs);
     return fail ? OR_ERR_OOM : total;
+}
+
+int64_t or_sample(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
+                  int64_t m, int model, uint64_t seed, uint64_t sid0, int64_t count,
+                  int64_t* off, int32_t* mem, int64_t mem_cap, int64_t* widths, int nthreads) {
+    return or_sample_mode(rowptr, src, thr, n, m, model, 0, seed, sid0, count, off, mem, mem_cap,
+                          widths, nthreads);
 }
 
 /* Sum of kappa over RR sets sid0 .. sid0+count-1 in 2^-63 fixed point, as a

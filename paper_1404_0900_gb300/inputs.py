@@ -136,6 +136,22 @@ def chung_lu(n: int, m_target: int, gamma: float = 2.1, seed: int = 1,
     return csr_from_pairs(n, s, d, name=f"chunglu{n}")
 
 
+def mixed_in_degree(n: int, hub_range=(512, 1023), light_range=(1, 64), seed: int = 1) -> Graph:
+    """Directed graph whose even nodes have in-degree drawn uniformly from hub_range and
+    odd nodes from light_range, each in-neighbour set drawn uniformly at random among
+    the other nodes (a graph with thousands of long in-lists beside short ones)."""
+    rng = _rng(seed)
+    src, dst = [], []
+    for v in range(n):
+        lo, hi = hub_range if v % 2 == 0 else light_range
+        d = int(rng.integers(lo, hi + 1))
+        u = rng.choice(n - 1, size=d, replace=False)
+        u = u + (u >= v)  # skip v itself
+        src.append(u)
+        dst.append(np.full(d, v, dtype=np.int64))
+    return csr_from_pairs(n, np.concatenate(src), np.concatenate(dst), name=f"mixed{n}")
+
+
 def from_edges(n: int, edges, name: str = "") -> Graph:
     """Graph from an explicit list of (u, v) pairs (u -> v)."""
     if len(edges) == 0:
