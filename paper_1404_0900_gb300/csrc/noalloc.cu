@@ -9,9 +9,11 @@
 // 13.3 MiB), which every GPU that loads the library holds until the process exits. Host code
 // cannot use the array's name as a device address, so the first call on each device
 // looks the address up with cudaGetSymbolAddress (with that device current) and keeps
-// it; that first call should come before any stream capture. Every call shares the
-// array and leaves its contents behind: each call clears what must start at zero, and
-// calls whose work overlaps on the GPU (other streams, other host threads) race.
+// it; make that first call before any stream capture. Every call also reads two
+// offsets back to the host and waits for its stream. Every call shares the array and
+// leaves its contents behind: each call clears what must start at zero, and calls
+// whose work overlaps on the GPU (other streams, other host threads) race. Members
+// must be distinct within a set; a repeated member is not detected.
 #include <mutex>
 
 #include "common.cuh"

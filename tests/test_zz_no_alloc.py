@@ -58,3 +58,51 @@ def test_noalloc_rejects_sizes_beyond_its_limits():
         with pytest.raises(tim.TimError) as ei:
             tim.tim_node_select_noalloc(0, None, n, n_sets, d_off, d_mem, k, d_seeds, d_cov)
         assert ei.value.code == -1
+
+
+def test_noalloc_call_takes_no_device_memory():
+    """After a first call (which looks up the array's address), further calls leave the
+    device's free memory unchanged: they allocate nothing."""
+    import torch
+    from paper_1404_0900_gb300 import tim
+    n, k, off, mem, seeds, cov = _reference_selections()["b"]
+    d_off = torch.from_numpy(off).cuda()
+    d_mem = torch.from_numpy(mem).cuda()
+    d_seeds = torch.zeros(k, dtype=torch.int32, device="cuda")
+    d_cov = torch.zeros(1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream()
+    call = lambda: tim.tim_node_select_noalloc(0, stream, n, off.shape[0] - 1, d_off, d_mem, k,
+                                               d_seeds, d_cov)
+    call()
+    torch.cuda.synchronize()
+    same = False
+    for _ in range(3):  # another process on the device could move the figure: retry
+        free0, _ = torch.cuda.mem_get_info()
+        call()
+        call()
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        if free1 == free0:
+            same = True
+            break
+    assert same, (free0, free1)
+    assert np.array_equal(d_seeds.cpu().numpy(), seeds) and int(d_cov.item()) == cov
+
+
+def test_noalloc_member_out_of_range_and_no_sets():
+    import torch
+    from paper_1404_0900_gb300 import tim
+    n, k = 100, 5
+    d_seeds = torch.full((k,), -1, dtype=torch.int32, device="cuda")
+    d_cov = torch.zeros(1, dtype=torch.int64, device="cuda")
+    # a member equal to n: checked after the run, reported as an argument error
+    d_off = torch.tensor([0, 2, 3], dtype=torch.int64, device="cuda")
+    d_mem = torch.tensor([1, n, 7], dtype=torch.int32, device="cuda")
+    with pytest.raises(tim.TimError) as ei:
+        tim.tim_node_select_noalloc(0, None, n, 2, d_off, d_mem, k, d_seeds, d_cov)
+    assert ei.value.code == -1
+    # no RR sets: nothing is covered and the smallest ids are the seeds
+    d_off = torch.zeros(1, dtype=torch.int64, device="cuda")
+    tim.tim_node_select_noalloc(0, None, n, 0, d_off, d_mem, k, d_seeds, d_cov)
+    torch.cuda.synchronize()
+    assert d_seeds.cpu().tolist() == list(range(k)) and int(d_cov.item()) == 0
