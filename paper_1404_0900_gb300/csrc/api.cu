@@ -224,6 +224,26 @@ int tim_set_chunk(tim_ctx* ctx, int sets) {
     return TIM_OK;
 }
 
+int tim_set_pass2_budget(tim_ctx* ctx, uint64_t budget) {
+    if (!ctx) return TIM_ERR_ARG;
+    ctx->width_budget2 = budget;
+    return TIM_OK;
+}
+
+int tim_set_wait_limit(tim_ctx* ctx, uint32_t polls) {
+    if (!ctx) return TIM_ERR_ARG;
+    ctx->wait_limit = polls;
+    return TIM_OK;
+}
+
+int tim_set_heavy_pass(tim_ctx* ctx, int stepped) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (stepped != 0 && stepped != 1)
+        return tim_fail(ctx, TIM_ERR_ARG, "heavy-pass mode must be 0 or 1");
+    ctx->bulk_stepped = stepped != 0;
+    return TIM_OK;
+}
+
 int tim_set_team_size(tim_ctx* ctx, int warps) {
     if (!ctx) return TIM_ERR_ARG;
     if (warps != 0 && warps != 1 && warps != 2 && warps != 4 && warps != 8)

@@ -99,11 +99,18 @@ struct tim_ctx {
 
     // batched second pass for heavy IC sets (sample_bulk.cu)
     DevBuf bulk_bitmap, bulk_slot, bulk_F, bulk_M, bulk_ng, bulk_gp, bulk_scal;
+    DevBuf bulk_bsum, bulk_bar;  // persistent launch: per-block sums, grid barrier
+    DevBuf bulk_info;            // per frontier item: in-list, set slot, set index
+    // run the heavy-set levels as host-stepped launches instead of one persistent launch
+    bool bulk_stepped = false;
     bool bulk_bitmap_clean = false;
     uint64_t bulk_fcap = 0, bulk_mcap = 0;
     // IC first pass: a warp gives a set to the second pass once its examined in-edges
     // would exceed this many
     unsigned long long width_budget = 16384;
+    // IC second pass: a team gives a set to the heavy-set pass once its examined
+    // in-edges would exceed this many
+    unsigned long long width_budget2 = ~0ull;
     // IC tier 2: warps per RR set (1, 2, 4 or 8); 0 = chosen from the number of sets
     int team_size = 0;
     // sets claimed per work-counter increment in tiers 1 and 2
@@ -111,6 +118,9 @@ struct tim_ctx {
     // set-id tag of this context's runs: ids are (phase << 56) | (round << 48) |
     // (tag << 32) | j
     uint32_t query_tag = 0;
+    // polls a block makes at a grid barrier of a persistent kernel before it gives up
+    // (the call then fails with TIM_ERR_TIMEOUT)
+    unsigned wait_limit = 1u << 24;
     // batch scratch (owner of a multi-query launch / batched greedy)
     DevBuf batch, greedy_batch;
     int last_team = 1;
@@ -436,6 +446,45 @@ __device__ __forceinline__ double kappa_fp64(unsigned long long w, unsigned long
 // kappa in 2^-63 fixed point, truncated toward zero.
 __device__ __forceinline__ unsigned long long kappa_fixed(double kappa) {
     return __double2ull_rz(__dmul_rn(kappa, 9223372036854775808.0));
+}
+
+// Barrier over all blocks of a co-resident (cooperative) launch: sense reversal on a
+// generation counter, which the host zeroes before each launch. The wait is bounded:
+// after `limit` polls a block sets TIM_DEV_ERR_TIMEOUT in *err and the barrier returns
+// false; it also returns false once any block has set that bit, so every block of the
+// launch stops within one barrier of the first timeout.
+struct GridBarrier {
+    unsigned count;
+    unsigned gen;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBarrier* bar, int* err, unsigned limit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        __threadfence();
+        const unsigned g = ((volatile unsigned*)&bar->gen)[0];
+        if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            atomicAdd(&bar->gen, 1u);
+        } else {
+            unsigned it = 0;
+            while (((volatile unsigned*)&bar->gen)[0] == g && it < limit) {
+                __nanosleep(64);
+                it++;
+            }
+            if (((volatile unsigned*)&bar->gen)[0] == g) {
+                atomicOr(err, TIM_DEV_ERR_TIMEOUT);
+                ok = 0;
+            }
+        }
+        __threadfence();
+        s_ok = ok && !(((volatile int*)err)[0] & TIM_DEV_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    return s_ok != 0;
 }
 
 // Add a 128-bit (hi, lo) into a global 128-bit accumulator.

@@ -77,6 +77,7 @@ struct SampleArgs {
     uint32_t* big_queue;
     uint64_t big_words;
     unsigned long long width_budget;  // tier 1 IC: in-edges one warp may examine per set
+    unsigned long long width_budget2; // tier 2 IC: in-edges one team may examine per set
     int chunk;                        // sets claimed per work-counter increment
     uint32_t* lt_col;                 // tier 1 LT: per-thread member columns
 };
@@ -463,7 +464,7 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
     uint16_t* slot = reinterpret_cast<uint16_t*>(queue + C::Q);
     int* ctl = TIER == 1 ? reinterpret_cast<int*>(queue + C::Q + C::Q / 2) : s_ctl[team];
     const unsigned long long budget =
-        (TIER == 1 && MODEL == TIM_IC) ? a.width_budget : ~0ull;
+        MODEL != TIM_IC ? ~0ull : TIER == 1 ? a.width_budget : a.width_budget2;
     unsigned long long* counter = TIER == 1 ? &a.ds->next_set : &a.ds->next2;
     const uint64_t items =
         TIER == 1 ? a.count : (uint64_t)min(((volatile unsigned*)&a.ds->cnt1)[0], a.list_cap);
@@ -986,7 +987,7 @@ struct QueryDesc {
     uint32_t* set_len;
     uint64_t* set_width;
     DevScalars* ds;
-    unsigned long long width_budget;
+    unsigned long long width_budget, width_budget2;
 };
 
 struct MultiArgs {
@@ -1114,7 +1115,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
                            d.n,      d.m,   d.flags, d.k,     d.seed_mark};
             const int model = d.model;
             const unsigned long long budget =
-                (TIER == 1 && model == TIM_IC) ? d.width_budget : ~0ull;
+                model != TIM_IC ? ~0ull : TIER == 1 ? d.width_budget : d.width_budget2;
             unsigned long long width;
             int st;
             if (model == TIM_IC)
@@ -1496,6 +1497,7 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
     a.set_len = (uint32_t*)ctx->set_len.p;
     a.set_width = (uint64_t*)ctx->set_width.p;
     a.width_budget = ctx->width_budget;
+    a.width_budget2 = ctx->width_budget2;
     a.chunk = std::max(1, ctx->chunk);
     for (int attempt = 0; attempt < 4; attempt++) {
         a.pool = (uint32_t*)ctx->pool.p;
@@ -1790,6 +1792,7 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
             d.set_width = (uint64_t*)c->set_width.p;
             d.ds = d_scal + i;
             d.width_budget = c->width_budget;
+            d.width_budget2 = c->width_budget2;
         }
         CUDA_TRY(owner, cudaMemcpyAsync(d_desc, h_desc.data(), (size_t)nq * sizeof(QueryDesc),
                                         cudaMemcpyHostToDevice, owner->stream));

@@ -21,6 +21,16 @@
 // After the last level, each slot's set is reduced (kappa), counted (cover) or copied
 // into the RR-set store (emit), and the visited bits are cleared through the member
 // list.
+//
+// The levels of a batch run in one persistent cooperative launch (bulk_levels_kernel):
+// per level, (A) every block computes the group counts of a contiguous range of items
+// and their sum, (B) every block turns its range into global group offsets from the sums
+// of the blocks before it, (C) all warps expand the level; a bounded grid barrier
+// separates the phases, so a level costs three barriers instead of a launch sequence
+// and a host round trip. Frontier items, group offsets and block sums written during
+// the launch are read with __ldcg (L2, not the SM's L1, which other SMs' writes do not
+// update). Without cooperative launch support the same phases run as separate kernels
+// stepped by the host.
 #include <algorithm>
 
 #include "common.cuh"
@@ -31,6 +41,9 @@ struct BulkScalars {
     unsigned long long f_count;  // frontier items appended (all levels)
     unsigned long long m_count;  // members appended
     unsigned long long live;     // live in-edges followed
+    unsigned long long exam;     // in-edges whose own coin was drawn
+    // persistent launch, block 0: levels and nanoseconds in phases A + B, in C, at barriers
+    unsigned long long levels, ns_offsets, ns_expand, ns_wait;
     int err;                     // bit 0: F overflow, bit 1: M overflow
     int pad;
 };
@@ -61,8 +74,12 @@ struct BulkArgs {
     uint64_t mcap;
     BulkScalars* bs;
     uint64_t lvl_lo, lvl_n;  // current level: F[lvl_lo .. lvl_lo + lvl_n)
-    const uint32_t* ng;
-    const uint64_t* gp;  // exclusive group prefix of the level, gp[lvl_n] = total
+    uint32_t* ng;        // group count of each item of the level (bit 31: skip-rule item)
+    uint4* info;         // record of each item of the level (item_prepare)
+    uint64_t* gp;        // exclusive group prefix of the level, gp[lvl_n] = total
+    unsigned long long* bsum;  // persistent launch: one group sum per block
+    GridBarrier* bar;          // persistent launch: grid barrier, zeroed before the launch
+    unsigned wait_limit;       // polls per barrier wait
     // outputs shared with the first pass
     DevScalars* ds;
     uint32_t* pool;
@@ -75,6 +92,18 @@ struct BulkArgs {
 
 __device__ __forceinline__ bool marked(const uint32_t* mark, uint32_t u) {
     return (__ldg(mark + (u >> 5)) >> (u & 31)) & 1u;
+}
+
+#ifdef BULK_TRACE
+// per-level record of block 0 (timing builds only): items, groups, ns of A, B, C, wait
+__device__ unsigned long long bulk_trace[1 << 16][6];
+__device__ unsigned long long bulk_trace_n;
+#endif
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ uint32_t pick4(uint4 v, int c) {
@@ -113,15 +142,26 @@ __device__ __forceinline__ bool skip_rule(unsigned long long nt, uint64_t beg, u
     return tim_skip_rule(nt, end - beg);
 }
 
-__global__ void bulk_ng_kernel(BulkArgs a, uint32_t* ng) {
+constexpr uint32_t NG_SKIP = 0x80000000u;
+
+// Groups of frontier item F[lo + i]: the 4-aligned groups of its in-list, or one
+// placeholder group (flagged NG_SKIP) for a list under the skip rule. Also stores the
+// item's record for the expand phase, info[i] = (first in-CSR position of the in-list,
+// end position, set slot | skip flag << 31, index of the set in the heavy list).
+__device__ __forceinline__ uint32_t item_prepare(const BulkArgs& a, uint64_t lo, uint64_t i) {
+    const uint2 it = __ldcg(&a.F[lo + i]);
+    const uint64_t beg = __ldg(a.rowptr + it.y), end = __ldg(a.rowptr + it.y + 1);
+    const bool skip = skip_rule(__ldg(a.node_thr + it.y), beg, end);
+    a.info[i] = make_uint4((uint32_t)beg, (uint32_t)end, it.x | (skip ? 0x80000000u : 0u),
+                           __ldg(a.list + a.base + it.x));
+    return skip ? (1u | NG_SKIP) : (uint32_t)(((end - 1) >> 2) - (beg >> 2) + 1);  // end > beg
+}
+
+// Host-stepped path: group counts of the level without the skip flag (the scan input).
+__global__ void bulk_ng_kernel(BulkArgs a) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.lvl_n;
-         i += (uint64_t)gridDim.x * blockDim.x) {
-        const uint32_t v = a.F[a.lvl_lo + i].y;
-        const uint64_t beg = a.rowptr[v], end = a.rowptr[v + 1];
-        ng[i] = skip_rule(a.node_thr[v], beg, end)
-                    ? 1u  // placeholder, ignored by bulk_expand_kernel
-                    : (uint32_t)(((end - 1) >> 2) - (beg >> 2) + 1);  // end > beg here
-    }
+         i += (uint64_t)gridDim.x * blockDim.x)
+        a.ng[i] = item_prepare(a, a.lvl_lo, i) & ~NG_SKIP;
 }
 
 // Warp-aggregated append of (slot, node) to one of the lists; returns nothing.
@@ -143,187 +183,308 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t s, uint32_t u,
     }
 }
 
-// Appends of one block staged in shared memory: a warp reserves buffer space with a
-// shared atomic, and the block reserves the global range once, at its end (a list's
-// global counter is one address for the whole GPU: one atomic per warp and step there
-// serialises). Appends that do not fit go to the global list directly.
-constexpr unsigned STAGE = 1024;
-struct Stage {
-    uint2 f[STAGE];
-    uint2 m[STAGE];
-    unsigned nf, nm;
-    unsigned long long gf, gm;
+// Appends of one warp staged in shared memory and copied to the global list in runs of
+// up to WSTAGE items with one atomic on the list's counter (one address for the whole
+// GPU, so one atomic per warp and step there would serialise): a warp flushes its
+// buffer when the next append would not fit and when it leaves the expand phase.
+constexpr uint32_t WSTAGE = 128;
+// live in-edges (position, set slot) a warp queues in expand_level before it resolves
+// them; one step adds at most 4 chunks x 32 lanes x 4 in-edges = 512
+constexpr uint32_t LBUF = 768;
+// groups of a super-chunk (8 chunks of 32), the unit of the expand phase
+constexpr uint64_t SCG = 256;
+// dynamic shared memory of the expand kernels: per warp, the two stages, the live queue
+// and the boundary mask of a super-chunk
+constexpr size_t EXPAND_SMEM = 8 * (2 * WSTAGE * sizeof(uint2) + LBUF * sizeof(uint2) + 8 * 4);
+#ifndef LEVELS_MIN_BLOCKS
+#define LEVELS_MIN_BLOCKS 3  // resident blocks per SM the persistent launch is built for
+#endif
+
+struct WarpStage {
+    uint2* buf;  // WSTAGE entries in shared memory
+    uint32_t n;  // entries held (the same on every lane)
 };
 
-__device__ __forceinline__ void staged_append(bool pred, uint32_t s, uint32_t u, uint2* buf,
-                                              unsigned* used, unsigned long long* counter,
-                                              uint2* list, uint64_t cap, int* err, int errbit,
-                                              int lane) {
-    const uint32_t bal = __ballot_sync(0xffffffffu, pred);
-    if (!bal) return;
-    const int leader = __ffs(bal) - 1;
-    unsigned base = 0;
-    if (lane == leader) base = atomicAdd(used, (unsigned)__popc(bal));
-    base = __shfl_sync(0xffffffffu, base, leader);
-    const unsigned r = __popc(bal & ((1u << lane) - 1u));
-    const bool staged = pred && base + r < STAGE;
-    if (staged) buf[base + r] = make_uint2(s, u);
-    warp_append(pred && !staged, s, u, counter, list, cap, err, errbit, lane);
+__device__ __forceinline__ void wstage_flush(WarpStage& ws, unsigned long long* counter,
+                                             uint2* list, uint64_t cap, int* err, int errbit,
+                                             int lane) {
+    __syncwarp();
+    if (ws.n) {
+        unsigned long long base = 0;
+        if (lane == 0) base = atomicAdd(counter, (unsigned long long)ws.n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (uint32_t i = lane; i < ws.n; i += 32) {
+            if (base + i < cap)
+                list[base + i] = ws.buf[i];
+            else
+                atomicOr(err, errbit);
+        }
+        ws.n = 0;
+    }
+    __syncwarp();
 }
 
-// Copy a block's staged appends to one reserved range of each global list.
-__device__ __forceinline__ void stage_flush(Stage& st, const BulkArgs& a) {
-    __syncthreads();
-    const unsigned nf = min(st.nf, STAGE), nm = min(st.nm, STAGE);
-    if (threadIdx.x == 0) {
-        st.gf = nf ? atomicAdd(&a.bs->f_count, (unsigned long long)nf) : 0ull;
-        st.gm = nm ? atomicAdd(&a.bs->m_count, (unsigned long long)nm) : 0ull;
-    }
-    __syncthreads();
-    for (unsigned i = threadIdx.x; i < nf; i += blockDim.x) {
-        if (st.gf + i < a.fcap)
-            a.F[st.gf + i] = st.f[i];
-        else
-            atomicOr(&a.bs->err, 1);
-    }
-    for (unsigned i = threadIdx.x; i < nm; i += blockDim.x) {
-        if (st.gm + i < a.mcap)
-            a.M[st.gm + i] = st.m[i];
-        else
-            atomicOr(&a.bs->err, 2);
-    }
-}
-
-// Add a fresh member's in-degree and count to its set, one atomic per set and warp.
-__device__ __forceinline__ void slot_add(bool fresh, uint32_t s, uint64_t deg, const BulkArgs& a,
-                                         int lane) {
+// Add the in-degrees and the number of a lane's new members (cnt, all of set slot s)
+// to the set, one atomic pair per set and warp.
+__device__ __forceinline__ void slot_add(bool fresh, uint32_t s, uint64_t deg, uint32_t cnt,
+                                         const BulkArgs& a, int lane) {
     const uint32_t fm = __ballot_sync(0xffffffffu, fresh);
     if (!fresh) return;
     const uint32_t grp = __match_any_sync(fm, s);
     // the group's members are distinct nodes of one set: their in-degrees sum below m
     const unsigned dsum = __reduce_add_sync(grp, (unsigned)deg);
+    const unsigned csum = __reduce_add_sync(grp, cnt);
     if (lane == __ffs(grp) - 1) {
         atomicAdd(&a.slot_width[s], (unsigned long long)dsum);
-        atomicAdd(&a.slot_cnt[s], (unsigned)__popc(grp));
+        atomicAdd(&a.slot_cnt[s], csum);
     }
+}
+
+// Append up to 4 items per lane (item k of lane l: (sv[k], u[k]) for bit k of bits) to
+// the warp's stage: one warp scan, no atomic unless the stage has to be flushed first.
+__device__ __forceinline__ void wstage_append4(uint32_t bits, const uint32_t* sv,
+                                               const uint32_t* u, WarpStage& ws,
+                                               unsigned long long* counter, uint2* list,
+                                               uint64_t cap, int* err, int errbit, int lane) {
+    const uint32_t cnt = __popc(bits);
+    uint32_t incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);  // <= 128 = WSTAGE
+    if (total == 0) return;
+    if (ws.n + total > WSTAGE) wstage_flush(ws, counter, list, cap, err, errbit, lane);
+    uint32_t pos = ws.n + incl - cnt;
+#pragma unroll
+    for (int c = 0; c < 4; c++)
+        if ((bits >> c) & 1u) ws.buf[pos++] = make_uint2(sv[c], u[c]);
+    ws.n += total;
+}
+
+// Expand the level F[lo .. lo + nl) over its G = gp[nl] groups. Warp wid of nw takes a
+// contiguous range of super-chunks (SCG groups). Per super-chunk the warp loads the
+// group offsets of the 256 items after its first one (8 independent loads per lane)
+// and marks the item starts in a 256-bit mask, so that every group finds its item and
+// the item's first group by popcounts; then, four chunks at a time, every lane loads
+// its group's item record, its 4 thresholds and draws its 4 coins, and the live
+// in-edges are queued as (position, set slot). The queue is resolved 64 at a time:
+// sources, then visited bits, then the new members' in-lists, each loaded together.
+// Appends go through the warp's stages (members, frontier).
+__device__ __forceinline__ void expand_level(const BulkArgs& a, uint64_t lo, uint64_t nl,
+                                             uint2* wbuf, uint2* lb, uint32_t* mwords,
+                                             uint64_t wid, uint64_t nw, int lane) {
+    (void)lo;
+    WarpStage wm{wbuf, 0u}, wf{wbuf + WSTAGE, 0u};
+    const uint64_t G = __ldcg(a.gp + nl);
+    const uint64_t nsc = (G + SCG - 1) / SCG;
+    const uint64_t per = (nsc + nw - 1) / nw;
+    const uint64_t sc0 = min(wid * per, nsc), sc1 = min(sc0 + per, nsc);
+    const bool cover = a.flags & SAMPLE_COVER;
+    uint32_t live_acc = 0, exam_acc = 0, nbuf = 0;
+    auto drain = [&]() {
+        __syncwarp();
+        for (uint32_t i = 0; i < nbuf; i += 64) {
+            const bool h0 = i + lane < nbuf, h1 = i + 32 + lane < nbuf;
+            const uint2 e0 = h0 ? lb[i + lane] : make_uint2(0u, 0u);
+            const uint2 e1 = h1 ? lb[i + 32 + lane] : make_uint2(0u, 0u);
+            uint32_t u[4] = {0u, 0u, 0u, 0u}, sv[4] = {e0.y, e1.y, 0u, 0u};
+            if (h0) u[0] = __ldg(a.src + e0.x);
+            if (h1) u[1] = __ldg(a.src + e1.x);
+            uint32_t fr = 0;
+#pragma unroll
+            for (int q = 0; q < 2; q++)
+                if (q == 0 ? h0 : h1) {
+                    const uint32_t b = 1u << (u[q] & 31);
+                    const uint32_t old =
+                        atomicOr(&a.bitmap[(uint64_t)sv[q] * a.words + (u[q] >> 5)], b);
+                    if (!(old & b)) fr |= 1u << q;
+                }
+            uint64_t d[2] = {0, 0};
+            uint32_t push = 0;
+#pragma unroll
+            for (int q = 0; q < 2; q++)
+                if ((fr >> q) & 1u) {
+                    d[q] = __ldg(a.rowptr + u[q] + 1) - __ldg(a.rowptr + u[q]);
+                    if (d[q]) push |= 1u << q;
+                    if (cover && marked(a.seed_mark, u[q])) a.slot_flag[sv[q]] = 1u;
+                }
+            slot_add(fr & 1u, sv[0], d[0], 1u, a, lane);
+            slot_add((fr >> 1) & 1u, sv[1], d[1], 1u, a, lane);
+            wstage_append4(fr, sv, u, wm, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2, lane);
+            if (cover) {
+#pragma unroll
+                for (int q = 0; q < 2; q++)
+                    if (((push >> q) & 1u) && a.slot_flag[sv[q]]) push &= ~(1u << q);
+            }
+            wstage_append4(push, sv, u, wf, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1, lane);
+        }
+        nbuf = 0;
+        __syncwarp();
+    };
+    if (sc0 < sc1) {
+        // the item holding group sc0 * SCG: the last i with gp[i] <= x, by a 32-ary
+        // search of the warp (gp[0] = 0 <= x < gp[nl] = G, gp non-decreasing)
+        uint64_t i0;
+        {
+            const uint64_t x = sc0 * SCG;
+            uint64_t l = 0, h = nl;  // gp[l] <= x < gp[h]
+            for (int guard = 0; guard < 16 && h - l > 1; guard++) {
+                const uint64_t stride = (h - l + 31) >> 5;
+                const uint64_t pr = l + (uint64_t)lane * stride;
+                const bool le = pr < h && __ldcg(a.gp + pr) <= x;
+                const uint32_t bl = __ballot_sync(0xffffffffu, le);  // lanes 0 .. k-1 hold
+                const int k = 32 - __clz(bl);                         // bl has bit 0 set
+                const uint64_t nl2 = l + (uint64_t)(k - 1) * stride;
+                h = min(h, nl2 + stride);
+                l = nl2;
+            }
+            i0 = l;
+        }
+        const uint32_t below = lane == 31 ? 0xFFFFFFFFu : ((2u << lane) - 1u);
+        for (uint64_t sc = sc0; sc < sc1; sc++) {
+            const uint64_t S0 = sc * SCG;  // gp[i0] <= S0 < gp[i0 + 1]
+            if (lane < 8) mwords[lane] = 0u;
+            __syncwarp();
+            uint32_t adv = 0;  // item starts in (S0, S0 + SCG]: the next super-chunk's i0
+            uint64_t b[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const uint64_t idx = i0 + 1 + (uint64_t)lane + 32ull * k;
+                b[k] = idx <= nl ? __ldcg(a.gp + idx) : ~0ull;
+            }
+            const uint64_t gs0 = __ldcg(a.gp + i0);
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                if (b[k] <= S0 + SCG) adv++;
+                if (b[k] < S0 + SCG)  // > S0: offsets after i0 exceed S0
+                    atomicOr(&mwords[(uint32_t)(b[k] - S0) >> 5], 1u << ((uint32_t)(b[k] - S0) & 31));
+            }
+            adv = __reduce_add_sync(0xffffffffu, adv);
+            __syncwarp();
+            uint32_t mw[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) mw[k] = mwords[k];
+#pragma unroll
+            for (int h = 0; h < 2; h++) {
+                uint4 inf[4];
+                uint64_t gof[4];  // group offset inside the item
+                bool act[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    const int c = 4 * h + k;
+                    const uint64_t t = S0 + (uint64_t)(c * 32 + lane);
+                    act[k] = t < G;
+                    // q = item starts at or before this group, pos = the last of them
+                    const uint32_t cur = mw[c] & below;
+                    uint32_t q = __popc(cur);
+                    int pos = cur ? c * 32 + 31 - __clz(cur) : -1;
+#pragma unroll
+                    for (int w = 7; w >= 0; w--) {  // words below, highest first
+                        if (w >= c) continue;
+                        q += __popc(mw[w]);
+                        if (pos < 0 && mw[w]) pos = w * 32 + 31 - __clz(mw[w]);
+                    }
+                    gof[k] = t - (q ? S0 + (uint64_t)pos : gs0);
+                    inf[k] = act[k] ? __ldcg(&a.info[i0 + q]) : make_uint4(0u, 0u, 0u, 0u);
+                }
+                uint4 tv[4];
+                uint64_t g[4];
+                bool wk[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    g[k] = ((uint64_t)inf[k].x >> 2) + gof[k];
+                    const uint32_t sl = inf[k].z & 0x7FFFFFFFu;
+                    wk[k] = act[k] && !(inf[k].z >> 31) &&
+                            !(cover && *(volatile uint32_t*)&a.slot_flag[sl]);
+                    tv[k] = wk[k] ? __ldg(reinterpret_cast<const uint4*>(a.thr) + g[k])
+                                  : make_uint4(0u, 0u, 0u, 0u);
+                }
+                uint32_t lm = 0;  // bit 4k + cc: position 4 g[k] + cc is live
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    if (!wk[k]) continue;
+                    const uint64_t sid = a.sid0 + inf[k].w;
+                    const uint4 x = philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32),
+                                                  (uint32_t)g[k], TIM_TAG_IC, a.K);
+#pragma unroll
+                    for (int cc = 0; cc < 4; cc++) {
+                        const uint64_t p = (g[k] << 2) + cc;
+                        const uint32_t th = pick4(tv[k], cc);
+                        if (p >= inf[k].x && p < inf[k].y) {
+                            exam_acc++;
+                            if (th == 0xFFFFFFFFu || pick4(x, cc) < th) lm |= 1u << (4 * k + cc);
+                        }
+                    }
+                }
+                const uint32_t cnt = __popc(lm);
+                uint32_t incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                uint32_t qpos = nbuf + incl - cnt;
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+#pragma unroll
+                    for (int cc = 0; cc < 4; cc++)
+                        if ((lm >> (4 * k + cc)) & 1u)
+                            lb[qpos++] = make_uint2((uint32_t)((g[k] << 2) + cc),
+                                                    inf[k].z & 0x7FFFFFFFu);
+                nbuf += __shfl_sync(0xffffffffu, incl, 31);
+                live_acc += cnt;
+                if (nbuf > LBUF - 512) drain();
+            }
+            i0 += adv;
+        }
+    }
+    drain();
+    wstage_flush(wm, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2, lane);
+    wstage_flush(wf, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1, lane);
+    live_acc = __reduce_add_sync(0xffffffffu, live_acc);
+    exam_acc = __reduce_add_sync(0xffffffffu, exam_acc);
+    if (lane == 0 && live_acc) atomicAdd(&a.bs->live, (unsigned long long)live_acc);
+    if (lane == 0 && exam_acc) atomicAdd(&a.bs->exam, (unsigned long long)exam_acc);
 }
 
 __global__ void __launch_bounds__(256) bulk_expand_kernel(BulkArgs a) {
-    __shared__ Stage st;
-    if (threadIdx.x == 0) st.nf = st.nm = 0;
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const uint64_t G = a.gp[a.lvl_n];
-    const uint64_t nchunks = (G + 31) >> 5;
-    const uint64_t wid = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    const uint64_t per = (nchunks + nw - 1) / nw;
-    const uint64_t c0 = min(wid * per, nchunks);
-    const uint64_t c1 = min(c0 + per, nchunks);
-    const bool cover = a.flags & SAMPLE_COVER;
-    // item holding group 32 * c0: the last i with gp[i] <= 32 * c0
-    uint64_t i0 = 0;
-    if (c0 < c1) {
-        uint64_t lo = 0, hi = a.lvl_n;  // gp[lo] <= x < gp[hi]
-        const uint64_t x = c0 << 5;
-        while (hi - lo > 1) {
-            uint64_t mid = (lo + hi) >> 1;
-            if (a.gp[mid] <= x)
-                lo = mid;
-            else
-                hi = mid;
-        }
-        i0 = lo;
-    }
-    uint32_t live_acc = 0;
-    for (uint64_t c = c0; c < c1; c++) {
-        const uint64_t base = c << 5;
-        for (int guard = 0; guard < 64 && i0 + 1 < a.lvl_n && a.gp[i0 + 1] <= base; guard++) i0++;
-        // boundaries of the next 32 items relative to this chunk
-        const uint64_t bi = i0 + 1 + lane;
-        const uint64_t bj = bi <= a.lvl_n ? a.gp[bi] : ~0ull;
-        const uint32_t bit = (bj > base && bj < base + 32) ? (1u << (uint32_t)(bj - base)) : 0u;
-        const uint32_t mask = __reduce_or_sync(0xffffffffu, bit);
-        const int q = __popc(mask & ((2u << lane) - 1u));
-        const uint64_t gstart_q = __shfl_sync(0xffffffffu, bj, max(q - 1, 0));
-        const uint64_t i = i0 + q;
-        const uint64_t t = base + lane;
-        const bool active = t < G;
-        uint32_t s = 0, v = 0;
-        uint64_t beg = 0, end = 0, g = 0;
-        bool work = false;
-        if (active) {
-            const uint64_t gstart = q ? gstart_q : a.gp[i0];
-            const uint2 it = a.F[a.lvl_lo + i];
-            s = it.x;
-            v = it.y;
-            work = !(cover && *(volatile uint32_t*)&a.slot_flag[s]);
-            if (work) {
-                beg = __ldg(a.rowptr + v);
-                end = __ldg(a.rowptr + v + 1);
-                g = (beg >> 2) + (t - gstart);
-                work = !skip_rule(__ldg(a.node_thr + v), beg, end);
-            }
-        }
-        uint4 x = make_uint4(0, 0, 0, 0), tv = make_uint4(0, 0, 0, 0);
-        uint32_t nlive = 0;
-        uint32_t j = 0;
-        if (work) {
-            j = __ldg(a.list + a.base + s);
-            const uint64_t sid = a.sid0 + j;
-            x = philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32), (uint32_t)g, TIM_TAG_IC, a.K);
-            tv = __ldg(reinterpret_cast<const uint4*>(a.thr) + g);
-        }
-#pragma unroll
-        for (int cc = 0; cc < 4; cc++) {
-            const uint64_t p = (g << 2) + cc;
-            bool fresh = false;
-            uint32_t u = 0;
-            uint64_t ub = 0, ue = 0;
-            if (work && p >= beg && p < end) {
-                const uint32_t th = pick4(tv, cc);
-                if (th == 0xFFFFFFFFu || pick4(x, cc) < th) {
-                    nlive++;
-                    u = __ldg(a.src + p);
-                    const uint32_t b = 1u << (u & 31);
-                    const uint32_t old = atomicOr(&a.bitmap[(uint64_t)s * a.words + (u >> 5)], b);
-                    fresh = !(old & b);
-                    if (fresh) {
-                        ub = __ldg(a.rowptr + u);
-                        ue = __ldg(a.rowptr + u + 1);
-                        if (cover && marked(a.seed_mark, u)) a.slot_flag[s] = 1u;
-                    }
-                }
-            }
-            slot_add(fresh, s, ue - ub, a, lane);
-            staged_append(fresh, s, u, st.m, &st.nm, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2,
-                          lane);
-            const bool push = fresh && ue > ub && !(cover && a.slot_flag[s]);
-            staged_append(push, s, u, st.f, &st.nf, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1,
-                          lane);
-        }
-        i0 = __shfl_sync(0xffffffffu, i, 31);
-        live_acc += nlive;
-    }
-    live_acc = __reduce_add_sync(0xffffffffu, live_acc);
-    if (lane == 0 && live_acc) atomicAdd(&a.bs->live, (unsigned long long)live_acc);
-    stage_flush(st, a);
+    extern __shared__ uint2 dsm[];
+    const int w = threadIdx.x >> 5;
+    uint2* wbuf = dsm + w * 2 * WSTAGE;
+    uint2* lb = dsm + 8 * 2 * WSTAGE + w * LBUF;
+    uint32_t* mw = reinterpret_cast<uint32_t*>(dsm + 8 * (2 * WSTAGE + LBUF)) + w * 8;
+    expand_level(a, a.lvl_lo, a.lvl_n, wbuf, lb, mw,
+                 (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5,
+                 ((uint64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
 }
 
-// The level's items under the skip rule: one warp per item draws the live in-edges
-// by geometric skipping and handles each like bulk_expand_kernel does.
-__global__ void __launch_bounds__(256) bulk_skip_kernel(BulkArgs a) {
-    const int lane = threadIdx.x & 31;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+// The level's items under the skip rule, one warp per item. The lanes screen 32 items
+// at a time: by the NG_SKIP flag of the item's group count (from_ng, persistent launch)
+// or from the graph (host-stepped path).
+__device__ __forceinline__ void skip_level(const BulkArgs& a, uint64_t lo, uint64_t nl,
+                                           bool from_ng, uint64_t wid, uint64_t nw, int lane) {
     const bool cover = a.flags & SAMPLE_COVER;
     uint32_t live_acc = 0;
-    for (uint64_t i = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; i < a.lvl_n;
-         i += nw) {
-        const uint2 it = a.F[a.lvl_lo + i];
+    for (uint64_t base = wid * 32; base < nl; base += nw * 32) {
+        bool sk = false;
+        if (base + lane < nl) {
+            if (from_ng) {
+                sk = (__ldcg(a.ng + base + lane) & NG_SKIP) != 0;
+            } else {
+                const uint32_t v = __ldcg(&a.F[lo + base + lane]).y;
+                sk = skip_rule(__ldg(a.node_thr + v), __ldg(a.rowptr + v), __ldg(a.rowptr + v + 1));
+            }
+        }
+        uint32_t todo = __ballot_sync(0xffffffffu, sk);
+        while (todo) {
+        const uint64_t i = base + (uint64_t)(__ffs(todo) - 1);
+        todo &= todo - 1;
+        const uint2 it = __ldcg(&a.F[lo + i]);
         const uint32_t s = it.x, v = it.y;
         const uint64_t beg = __ldg(a.rowptr + v), end = __ldg(a.rowptr + v + 1);
         const unsigned long long nt = __ldg(a.node_thr + v);
-        if (!skip_rule(nt, beg, end)) continue;
         if (cover && *(volatile uint32_t*)&a.slot_flag[s]) continue;
         const uint64_t sid = a.sid0 + __ldg(a.list + a.base + s);
         skip_live_warp((uint32_t)sid, (uint32_t)(sid >> 32), a.K, (uint32_t)beg,
@@ -353,9 +514,161 @@ __global__ void __launch_bounds__(256) bulk_skip_kernel(BulkArgs a) {
                                        lane);
                            return false;
                        });
+        }
     }
     live_acc = __reduce_add_sync(0xffffffffu, live_acc);
     if (lane == 0 && live_acc) atomicAdd(&a.bs->live, (unsigned long long)live_acc);
+}
+
+__global__ void __launch_bounds__(256) bulk_skip_kernel(BulkArgs a) {
+    skip_level(a, a.lvl_lo, a.lvl_n, false, (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5,
+               ((uint64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
+}
+
+// Sum of v over the block (every thread gets it). blockDim.x is a multiple of 32, <= 1024.
+__device__ __forceinline__ unsigned long long block_sum(unsigned long long v,
+                                                        unsigned long long* red) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) red[w] = v;
+    __syncthreads();
+    unsigned long long t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) t += red[i];
+    return t;
+}
+
+// Exclusive scan of x over the block; *total = the block's sum. Same conditions.
+__device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long x,
+                                                              unsigned long long* red,
+                                                              unsigned long long* total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    unsigned long long inc = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) red[w] = inc;
+    __syncthreads();
+    unsigned long long before = 0, all = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); i++) {
+        if (i < w) before += red[i];
+        all += red[i];
+    }
+    *total = all;
+    return before + inc - x;
+}
+
+// All levels of a batch in one cooperative launch (see the file comment). Every block
+// reads the level bounds from f_count after the barrier that ends a level, before any
+// block appends to F again, so all blocks agree on them; on a timeout or a full list
+// every block leaves at the same barrier or the next one.
+__global__ void __launch_bounds__(256, LEVELS_MIN_BLOCKS) bulk_levels_kernel(BulkArgs a) {
+    extern __shared__ uint2 dsm[];
+    __shared__ unsigned long long red[32];
+    const int lane = threadIdx.x & 31;
+    const uint64_t wid = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    int* err = &a.bs->err;
+    uint64_t lo = 0, hi = __ldcg(&a.bs->f_count);
+    if (__ldcg(err)) return;
+    // block 0 accounts where its time goes (phases and barrier waits)
+    const bool clerk = blockIdx.x == 0 && threadIdx.x == 0;
+    unsigned long long t_prev = clerk ? globaltimer_ns() : 0ull, ns_off = 0, ns_exp = 0,
+                       ns_wait = 0, nlev = 0;
+    auto lap = [&](unsigned long long& acc) {
+        if (clerk) {
+            const unsigned long long t = globaltimer_ns();
+            acc += t - t_prev;
+            t_prev = t;
+        }
+    };
+    auto account = [&]() {
+        if (clerk) {
+            a.bs->levels += nlev;
+            a.bs->ns_offsets += ns_off;
+            a.bs->ns_expand += ns_exp;
+            a.bs->ns_wait += ns_wait;
+        }
+    };
+    for (int level = 0; level < (1 << 26) && hi > lo; level++) {
+        nlev++;
+        const uint64_t nl = hi - lo;
+        if (nl > a.fcap) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 1);
+            return;
+        }
+#ifdef BULK_TRACE
+        unsigned long long tr0 = clerk ? globaltimer_ns() : 0ull, tr[4] = {0, 0, 0, 0};
+#endif
+        // (A) group counts of this block's items and their sum
+        const uint64_t per = (nl + gridDim.x - 1) / gridDim.x;
+        const uint64_t ib = min((uint64_t)blockIdx.x * per, nl), ie = min(ib + per, nl);
+        unsigned long long sum = 0;
+        for (uint64_t i = ib + threadIdx.x; i < ie; i += blockDim.x) {
+            const uint32_t g = item_prepare(a, lo, i);
+            a.ng[i] = g;
+            sum += g & ~NG_SKIP;
+        }
+        sum = block_sum(sum, red);
+        if (threadIdx.x == 0) a.bsum[blockIdx.x] = sum;
+        lap(ns_off);
+        if (!grid_barrier(a.bar, err, a.wait_limit)) return;
+        lap(ns_wait);
+        // (B) global group offsets of this block's items
+        unsigned long long before = 0, all = 0;
+        for (unsigned b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+            const unsigned long long x = __ldcg(a.bsum + b);
+            if (b < blockIdx.x) before += x;
+            all += x;
+        }
+        before = block_sum(before, red);
+        all = block_sum(all, red);
+        for (uint64_t c = ib; c < ie; c += blockDim.x) {
+            const uint64_t i = c + threadIdx.x;
+            const unsigned long long g = i < ie ? (a.ng[i] & ~NG_SKIP) : 0u;
+            unsigned long long tot;
+            const unsigned long long ex = block_excl_scan(g, red, &tot);
+            if (i < ie) a.gp[i] = before + ex;
+            before += tot;
+        }
+        if (blockIdx.x == 0 && threadIdx.x == 0) a.gp[nl] = all;
+        lap(ns_off);
+        if (!grid_barrier(a.bar, err, a.wait_limit)) return;
+        lap(ns_wait);
+        // (C) expand: in-lists by groups over all warps, skip-rule lists by one warp each
+        {
+            const int w = threadIdx.x >> 5;
+            expand_level(a, lo, nl, dsm + w * 2 * WSTAGE, dsm + 8 * 2 * WSTAGE + w * LBUF,
+                         reinterpret_cast<uint32_t*>(dsm + 8 * (2 * WSTAGE + LBUF)) + w * 8,
+                         wid, nw, lane);
+        }
+        skip_level(a, lo, nl, true, wid, nw, lane);
+        lap(ns_exp);
+        if (!grid_barrier(a.bar, err, a.wait_limit)) return;
+        lap(ns_wait);
+#ifdef BULK_TRACE
+        if (clerk) {
+            const unsigned long long k = atomicAdd(&bulk_trace_n, 1ull) & 0xFFFFull;
+            bulk_trace[k][0] = nl;
+            bulk_trace[k][1] = all;
+            bulk_trace[k][2] = t_prev - tr0;
+            bulk_trace[k][3] = __ldcg(&a.bs->m_count);
+            bulk_trace[k][4] = __ldcg(&a.bs->live);
+            bulk_trace[k][5] = level;
+        }
+#endif
+        lo = hi;
+        hi = __ldcg(&a.bs->f_count);
+        if (__ldcg(err)) {
+            account();
+            return;
+        }
+    }
+    account();
 }
 
 __global__ void bulk_finalize_kernel(BulkArgs a) {
@@ -393,6 +706,7 @@ __global__ void bulk_finalize_kernel(BulkArgs a) {
     }
     if (cov) atomicAdd(&a.ds->covered, cov);
     if (memb) atomicAdd(&a.ds->memb[2], memb);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && a.bs->exam) atomicAdd(&a.ds->exam[2], a.bs->exam);
 }
 
 // Copy members into the store (emit) and clear the visited bits, one member each.
@@ -448,8 +762,30 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
     TIM_TRY(tim_ensure(ctx, ctx->bulk_F, ctx->bulk_fcap * sizeof(uint2)));
     TIM_TRY(tim_ensure(ctx, ctx->bulk_M, ctx->bulk_mcap * sizeof(uint2)));
     TIM_TRY(tim_ensure(ctx, ctx->bulk_ng, ctx->bulk_fcap * sizeof(uint32_t)));
+    TIM_TRY(tim_ensure(ctx, ctx->bulk_info, ctx->bulk_fcap * sizeof(uint4)));
     TIM_TRY(tim_ensure(ctx, ctx->bulk_gp, (ctx->bulk_fcap + 1) * sizeof(uint64_t)));
     TIM_TRY(tim_ensure(ctx, ctx->bulk_scal, sizeof(BulkScalars)));
+    CUDA_TRY(ctx, cudaFuncSetAttribute(bulk_levels_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)EXPAND_SMEM));
+    CUDA_TRY(ctx, cudaFuncSetAttribute(bulk_expand_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)EXPAND_SMEM));
+    // persistent launch: co-resident blocks (at most 4 per SM), their sums and a barrier
+    int coop = 0, nb = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, ctx->device);
+    if (!ctx->bulk_stepped && coop &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, bulk_levels_kernel, 256, EXPAND_SMEM) !=
+            cudaSuccess) {
+        cudaGetLastError();
+        nb = 0;
+    }
+    const bool persistent = !ctx->bulk_stepped && coop && nb > 0;
+    const unsigned GP = (unsigned)(ctx->num_sms * std::min(nb, 4));
+    if (persistent) {
+        TIM_TRY(tim_ensure(ctx, ctx->bulk_bsum, (size_t)GP * sizeof(unsigned long long)));
+        TIM_TRY(tim_ensure(ctx, ctx->bulk_bar, sizeof(GridBarrier)));
+    }
 
     BulkArgs a;
     a.rowptr = (const uint64_t*)ctx->rowptr.p;
@@ -481,6 +817,9 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
     a.set_start = (uint64_t*)ctx->set_start.p;
     a.set_len = (uint32_t*)ctx->set_len.p;
     a.set_width = (uint64_t*)ctx->set_width.p;
+    a.bsum = (unsigned long long*)ctx->bulk_bsum.p;
+    a.bar = (GridBarrier*)ctx->bulk_bar.p;
+    a.wait_limit = ctx->wait_limit;
     BulkScalars hb;
     const unsigned GX = (unsigned)(ctx->num_sms * 4);
     uint32_t done = 0;
@@ -493,27 +832,48 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
         a.M = (uint2*)ctx->bulk_M.p;
         a.fcap = ctx->bulk_fcap;
         a.mcap = ctx->bulk_mcap;
+        a.ng = (uint32_t*)ctx->bulk_ng.p;
+        a.info = (uint4*)ctx->bulk_info.p;
+        a.gp = (uint64_t*)ctx->bulk_gp.p;
         CUDA_TRY(ctx, cudaMemsetAsync(a.bs, 0, sizeof(BulkScalars), ctx->stream));
         bulk_init_kernel<<<(bs + 255) / 256, 256, 0, ctx->stream>>>(a);
         LAUNCH_CHECK(ctx, "bulk_init_kernel");
-        CUDA_TRY(ctx, cudaMemcpyAsync(&hb, a.bs, sizeof hb, cudaMemcpyDeviceToHost, ctx->stream));
-        TIM_TRY(tim_sync(ctx));
-        uint64_t lo = 0, hi = hb.f_count;
-        bool overflow = hb.err != 0;
-        for (int level = 0; !overflow && hi > lo && level < (1 << 26); level++) {
+        uint64_t lo = 0, hi = 0;
+        bool overflow = false;
+        if (persistent) {
+            CUDA_TRY(ctx, cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), ctx->stream));
+            void* args[] = {&a};
+            CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)bulk_levels_kernel, dim3(GP),
+                                                      dim3(256), args, EXPAND_SMEM,
+                                                      ctx->stream));
+            LAUNCH_CHECK(ctx, "bulk_levels_kernel");
+            CUDA_TRY(ctx, cudaMemcpyAsync(&hb, a.bs, sizeof hb, cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+            TIM_TRY(tim_sync(ctx));
+            if (hb.err & TIM_DEV_ERR_TIMEOUT) {
+                ctx->bulk_bitmap_clean = false;
+                return tim_fail(ctx, TIM_ERR_TIMEOUT, "heavy-set grid barrier timed out");
+            }
+            overflow = hb.err != 0;
+        } else {
+            CUDA_TRY(ctx, cudaMemcpyAsync(&hb, a.bs, sizeof hb, cudaMemcpyDeviceToHost,
+                                          ctx->stream));
+            TIM_TRY(tim_sync(ctx));
+            hi = hb.f_count;
+            overflow = hb.err != 0;
+        }
+        for (int level = 0; !persistent && !overflow && hi > lo && level < (1 << 26); level++) {
             a.lvl_lo = lo;
             a.lvl_n = hi - lo;
             if (a.lvl_n > ctx->bulk_fcap) {
                 overflow = true;
                 break;
             }
-            a.ng = (const uint32_t*)ctx->bulk_ng.p;
-            a.gp = (const uint64_t*)ctx->bulk_gp.p;
-            bulk_ng_kernel<<<GX * 2, 256, 0, ctx->stream>>>(a, (uint32_t*)ctx->bulk_ng.p);
+            bulk_ng_kernel<<<GX * 2, 256, 0, ctx->stream>>>(a);
             LAUNCH_CHECK(ctx, "bulk_ng_kernel");
             TIM_TRY(tim_scan_u32_to_u64(ctx, (const uint32_t*)ctx->bulk_ng.p,
                                         (uint64_t*)ctx->bulk_gp.p, a.lvl_n));
-            bulk_expand_kernel<<<GX * 4, 256, 0, ctx->stream>>>(a);
+            bulk_expand_kernel<<<GX * 4, 256, EXPAND_SMEM, ctx->stream>>>(a);
             LAUNCH_CHECK(ctx, "bulk_expand_kernel");
             bulk_skip_kernel<<<GX * 2, 256, 0, ctx->stream>>>(a);
             LAUNCH_CHECK(ctx, "bulk_skip_kernel");
@@ -533,10 +893,12 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
             tim_free(ctx->bulk_F);
             tim_free(ctx->bulk_M);
             tim_free(ctx->bulk_ng);
+            tim_free(ctx->bulk_info);
             tim_free(ctx->bulk_gp);
             TIM_TRY(tim_ensure(ctx, ctx->bulk_F, ctx->bulk_fcap * sizeof(uint2)));
             TIM_TRY(tim_ensure(ctx, ctx->bulk_M, ctx->bulk_mcap * sizeof(uint2)));
             TIM_TRY(tim_ensure(ctx, ctx->bulk_ng, ctx->bulk_fcap * sizeof(uint32_t)));
+            TIM_TRY(tim_ensure(ctx, ctx->bulk_info, ctx->bulk_fcap * sizeof(uint4)));
             TIM_TRY(tim_ensure(ctx, ctx->bulk_gp, (ctx->bulk_fcap + 1) * sizeof(uint64_t)));
             continue;
         }
@@ -548,7 +910,25 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
         LAUNCH_CHECK(ctx, "bulk_emit_clear_kernel");
         live += hb.live;
         done += bs;
+        if (persistent) {
+            tim_profile& P = ctx->prof;
+            P.pass3_batches += 1;
+            P.pass3_levels += hb.levels;
+            P.pass3_ms_offsets += hb.ns_offsets * 1e-6;
+            P.pass3_ms_expand += hb.ns_expand * 1e-6;
+            P.pass3_ms_wait += hb.ns_wait * 1e-6;
+        }
     }
     if (live_out) *live_out = live;
     return TIM_OK;
 }
+
+#ifdef BULK_TRACE
+extern "C" int tim_debug_bulk_trace(unsigned long long* out, unsigned long long cap) {
+    unsigned long long n = 0;
+    cudaMemcpyFromSymbol(&n, bulk_trace_n, sizeof n);
+    const unsigned long long k = n < cap ? n : cap;
+    cudaMemcpyFromSymbol(out, bulk_trace, k * 6 * sizeof(unsigned long long));
+    return (int)k;
+}
+#endif

@@ -132,45 +132,6 @@ __global__ void cover_kernel(const unsigned long long* __restrict__ best,
     if (lane == 0 && fresh) atomicAdd(ncov, fresh);
 }
 
-// Barrier over all blocks of a co-resident (cooperative) launch: sense reversal on a
-// generation counter. The wait is bounded: after GRID_WAIT_LIMIT polls the block sets
-// TIM_DEV_ERR_TIMEOUT in *err and returns false (the caller then stops).
-constexpr unsigned GRID_WAIT_LIMIT = 1u << 24;
-
-struct GridBarrier {
-    unsigned count;
-    unsigned gen;
-};
-
-__device__ bool grid_barrier(GridBarrier* bar, int* err) {
-    __shared__ int s_ok;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        int ok = 1;
-        __threadfence();
-        const unsigned g = ((volatile unsigned*)&bar->gen)[0];
-        if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            atomicAdd(&bar->gen, 1u);
-        } else {
-            unsigned it = 0;
-            while (((volatile unsigned*)&bar->gen)[0] == g && it < GRID_WAIT_LIMIT) {
-                __nanosleep(64);
-                it++;
-            }
-            if (it >= GRID_WAIT_LIMIT) {
-                atomicOr(err, TIM_DEV_ERR_TIMEOUT);
-                ok = 0;
-            }
-        }
-        __threadfence();
-        s_ok = ok && !(((volatile int*)err)[0] & TIM_DEV_ERR_TIMEOUT);
-    }
-    __syncthreads();
-    return s_ok != 0;
-}
-
 // All k greedy rounds in one cooperative launch: per round an argmax over the counts
 // (every block reduces a slice, atomicMax into best[r]), a grid barrier, the cover step
 // of the chosen node (warps over its set list), and a second barrier.
@@ -180,7 +141,8 @@ greedy_rounds_kernel(int* __restrict__ counts, uint8_t* __restrict__ chosen, uin
                      const uint64_t* __restrict__ set_start, const uint32_t* __restrict__ set_len,
                      const uint32_t* __restrict__ pool, uint8_t* __restrict__ covered, int k,
                      unsigned long long* __restrict__ best, int32_t* __restrict__ seeds,
-                     unsigned long long* __restrict__ ncov, GridBarrier* bar, int* err) {
+                     unsigned long long* __restrict__ ncov, GridBarrier* bar, int* err,
+                     unsigned limit) {
     __shared__ unsigned long long wb[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -211,7 +173,7 @@ greedy_rounds_kernel(int* __restrict__ counts, uint8_t* __restrict__ chosen, uin
             }
             if (lane == 0 && b) atomicMax(best + r, b);
         }
-        if (!grid_barrier(bar, err)) return;
+        if (!grid_barrier(bar, err, limit)) return;
         const unsigned long long key = ((volatile unsigned long long*)best)[r];
         if (key != 0) {
             const uint32_t v = ~(uint32_t)(key & 0xFFFFFFFFull);
@@ -233,7 +195,7 @@ greedy_rounds_kernel(int* __restrict__ counts, uint8_t* __restrict__ chosen, uin
                 for (uint32_t t = lane; t < len; t += 32) atomicSub(&counts[pool[st + t]], 1);
             }
         }
-        if (!grid_barrier(bar, err)) return;
+        if (!grid_barrier(bar, err, limit)) return;
     }
     if (lane == 0 && fresh) atomicAdd(ncov, fresh);
 }
@@ -303,8 +265,9 @@ int tim_greedy(tim_ctx* ctx, int k, int32_t* host_seeds, uint64_t* covered) {
         unsigned long long* d_ncov = &ds->covered;
         GridBarrier* d_bar = (GridBarrier*)ctx->greedy_bar.p;
         int* d_err = &ds->err;
+        unsigned limit = ctx->wait_limit;
         void* args[] = {&d_counts, &d_chosen, &nn, &d_off, &d_ns, &d_ss, &d_sl, &d_pool,
-                        &d_cov, &kk, &best, &d_seeds, &d_ncov, &d_bar, &d_err};
+                        &d_cov, &kk, &best, &d_seeds, &d_ncov, &d_bar, &d_err, &limit};
         CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)greedy_rounds_kernel, dim3(grid),
                                                   dim3(256), args, 0, ctx->stream));
         LAUNCH_CHECK(ctx, "greedy_rounds_kernel");

@@ -63,6 +63,9 @@ class tim_profile(C.Structure):
         ("pass3_members", C.c_uint64),
         ("pass1_examined", C.c_uint64), ("pass2_examined", C.c_uint64),
         ("pass3_examined", C.c_uint64),
+        ("pass3_batches", C.c_uint64), ("pass3_levels", C.c_uint64),
+        ("pass3_ms_offsets", C.c_double), ("pass3_ms_expand", C.c_double),
+        ("pass3_ms_wait", C.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -120,6 +123,9 @@ _SIGS = {
     "tim_get_profile": (C.c_int, [_P, _P, C.c_int]),
     "tim_set_width_budget": (C.c_int, [_P, C.c_uint64]),
     "tim_set_team_size": (C.c_int, [_P, C.c_int]),
+    "tim_set_wait_limit": (C.c_int, [_P, C.c_uint32]),
+    "tim_set_pass2_budget": (C.c_int, [_P, C.c_uint64]),
+    "tim_set_heavy_pass": (C.c_int, [_P, C.c_int]),
     "tim_set_query_tag": (C.c_int, [_P, C.c_uint32]),
     "tim_set_chunk": (C.c_int, [_P, C.c_int]),
     "tim_run_batch": (C.c_int, [_P, C.c_int, C.c_uint64, C.c_int, _P]),
@@ -381,6 +387,18 @@ def tim_autotune(ctx, sample_sets: int, seed: int = 1) -> dict:
 
 def tim_set_team_size(ctx, warps: int):
     _check(ctx, lib().tim_set_team_size(ctx, warps))
+
+
+def tim_set_pass2_budget(ctx, budget: int):
+    _check(ctx, lib().tim_set_pass2_budget(ctx, budget))
+
+
+def tim_set_wait_limit(ctx, polls: int):
+    _check(ctx, lib().tim_set_wait_limit(ctx, polls))
+
+
+def tim_set_heavy_pass(ctx, stepped: bool):
+    _check(ctx, lib().tim_set_heavy_pass(ctx, int(bool(stepped))))
 
 
 def tim_get_profile(ctx, reset: bool = False) -> dict:

@@ -349,3 +349,66 @@ def test_skip_lists_bit_exact_in_every_pass(eng, weights, budget, team):
     finally:
         tim.tim_set_width_budget(eng.ctx, 16384)
         tim.tim_set_team_size(eng.ctx, 0)
+
+
+def _heavy_skip_graph():
+    """Sets far beyond pass 2's queue (p = 0.3 on a background of mean in-degree 5) that
+    also reach hubs whose in-lists take the skip rule (weighted cascade, 600-9000
+    in-edges): the heavy-set pass meets both kinds of list."""
+    g = _hub_graph(30000, 150000, [600, 1500, 3000, 9000], seed=3)
+    w = inputs.constant(g, 0.3)
+    hub = g.dst < 4
+    w[hub] = inputs.weighted_cascade(g)[hub]
+    return g, w
+
+
+@pytest.mark.parametrize("stepped", [0, 1])
+def test_heavy_pass_persistent_and_stepped_bit_exact(eng, stepped):
+    g, w = _heavy_skip_graph()
+    og = _load(eng, g, w, O.IC)
+    tim.tim_set_heavy_pass(eng.ctx, stepped)
+    try:
+        tim.tim_get_profile(eng.ctx, reset=True)
+        off = _compare_store(eng, og, 5, O.make_sid(3, 0, 0), 400)
+        assert np.diff(off).max() > 8192
+        assert tim.tim_get_profile(eng.ctx)["pass3_sets"] > 0
+        k = O.kappa_sum(og, 10, 5, O.make_sid(1, 3, 0), 300)
+        assert tim.tim_kappa_sum(eng.ctx, 10, 5, O.make_sid(1, 3, 0), 300) == k
+        seeds = np.array([0, 1, 7, 11], dtype=np.int32)
+        assert tim.tim_covered_count(eng.ctx, seeds, 5, 77, 300) == \
+            O.covered_count(og, 5, 77, 300, seeds)
+    finally:
+        tim.tim_set_heavy_pass(eng.ctx, 0)
+
+
+def test_grid_barrier_timeout_is_reported_and_the_context_recovers(eng):
+    """A poll limit of zero makes every block that waits at a grid barrier give up at
+    once: the heavy-set pass and the greedy return TIM_ERR_TIMEOUT (no fault, no hang),
+    and with the default limit the same context gives the oracle's results again."""
+    g, w = _heavy_skip_graph()
+    og = _load(eng, g, w, O.IC)
+    sid0 = O.make_sid(3, 0, 0)
+    tim.tim_set_wait_limit(eng.ctx, 0)
+    try:
+        with pytest.raises(tim.TimError) as ei:
+            tim.tim_sample_rr(eng.ctx, 400, 5, sid0)
+        assert ei.value.code == -4
+    finally:
+        tim.tim_set_wait_limit(eng.ctx, 1 << 24)
+    _compare_store(eng, og, 5, sid0, 400)
+    # the greedy's cooperative launch
+    h = inputs.rmat(12, seed=5)
+    wh = inputs.weighted_cascade(h)
+    oh = _load(eng, h, wh, O.IC)
+    tim.tim_sample_rr(eng.ctx, 20000, 5, sid0)
+    tim.tim_set_wait_limit(eng.ctx, 0)
+    try:
+        with pytest.raises(tim.TimError) as ei:
+            tim.tim_node_select(eng.ctx, 10)
+        assert ei.value.code == -4
+    finally:
+        tim.tim_set_wait_limit(eng.ctx, 1 << 24)
+    seeds, _, cov = tim.tim_node_select(eng.ctx, 10)
+    roff, rmem, _ = O.sample(oh, 5, sid0, 20000)
+    rseeds, rcov, _ = O.greedy(h.n, roff, rmem, 10)
+    assert np.array_equal(seeds, rseeds) and cov == rcov
