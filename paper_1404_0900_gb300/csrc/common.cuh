@@ -100,7 +100,6 @@ struct tim_ctx {
     // batched second pass for heavy IC sets (sample_bulk.cu)
     DevBuf bulk_bitmap, bulk_slot, bulk_F, bulk_M, bulk_ng, bulk_gp, bulk_scal;
     DevBuf bulk_bsum, bulk_bar;  // persistent launch: per-block sums, grid barrier
-    DevBuf bulk_info;            // per frontier item: in-list, set slot, set index
     // run the heavy-set levels as host-stepped launches instead of one persistent launch
     bool bulk_stepped = false;
     bool bulk_bitmap_clean = false;

@@ -68,14 +68,13 @@ struct BulkArgs {
     uint32_t* slot_flag;
     unsigned long long* slot_start;
     uint32_t* slot_cursor;
-    uint2* F;
+    uint4* F;  // frontier items: (in-list begin, end, set slot | skip flag << 31, node)
     uint64_t fcap;
     uint2* M;
     uint64_t mcap;
     BulkScalars* bs;
     uint64_t lvl_lo, lvl_n;  // current level: F[lvl_lo .. lvl_lo + lvl_n)
     uint32_t* ng;        // group count of each item of the level (bit 31: skip-rule item)
-    uint4* info;         // record of each item of the level (item_prepare)
     uint64_t* gp;        // exclusive group prefix of the level, gp[lvl_n] = total
     unsigned long long* bsum;  // persistent launch: one group sum per block
     GridBarrier* bar;          // persistent launch: grid barrier, zeroed before the launch
@@ -129,39 +128,30 @@ __global__ void bulk_init_kernel(BulkArgs a) {
             atomicOr(&a.bs->err, 2);
         if (end > beg && !cov) {
             unsigned long long pf = atomicAdd(&a.bs->f_count, 1ull);
+            const bool sk = tim_skip_rule(a.node_thr[root], end - beg);
             if (pf < a.fcap)
-                a.F[pf] = make_uint2(s, root);
+                a.F[pf] = make_uint4((uint32_t)beg, (uint32_t)end, s | (sk ? 0x80000000u : 0u),
+                                     root);
             else
                 atomicOr(&a.bs->err, 1);
         }
     }
 }
 
-// Does in-list [beg, end) with per-node threshold word nt take the skip rule?
-__device__ __forceinline__ bool skip_rule(unsigned long long nt, uint64_t beg, uint64_t end) {
-    return tim_skip_rule(nt, end - beg);
-}
-
 constexpr uint32_t NG_SKIP = 0x80000000u;
 
 // Groups of frontier item F[lo + i]: the 4-aligned groups of its in-list, or one
-// placeholder group (flagged NG_SKIP) for a list under the skip rule. Also stores the
-// item's record for the expand phase, info[i] = (first in-CSR position of the in-list,
-// end position, set slot | skip flag << 31, index of the set in the heavy list).
-__device__ __forceinline__ uint32_t item_prepare(const BulkArgs& a, uint64_t lo, uint64_t i) {
-    const uint2 it = __ldcg(&a.F[lo + i]);
-    const uint64_t beg = __ldg(a.rowptr + it.y), end = __ldg(a.rowptr + it.y + 1);
-    const bool skip = skip_rule(__ldg(a.node_thr + it.y), beg, end);
-    a.info[i] = make_uint4((uint32_t)beg, (uint32_t)end, it.x | (skip ? 0x80000000u : 0u),
-                           __ldg(a.list + a.base + it.x));
-    return skip ? (1u | NG_SKIP) : (uint32_t)(((end - 1) >> 2) - (beg >> 2) + 1);  // end > beg
+// placeholder group (flagged NG_SKIP) for a list under the skip rule.
+__device__ __forceinline__ uint32_t item_groups(const BulkArgs& a, uint64_t lo, uint64_t i) {
+    const uint4 it = __ldcg(&a.F[lo + i]);
+    return (it.z >> 31) ? (1u | NG_SKIP) : ((it.y - 1) >> 2) - (it.x >> 2) + 1u;  // y > x
 }
 
 // Host-stepped path: group counts of the level without the skip flag (the scan input).
 __global__ void bulk_ng_kernel(BulkArgs a) {
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.lvl_n;
          i += (uint64_t)gridDim.x * blockDim.x)
-        a.ng[i] = item_prepare(a, a.lvl_lo, i) & ~NG_SKIP;
+        a.ng[i] = item_groups(a, a.lvl_lo, i) & ~NG_SKIP;
 }
 
 // Warp-aggregated append of (slot, node) to one of the lists; returns nothing.
@@ -183,6 +173,24 @@ __device__ __forceinline__ void warp_append(bool pred, uint32_t s, uint32_t u,
     }
 }
 
+// Warp-aggregated append of a frontier item to F.
+__device__ __forceinline__ void warp_append_f(bool pred, uint4 item, unsigned long long* counter,
+                                              uint4* list, uint64_t cap, int* err, int lane) {
+    const uint32_t bal = __ballot_sync(0xffffffffu, pred);
+    if (!bal) return;
+    const int leader = __ffs(bal) - 1;
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(bal));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) {
+        const unsigned long long pos = base + __popc(bal & ((1u << lane) - 1u));
+        if (pos < cap)
+            list[pos] = item;
+        else
+            atomicOr(err, 1);
+    }
+}
+
 // Appends of one warp staged in shared memory and copied to the global list in runs of
 // up to WSTAGE items with one atomic on the list's counter (one address for the whole
 // GPU, so one atomic per warp and step there would serialise): a warp flushes its
@@ -195,18 +203,21 @@ constexpr uint32_t LBUF = 768;
 constexpr uint64_t SCG = 256;
 // dynamic shared memory of the expand kernels: per warp, the two stages, the live queue
 // and the boundary mask of a super-chunk
-constexpr size_t EXPAND_SMEM = 8 * (2 * WSTAGE * sizeof(uint2) + LBUF * sizeof(uint2) + 8 * 4);
+constexpr size_t EXPAND_SMEM =
+    8 * (WSTAGE * (sizeof(uint2) + sizeof(uint4)) + LBUF * sizeof(uint2) + 8 * 4);
 #ifndef LEVELS_MIN_BLOCKS
-#define LEVELS_MIN_BLOCKS 3  // resident blocks per SM the persistent launch is built for
+#define LEVELS_MIN_BLOCKS 2  // resident blocks per SM the persistent launch is built for
 #endif
 
+template <class T>
 struct WarpStage {
-    uint2* buf;  // WSTAGE entries in shared memory
+    T* buf;      // WSTAGE entries in shared memory
     uint32_t n;  // entries held (the same on every lane)
 };
 
-__device__ __forceinline__ void wstage_flush(WarpStage& ws, unsigned long long* counter,
-                                             uint2* list, uint64_t cap, int* err, int errbit,
+template <class T>
+__device__ __forceinline__ void wstage_flush(WarpStage<T>& ws, unsigned long long* counter,
+                                             T* list, uint64_t cap, int* err, int errbit,
                                              int lane) {
     __syncwarp();
     if (ws.n) {
@@ -240,11 +251,11 @@ __device__ __forceinline__ void slot_add(bool fresh, uint32_t s, uint64_t deg, u
     }
 }
 
-// Append up to 4 items per lane (item k of lane l: (sv[k], u[k]) for bit k of bits) to
-// the warp's stage: one warp scan, no atomic unless the stage has to be flushed first.
-__device__ __forceinline__ void wstage_append4(uint32_t bits, const uint32_t* sv,
-                                               const uint32_t* u, WarpStage& ws,
-                                               unsigned long long* counter, uint2* list,
+// Append up to 4 items per lane (items[k] for bit k of bits) to the warp's stage: one
+// warp scan, no atomic unless the stage has to be flushed first.
+template <class T>
+__device__ __forceinline__ void wstage_append4(uint32_t bits, const T* items, WarpStage<T>& ws,
+                                               unsigned long long* counter, T* list,
                                                uint64_t cap, int* err, int errbit, int lane) {
     const uint32_t cnt = __popc(bits);
     uint32_t incl = cnt;
@@ -259,7 +270,7 @@ __device__ __forceinline__ void wstage_append4(uint32_t bits, const uint32_t* sv
     uint32_t pos = ws.n + incl - cnt;
 #pragma unroll
     for (int c = 0; c < 4; c++)
-        if ((bits >> c) & 1u) ws.buf[pos++] = make_uint2(sv[c], u[c]);
+        if ((bits >> c) & 1u) ws.buf[pos++] = items[c];
     ws.n += total;
 }
 
@@ -273,10 +284,11 @@ __device__ __forceinline__ void wstage_append4(uint32_t bits, const uint32_t* sv
 // sources, then visited bits, then the new members' in-lists, each loaded together.
 // Appends go through the warp's stages (members, frontier).
 __device__ __forceinline__ void expand_level(const BulkArgs& a, uint64_t lo, uint64_t nl,
-                                             uint2* wbuf, uint2* lb, uint32_t* mwords,
-                                             uint64_t wid, uint64_t nw, int lane) {
-    (void)lo;
-    WarpStage wm{wbuf, 0u}, wf{wbuf + WSTAGE, 0u};
+                                             uint2* mbuf, uint4* fbuf, uint2* lb,
+                                             uint32_t* mwords, uint64_t wid, uint64_t nw,
+                                             int lane) {
+    WarpStage<uint2> wm{mbuf, 0u};
+    WarpStage<uint4> wf{fbuf, 0u};
     const uint64_t G = __ldcg(a.gp + nl);
     const uint64_t nsc = (G + SCG - 1) / SCG;
     const uint64_t per = (nsc + nw - 1) / nw;
@@ -303,22 +315,31 @@ __device__ __forceinline__ void expand_level(const BulkArgs& a, uint64_t lo, uin
                 }
             uint64_t d[2] = {0, 0};
             uint32_t push = 0;
+            uint4 fi[4];
+            uint2 mi[4];
 #pragma unroll
-            for (int q = 0; q < 2; q++)
+            for (int q = 0; q < 2; q++) {
+                mi[q] = make_uint2(sv[q], u[q]);
                 if ((fr >> q) & 1u) {
-                    d[q] = __ldg(a.rowptr + u[q] + 1) - __ldg(a.rowptr + u[q]);
+                    const uint64_t ub = __ldg(a.rowptr + u[q]), ue = __ldg(a.rowptr + u[q] + 1);
+                    const unsigned long long nt = __ldg(a.node_thr + u[q]);
+                    d[q] = ue - ub;
                     if (d[q]) push |= 1u << q;
+                    fi[q] = make_uint4((uint32_t)ub, (uint32_t)ue,
+                                       sv[q] | (tim_skip_rule(nt, ue - ub) ? 0x80000000u : 0u),
+                                       u[q]);
                     if (cover && marked(a.seed_mark, u[q])) a.slot_flag[sv[q]] = 1u;
                 }
+            }
             slot_add(fr & 1u, sv[0], d[0], 1u, a, lane);
             slot_add((fr >> 1) & 1u, sv[1], d[1], 1u, a, lane);
-            wstage_append4(fr, sv, u, wm, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2, lane);
+            wstage_append4(fr, mi, wm, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2, lane);
             if (cover) {
 #pragma unroll
                 for (int q = 0; q < 2; q++)
                     if (((push >> q) & 1u) && a.slot_flag[sv[q]]) push &= ~(1u << q);
             }
-            wstage_append4(push, sv, u, wf, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1, lane);
+            wstage_append4(push, fi, wf, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1, lane);
         }
         nbuf = 0;
         __syncwarp();
@@ -387,10 +408,11 @@ __device__ __forceinline__ void expand_level(const BulkArgs& a, uint64_t lo, uin
                         if (pos < 0 && mw[w]) pos = w * 32 + 31 - __clz(mw[w]);
                     }
                     gof[k] = t - (q ? S0 + (uint64_t)pos : gs0);
-                    inf[k] = act[k] ? __ldcg(&a.info[i0 + q]) : make_uint4(0u, 0u, 0u, 0u);
+                    inf[k] = act[k] ? __ldcg(&a.F[lo + i0 + q]) : make_uint4(0u, 0u, 0u, 0u);
                 }
                 uint4 tv[4];
                 uint64_t g[4];
+                uint32_t jj[4];
                 bool wk[4];
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
@@ -400,12 +422,13 @@ __device__ __forceinline__ void expand_level(const BulkArgs& a, uint64_t lo, uin
                             !(cover && *(volatile uint32_t*)&a.slot_flag[sl]);
                     tv[k] = wk[k] ? __ldg(reinterpret_cast<const uint4*>(a.thr) + g[k])
                                   : make_uint4(0u, 0u, 0u, 0u);
+                    jj[k] = wk[k] ? __ldg(a.list + a.base + sl) : 0u;
                 }
                 uint32_t lm = 0;  // bit 4k + cc: position 4 g[k] + cc is live
 #pragma unroll
                 for (int k = 0; k < 4; k++) {
                     if (!wk[k]) continue;
-                    const uint64_t sid = a.sid0 + inf[k].w;
+                    const uint64_t sid = a.sid0 + jj[k];
                     const uint4 x = philox4x32_10((uint32_t)sid, (uint32_t)(sid >> 32),
                                                   (uint32_t)g[k], TIM_TAG_IC, a.K);
 #pragma unroll
@@ -449,41 +472,48 @@ __device__ __forceinline__ void expand_level(const BulkArgs& a, uint64_t lo, uin
     if (lane == 0 && exam_acc) atomicAdd(&a.bs->exam, (unsigned long long)exam_acc);
 }
 
+// Shared memory of one warp in the expand kernels: member stage, frontier stage, live
+// queue, boundary mask.
+struct ExpandSmem {
+    uint2* m;
+    uint4* f;
+    uint2* lb;
+    uint32_t* mw;
+};
+
+__device__ __forceinline__ ExpandSmem expand_smem(unsigned char* dsm, int w) {
+    ExpandSmem e;
+    e.f = reinterpret_cast<uint4*>(dsm) + w * WSTAGE;
+    e.m = reinterpret_cast<uint2*>(dsm + 8 * WSTAGE * sizeof(uint4)) + w * WSTAGE;
+    e.lb = reinterpret_cast<uint2*>(dsm + 8 * WSTAGE * (sizeof(uint4) + sizeof(uint2))) + w * LBUF;
+    e.mw = reinterpret_cast<uint32_t*>(dsm + 8 * WSTAGE * (sizeof(uint4) + sizeof(uint2)) +
+                                       8 * LBUF * sizeof(uint2)) + w * 8;
+    return e;
+}
+
 __global__ void __launch_bounds__(256) bulk_expand_kernel(BulkArgs a) {
-    extern __shared__ uint2 dsm[];
-    const int w = threadIdx.x >> 5;
-    uint2* wbuf = dsm + w * 2 * WSTAGE;
-    uint2* lb = dsm + 8 * 2 * WSTAGE + w * LBUF;
-    uint32_t* mw = reinterpret_cast<uint32_t*>(dsm + 8 * (2 * WSTAGE + LBUF)) + w * 8;
-    expand_level(a, a.lvl_lo, a.lvl_n, wbuf, lb, mw,
+    extern __shared__ __align__(16) unsigned char dsm[];
+    const ExpandSmem e = expand_smem(dsm, threadIdx.x >> 5);
+    expand_level(a, a.lvl_lo, a.lvl_n, e.m, e.f, e.lb, e.mw,
                  (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5,
                  ((uint64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
 }
 
-// The level's items under the skip rule, one warp per item. The lanes screen 32 items
-// at a time: by the NG_SKIP flag of the item's group count (from_ng, persistent launch)
-// or from the graph (host-stepped path).
+// The level's items under the skip rule (flag of their frontier record), one warp per
+// item; the lanes screen 32 items at a time.
 __device__ __forceinline__ void skip_level(const BulkArgs& a, uint64_t lo, uint64_t nl,
-                                           bool from_ng, uint64_t wid, uint64_t nw, int lane) {
+                                           uint64_t wid, uint64_t nw, int lane) {
     const bool cover = a.flags & SAMPLE_COVER;
     uint32_t live_acc = 0;
     for (uint64_t base = wid * 32; base < nl; base += nw * 32) {
-        bool sk = false;
-        if (base + lane < nl) {
-            if (from_ng) {
-                sk = (__ldcg(a.ng + base + lane) & NG_SKIP) != 0;
-            } else {
-                const uint32_t v = __ldcg(&a.F[lo + base + lane]).y;
-                sk = skip_rule(__ldg(a.node_thr + v), __ldg(a.rowptr + v), __ldg(a.rowptr + v + 1));
-            }
-        }
+        const bool sk = base + lane < nl && (__ldcg(&a.F[lo + base + lane]).z >> 31);
         uint32_t todo = __ballot_sync(0xffffffffu, sk);
         while (todo) {
         const uint64_t i = base + (uint64_t)(__ffs(todo) - 1);
         todo &= todo - 1;
-        const uint2 it = __ldcg(&a.F[lo + i]);
-        const uint32_t s = it.x, v = it.y;
-        const uint64_t beg = __ldg(a.rowptr + v), end = __ldg(a.rowptr + v + 1);
+        const uint4 it = __ldcg(&a.F[lo + i]);
+        const uint32_t s = it.z & 0x7FFFFFFFu, v = it.w;
+        const uint64_t beg = it.x, end = it.y;
         const unsigned long long nt = __ldg(a.node_thr + v);
         if (cover && *(volatile uint32_t*)&a.slot_flag[s]) continue;
         const uint64_t sid = a.sid0 + __ldg(a.list + a.base + s);
@@ -492,6 +522,7 @@ __device__ __forceinline__ void skip_level(const BulkArgs& a, uint64_t lo, uint6
                            bool fresh = false;
                            uint32_t u = 0;
                            uint64_t ub = 0, ue = 0;
+                           unsigned long long unt = 0;
                            if (lane == 0) {
                                live_acc++;
                                u = __ldg(a.src + p);
@@ -502,6 +533,7 @@ __device__ __forceinline__ void skip_level(const BulkArgs& a, uint64_t lo, uint6
                                if (fresh) {
                                    ub = __ldg(a.rowptr + u);
                                    ue = __ldg(a.rowptr + u + 1);
+                                   unt = __ldg(a.node_thr + u);
                                    atomicAdd(&a.slot_width[s], ue - ub);
                                    atomicAdd(&a.slot_cnt[s], 1u);
                                    if (cover && marked(a.seed_mark, u)) a.slot_flag[s] = 1u;
@@ -510,8 +542,11 @@ __device__ __forceinline__ void skip_level(const BulkArgs& a, uint64_t lo, uint6
                            warp_append(fresh, s, u, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2,
                                        lane);
                            const bool push = fresh && ue > ub && !(cover && a.slot_flag[s]);
-                           warp_append(push, s, u, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1,
-                                       lane);
+                           const uint4 item = make_uint4(
+                               (uint32_t)ub, (uint32_t)ue,
+                               s | (tim_skip_rule(unt, ue - ub) ? 0x80000000u : 0u), u);
+                           warp_append_f(push, item, &a.bs->f_count, a.F, a.fcap, &a.bs->err,
+                                         lane);
                            return false;
                        });
         }
@@ -521,7 +556,7 @@ __device__ __forceinline__ void skip_level(const BulkArgs& a, uint64_t lo, uint6
 }
 
 __global__ void __launch_bounds__(256) bulk_skip_kernel(BulkArgs a) {
-    skip_level(a, a.lvl_lo, a.lvl_n, false, (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5,
+    skip_level(a, a.lvl_lo, a.lvl_n, (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5,
                ((uint64_t)gridDim.x * blockDim.x) >> 5, threadIdx.x & 31);
 }
 
@@ -567,7 +602,7 @@ __device__ __forceinline__ unsigned long long block_excl_scan(unsigned long long
 // block appends to F again, so all blocks agree on them; on a timeout or a full list
 // every block leaves at the same barrier or the next one.
 __global__ void __launch_bounds__(256, LEVELS_MIN_BLOCKS) bulk_levels_kernel(BulkArgs a) {
-    extern __shared__ uint2 dsm[];
+    extern __shared__ __align__(16) unsigned char dsm[];
     __shared__ unsigned long long red[32];
     const int lane = threadIdx.x & 31;
     const uint64_t wid = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
@@ -609,7 +644,7 @@ __global__ void __launch_bounds__(256, LEVELS_MIN_BLOCKS) bulk_levels_kernel(Bul
         const uint64_t ib = min((uint64_t)blockIdx.x * per, nl), ie = min(ib + per, nl);
         unsigned long long sum = 0;
         for (uint64_t i = ib + threadIdx.x; i < ie; i += blockDim.x) {
-            const uint32_t g = item_prepare(a, lo, i);
+            const uint32_t g = item_groups(a, lo, i);
             a.ng[i] = g;
             sum += g & ~NG_SKIP;
         }
@@ -641,12 +676,10 @@ __global__ void __launch_bounds__(256, LEVELS_MIN_BLOCKS) bulk_levels_kernel(Bul
         lap(ns_wait);
         // (C) expand: in-lists by groups over all warps, skip-rule lists by one warp each
         {
-            const int w = threadIdx.x >> 5;
-            expand_level(a, lo, nl, dsm + w * 2 * WSTAGE, dsm + 8 * 2 * WSTAGE + w * LBUF,
-                         reinterpret_cast<uint32_t*>(dsm + 8 * (2 * WSTAGE + LBUF)) + w * 8,
-                         wid, nw, lane);
+            const ExpandSmem e = expand_smem(dsm, threadIdx.x >> 5);
+            expand_level(a, lo, nl, e.m, e.f, e.lb, e.mw, wid, nw, lane);
         }
-        skip_level(a, lo, nl, true, wid, nw, lane);
+        skip_level(a, lo, nl, wid, nw, lane);
         lap(ns_exp);
         if (!grid_barrier(a.bar, err, a.wait_limit)) return;
         lap(ns_wait);
@@ -759,10 +792,9 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
     TIM_TRY(tim_ensure(ctx, ctx->bulk_slot, (size_t)smax * 40));
     if (ctx->bulk_fcap == 0) ctx->bulk_fcap = 1 << 22;
     if (ctx->bulk_mcap == 0) ctx->bulk_mcap = 1 << 22;
-    TIM_TRY(tim_ensure(ctx, ctx->bulk_F, ctx->bulk_fcap * sizeof(uint2)));
+    TIM_TRY(tim_ensure(ctx, ctx->bulk_F, ctx->bulk_fcap * sizeof(uint4)));
     TIM_TRY(tim_ensure(ctx, ctx->bulk_M, ctx->bulk_mcap * sizeof(uint2)));
     TIM_TRY(tim_ensure(ctx, ctx->bulk_ng, ctx->bulk_fcap * sizeof(uint32_t)));
-    TIM_TRY(tim_ensure(ctx, ctx->bulk_info, ctx->bulk_fcap * sizeof(uint4)));
     TIM_TRY(tim_ensure(ctx, ctx->bulk_gp, (ctx->bulk_fcap + 1) * sizeof(uint64_t)));
     TIM_TRY(tim_ensure(ctx, ctx->bulk_scal, sizeof(BulkScalars)));
     CUDA_TRY(ctx, cudaFuncSetAttribute(bulk_levels_kernel,
@@ -828,12 +860,11 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
         const uint32_t bs = std::min<uint32_t>(S, count - done);
         a.base = done;
         a.S = bs;
-        a.F = (uint2*)ctx->bulk_F.p;
+        a.F = (uint4*)ctx->bulk_F.p;
         a.M = (uint2*)ctx->bulk_M.p;
         a.fcap = ctx->bulk_fcap;
         a.mcap = ctx->bulk_mcap;
         a.ng = (uint32_t*)ctx->bulk_ng.p;
-        a.info = (uint4*)ctx->bulk_info.p;
         a.gp = (uint64_t*)ctx->bulk_gp.p;
         CUDA_TRY(ctx, cudaMemsetAsync(a.bs, 0, sizeof(BulkScalars), ctx->stream));
         bulk_init_kernel<<<(bs + 255) / 256, 256, 0, ctx->stream>>>(a);
@@ -893,13 +924,11 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
             tim_free(ctx->bulk_F);
             tim_free(ctx->bulk_M);
             tim_free(ctx->bulk_ng);
-            tim_free(ctx->bulk_info);
             tim_free(ctx->bulk_gp);
-            TIM_TRY(tim_ensure(ctx, ctx->bulk_F, ctx->bulk_fcap * sizeof(uint2)));
+            TIM_TRY(tim_ensure(ctx, ctx->bulk_F, ctx->bulk_fcap * sizeof(uint4)));
             TIM_TRY(tim_ensure(ctx, ctx->bulk_M, ctx->bulk_mcap * sizeof(uint2)));
             TIM_TRY(tim_ensure(ctx, ctx->bulk_ng, ctx->bulk_fcap * sizeof(uint32_t)));
-            TIM_TRY(tim_ensure(ctx, ctx->bulk_info, ctx->bulk_fcap * sizeof(uint4)));
-            TIM_TRY(tim_ensure(ctx, ctx->bulk_gp, (ctx->bulk_fcap + 1) * sizeof(uint64_t)));
+                    TIM_TRY(tim_ensure(ctx, ctx->bulk_gp, (ctx->bulk_fcap + 1) * sizeof(uint64_t)));
             continue;
         }
         bulk_finalize_kernel<<<(bs + 255) / 256, 256, 0, ctx->stream>>>(a);
