@@ -1,11 +1,16 @@
-"""Benchmark: end-to-end TIM+ on a directed R-MAT scale-20 graph, once under IC weighted
-cascade and once under LT with 1/indeg in-weights (k = 50, eps = 0.1, l = 1).
+"""Benchmark of the TIM+ hot path on one GB300 (or N, as independent replicas).
 
-One step = for each model: build G^T from the device-resident out-CSR
-(tim_load_graph_device) and run TIM+ (tim_run: Algorithm 2 -> Algorithm 3 -> theta ->
-Algorithm 1). The metric is RR sets generated per second over the whole step.
+Default workload (the largest configuration, the size of the paper's Twitter graph in
+Section 7): a directed Chung-Lu graph with 41.6M nodes and 1.4B edges (exponent 2.1),
+IC trivalency (p per edge from {0.1, 0.01, 0.001}), k = 50, eps = 0.2, l = 1. One step
+= build G^T from the device-resident out-CSR (tim_load_graph_device) and run TIM+
+(tim_run: Algorithm 2 -> Algorithm 3 -> theta -> Algorithm 1). The metric is RR sets
+generated per second over the whole step. The R-MAT scale-20 workload (IC weighted
+cascade then LT 1/indeg, k = 50, eps = 0.1) rides along as a nested object, and is the
+headline with --workload c2.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c3|c2]
 
 Prints one JSON line (rank 0). Under torchrun every rank runs its own independent
 TIM+ step on its own GPU with a rank-specific seed (weak scaling, no data exchange).
@@ -29,14 +34,14 @@ sys.path.insert(0, ROOT)
 from paper_1404_0900_gb300 import inputs, start_round  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-# DRAM bytes (read + write) per RR-set member of the IC sampler passes 1 and 2, from a
-# one-pass ncu capture (`-k regex:rr_team_kernel`) of the full-size run `bench.py
-# --steps 1 --warmup 1 --no-e2e --no-cpu-baseline --no-batch --no-learned`
-# (dram__bytes_read.sum + dram__bytes_write.sum over the timed step's launches of the
-# pass / the members that pass produced in that step); the traffic of one launch is
-# scaled from it by members. None where no capture exists for the current kernel.
-DRAM_BYTES_PER_MEMBER = {1: 70.5, 2: 275.1, 3: None}
+# DRAM bytes (read + write) per RR-set member of the IC sampler passes, from a one-pass
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the pass's kernel on the
+# workload the bench times, divided by the members that pass produced; the traffic of
+# one launch is scaled from it by members. None where no capture of the current kernel
+# exists.
+DRAM_BYTES_PER_MEMBER = {1: None, 2: None, 3: None}
 FALLBACK_HBM_GBS = 6800.0
+METRIC = "RR sets/s (TIM+ end to end, graph load included)"
 L2_FLUSH_BYTES = 512 << 20
 
 
@@ -46,6 +51,12 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["c3", "c2"], default="c3",
+                   help="c3: TIM+ on the 41.6M-node / 1.4B-edge Chung-Lu graph, IC "
+                        "trivalency, k=50, eps=0.2 (the headline; the c2 line rides along "
+                        "nested); c2: TIM+ on R-MAT --scale, IC and LT, --k, --eps")
+    p.add_argument("--no-c2", action="store_true",
+                   help="with --workload c3: skip the nested R-MAT scale-20 line")
     p.add_argument("--scale", type=int, default=20)
     p.add_argument("--k", type=int, default=50)
     p.add_argument("--eps", type=float, default=0.1)
@@ -53,20 +64,19 @@ def parse_args(argv=None):
     p.add_argument("--seed", type=int, default=1)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-seconds", type=float, default=12.0,
-                   help="target CPU time of the oracle baseline sample")
+    p.add_argument("--cpu-seconds", type=float, default=20.0,
+                   help="cap on the CPU time of the oracle's RR-set sample (c3 baseline)")
     p.add_argument("--no-batch", action="store_true",
                    help="skip the 64-query batched-vs-plain comparison")
     p.add_argument("--batch-queries", type=int, default=64)
     p.add_argument("--no-learned", action="store_true",
                    help="skip the learned-start-round comparisons")
-    p.add_argument("--mode", choices=["timplus", "sample", "batch", "learned", "c3", "spread"],
+    p.add_argument("--mode", choices=["timplus", "sample", "batch", "learned", "spread"],
                    default="timplus",
-                   help="timplus: the TIM+ step (default); sample: only RR-set generation "
-                        "(tim_sample_rr of --theta NodeSelection sets), for profiling; "
-                        "c3: TIM+ on the 41.6M-node / 1.4B-edge Chung-Lu graph, IC "
-                        "trivalency, k=50, eps=0.2; spread: forward Monte-Carlo spread "
-                        "of TIM+'s seeds (--cascades) against the RR estimate")
+                   help="timplus: the TIM+ step of --workload (default); sample: only RR-set "
+                        "generation (tim_sample_rr of --theta NodeSelection sets on R-MAT "
+                        "--scale), for profiling; spread: forward Monte-Carlo spread of "
+                        "TIM+'s seeds (--cascades) against the RR estimate")
     p.add_argument("--theta", type=int, default=1_000_000)
     p.add_argument("--cascades", type=int, default=10_000)
     p.add_argument("--model", choices=["ic", "lt"], default="ic")
@@ -178,7 +188,9 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- our arm
 
-def run_ours(args):
+def run_c2_line(args, nested: bool = False):
+    """The R-MAT workload's TIM+ step (IC then LT). nested: a sub-object of the c3
+    line (no process group of its own; batched and learned comparisons left out)."""
     import torch
 
     from paper_1404_0900_gb300 import tim
@@ -186,7 +198,7 @@ def run_ours(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     device = torch.device("cuda", local)
-    dist = init_dist(world, "nccl")
+    dist = None if nested else init_dist(world, "nccl")
     seed = args.seed + rank
     g, w_ic, w_lt = workload(args)
     stream = torch.cuda.Stream(device=device)
@@ -286,30 +298,15 @@ def run_ours(args):
         dist.destroy_process_group()
     if rank != 0:
         return None
+    del flush
+    torch.cuda.empty_cache()
 
     # roofline of the dominant kernel: the IC sampler pass with the most device time
-    p = prof_ic
-    dom = max((1, 2, 3), key=lambda i: p[f"pass{i}_ms"])
-    names = {1: "rr_team_kernel<IC, Cap<256,9>, pass 1> (shared-memory hash, warp per set)",
-             2: "rr_team_kernel<IC, Cap<8192,14>, pass 2> (global-arena hash, team per set)",
-             3: "bulk level-synchronous IC pass (pass 3)"}
-    alg_bytes = sampler_bytes(p, dom)
-    launches_dom = max(p[f"pass{dom}_launches"], 1)
-    per_launch_bytes = alg_bytes / launches_dom
-    per_launch_ms = p[f"pass{dom}_ms"] / launches_dom
-    peaks = measured_peaks()
-    if peaks and peaks.get("hbm_gbs"):
-        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
-    else:
-        peak, peak_src = FALLBACK_HBM_GBS, "fallback"
-    ms_dom = p[f"pass{dom}_ms"]
-    achieved = alg_bytes / (ms_dom / 1e3) / 1e9 if ms_dom > 0 else 0.0
-    ratio = DRAM_BYTES_PER_MEMBER.get(dom)
-    traffic = ratio * p[f"pass{dom}_members"] / launches_dom if ratio else None
+    roofline = sampler_roofline(prof_ic)
     ic = per_model[tim.TIM_IC][-1]
     lt = per_model[tim.TIM_LT][-1]
     line = {
-        "metric": "RR sets/s (TIM+ end to end: IC + LT)",
+        "metric": METRIC,
         "value": sets_all / sec,
         "unit": "RR sets/s",
         "n_gpus": world,
@@ -322,7 +319,8 @@ def run_ours(args):
         "dtype": "u32/int64 (FP64 for kappa and theta)",
         "data": "synthetic (seeded R-MAT, no dataset)",
         "config": config_dict(args, g, world),
-        "gteps_width": widths / (total_ms / 1e3) / 1e9,
+        "width_rate": {"value": widths / (total_ms / 1e3), "unit": "in-edges of R's nodes "
+                       "(w(R), Eq. 1) per second; skipped lists counted in full, so not GTEPS"},
         "gteps_examined": sum(prof_ic[f"pass{i}_examined"] + prof_lt[f"pass{i}_examined"]
                               for i in (1, 2, 3)) / (total_ms / 1e3) / 1e9,
         "tim_plus_ms": {"IC": statistics.mean(s["ms_total"] for s in per_model[tim.TIM_IC]),
@@ -333,14 +331,7 @@ def run_ours(args):
                                              "ms_select_greedy")},
         "theta": {"IC": ic["theta"], "LT": lt["theta"]},
         "kpt_plus": {"IC": ic["kpt_plus"], "LT": lt["kpt_plus"]},
-        "roofline": {"kernel": names[dom], "bound": "hbm",
-                     "achieved": achieved, "peak": peak, "peak_source": peak_src,
-                     "unit": "GB/s", "frac": achieved / peak,
-                     "bytes_per_launch": per_launch_bytes, "ms_per_launch": per_launch_ms,
-                     "traffic": traffic,
-                     "traffic_note": "DRAM bytes per launch: bytes per member from the "
-                                     "full-size one-pass ncu capture of this workload x the "
-                                     "members per launch (null: no capture of this kernel)"},
+        "roofline": roofline,
         "sampler_profile": {"IC": prof_ic, "LT": prof_lt},
         "autotune": tuning,
         "clocks": clk,
@@ -348,8 +339,9 @@ def run_ours(args):
         "e2e": e2e,
     }
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(args, g, w_ic, w_lt,
-                                            n_ic=ic["sets_total"], n_lt=lt["sets_total"])
+        line["cpu_baseline"] = cpu_baseline_timplus(args, g, w_ic, w_lt, per_model)
+    if nested:
+        return line
     if not args.no_batch and world == 1:
         line["batched_vs_plain"] = run_batch_compare(args)
     if not args.no_learned and world == 1:
@@ -364,6 +356,39 @@ def sampler_bytes(p: dict, i: int) -> float:
     rule plus the live ones the rule finds (in-edges it skips are not touched)."""
     return (8.0 * (p[f"pass{i}_members"] + p[f"pass{i}_sets"]) + 8.0 * p[f"pass{i}_examined"]
             + 4.0 * p[f"pass{i}_members"] + 8.0 * p[f"pass{i}_sets"])
+
+
+def sampler_roofline(p: dict) -> dict:
+    """Roofline of the IC sampler pass with the most device time. Its time is the
+    pass's own kernels (for the heavy-set pass: the persistent launches alone), its
+    bytes the algorithmic bytes of sampler_bytes, per launch (heavy pass: per batch)."""
+    def kernel_ms(i):
+        return p["pass3_ms_kernel"] if i == 3 and p.get("pass3_batches") else p[f"pass{i}_ms"]
+
+    def launches(i):
+        return max(p["pass3_batches"] if i == 3 and p.get("pass3_batches")
+                   else p[f"pass{i}_launches"], 1)
+    dom = max((1, 2, 3), key=kernel_ms)
+    names = {1: "rr_team_kernel<IC, Cap<256,9>, pass 1> (shared-memory hash, warp per set)",
+             2: "rr_team_kernel<IC, Cap<8192,14>, pass 2> (global-arena hash, team per set)",
+             3: "bulk_levels_kernel (heavy sets: all BFS levels of a batch in one "
+                "persistent cooperative launch)"}
+    alg = sampler_bytes(p, dom)
+    ms, n = kernel_ms(dom), launches(dom)
+    peaks = measured_peaks()
+    if peaks and peaks.get("hbm_gbs"):
+        peak, src = float(peaks["hbm_gbs"]), "measured"
+    else:
+        peak, src = FALLBACK_HBM_GBS, "fallback"
+    achieved = alg / (ms / 1e3) / 1e9 if ms > 0 else 0.0
+    ratio = DRAM_BYTES_PER_MEMBER.get(dom)
+    return {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak,
+            "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
+            "bytes_per_launch": alg / n, "ms_per_launch": ms / n, "launches": n,
+            "traffic": ratio * p[f"pass{dom}_members"] / n if ratio else None,
+            "traffic_note": "DRAM bytes per launch: bytes per member from a one-pass ncu "
+                            "capture of this kernel x the members per launch (null: no "
+                            "capture of the current kernel)"}
 
 
 # --------------------------------------------------------- the CPU oracle arm
@@ -397,46 +422,120 @@ def mix_rate(rates, n_ic, n_lt):
     return (n_ic + n_lt) / t
 
 
-def cpu_baseline(args, g, w_ic, w_lt, n_ic, n_lt):
+def cpu_baseline_timplus(args, g, w_ic, w_lt, per_model) -> dict:
+    """The oracle's TIM+ end to end on the same graph and seed, IC then LT, on all host
+    threads, with seconds per phase (Algorithm 2, Algorithm 3, Algorithm 1's sampling
+    and greedy together); value = RR sets of all phases / seconds."""
     from oracle import oracle as O
     nth = O.host_threads()
-    rates = oracle_rates(args, g, w_ic, w_lt, args.cpu_seconds, nth)
-    return {"value": mix_rate(rates, n_ic, n_lt), "unit": "RR sets/s", "cores": nth,
+    out, sets_all, secs_all = {}, 0, 0.0
+    for name, model, w in (("IC", O.IC, w_ic), ("LT", O.LT, w_lt)):
+        og = O.load_graph(g.n, g.rowptr, g.dst, w, model)
+        t0 = time.perf_counter()
+        kpt = O.kpt_estimation(og, args.k, args.ell, args.seed, nth)
+        t1 = time.perf_counter()
+        ref = O.refine_kpt(og, args.k, args.ell, args.eps, args.seed, kpt, nth)
+        t2 = time.perf_counter()
+        theta = O.theta_from(g.n, args.k, args.eps, args.ell, ref.kpt_plus)
+        O.node_selection(og, args.k, theta, args.seed, nth)
+        t3 = time.perf_counter()
+        sets = kpt.sets_generated + ref.theta_prime + theta
+        out[name] = {"s_kpt": t1 - t0, "s_refine": t2 - t1, "s_select": t3 - t2,
+                     "sets": sets, "theta": theta}
+        sets_all += sets
+        secs_all += t3 - t0
+        del og
+    return {"value": sets_all / secs_all, "unit": "RR sets/s", "cores": nth, "kind": "oracle",
+            "sample": f"oracle TIM+ end to end, IC and LT, on the same graph and seed "
+                      f"({nth} threads): {secs_all:.1f} s for {sets_all} RR sets",
+            "phases_s": out}
+
+
+def cpu_baseline_c3(args, n, rowptr, dst, w) -> dict:
+    """The oracle on the largest configuration: a fixed sample of RR sets with
+    NodeSelection ids (up to 10^6, in chunks of 50,000, until --cpu-seconds) plus one
+    Algorithm 2 round (round 10: c_10 sets, kappa sum), on all host threads; value =
+    their RR sets / their seconds. The oracle's own G^T build is not timed."""
+    from oracle import oracle as O
+    nth = O.host_threads()
+    t0 = time.perf_counter()
+    og = O.load_graph(n, rowptr, dst, w, O.IC)
+    load_s = time.perf_counter() - t0
+    done, secs, chunk = 0, 0.0, 50_000
+    while done < 1_000_000 and secs < args.cpu_seconds:
+        t = time.perf_counter()
+        O.sample(og, args.seed, O.make_sid(3, 0, done), chunk, nth)
+        secs += time.perf_counter() - t
+        done += chunk
+    rnd = 10
+    c = O.c_i(n, args.ell, rnd)
+    t = time.perf_counter()
+    O.kappa_sum(og, 50, args.seed, O.make_sid(1, rnd, 0), c, nth)
+    rsecs = time.perf_counter() - t
+    del og
+    return {"value": (done + c) / (secs + rsecs), "unit": "RR sets/s", "cores": nth,
             "kind": "oracle",
-            "sample": (f"oracle RR-set generation on the same graph: {rates['IC'][1]} IC sets in "
-                       f"{rates['IC'][2]:.1f} s and {rates['LT'][1]} LT sets in "
-                       f"{rates['LT'][2]:.1f} s ({nth} threads), rate weighted to one step's "
-                       f"mix of {n_ic} IC and {n_lt} LT sets")}
+            "sample": f"{done} RR sets (NodeSelection ids) in {secs:.1f} s and Algorithm 2 "
+                      f"round {rnd} ({c} sets, kappa sum) in {rsecs:.1f} s on the same graph "
+                      f"({nth} threads); the oracle's own G^T build ({load_s:.0f} s) untimed"}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, on the host cores, on the same
+    workload. Each step is a bounded sample of the workload's RR sets (NodeSelection set
+    ids, fresh ids every step): c3, 50,000 sets of the Chung-Lu graph (drawn with the
+    same generator, on the GPU, and copied to the host; the oracle builds its own G^T,
+    untimed); c2, about 2 s of IC and LT sets, the rate weighted 7:2 (the GPU step's
+    mix). Rank 0 alone runs; the other ranks exit at once."""
     rank, world, _ = dist_env()
     if rank != 0:
         return None
     from oracle import oracle as O
-    g, w_ic, w_lt = workload(args)
     nth = O.host_threads()
-    # one step = a bounded sample of the workload's RR sets (IC:LT in the GPU step's
-    # proportion, about 7:2), about two seconds of oracle time
-    per_step = max(1.0, 2.0)
-    for _ in range(args.warmup):
-        oracle_rates(args, g, w_ic, w_lt, per_step / 4, nth)
     vals, secs = [], 0.0
-    for _ in range(args.steps):
-        t0 = time.perf_counter()
-        r = oracle_rates(args, g, w_ic, w_lt, per_step, nth)
-        secs += time.perf_counter() - t0
-        vals.append(mix_rate(r, 7, 2))
+    if args.workload == "c3":
+        import torch
+        g, w = c3_graph(torch.device("cuda", 0))
+        n, m = g.n, g.m
+        rowptr, dst, wh = g.rowptr.cpu().numpy(), g.dst.cpu().numpy(), w.cpu().numpy()
+        del g, w
+        torch.cuda.empty_cache()
+        og = O.load_graph(n, rowptr, dst, wh, O.IC)
+        del rowptr, dst, wh
+        per = 50_000
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            O.sample(og, args.seed, O.make_sid(3, 0, i * per), per, nth)
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                secs += dt
+                vals.append(per / dt)
+        config = c3_config(world, n, m)
+        timed = (f"per step: oracle RR-set generation of {per} sets of the same graph "
+                 f"(NodeSelection ids), {nth} threads")
+        data = "synthetic (seeded Chung-Lu drawn on the GPU, no dataset)"
+    else:
+        g, w_ic, w_lt = workload(args)
+        per_step = 2.0
+        for _ in range(args.warmup):
+            oracle_rates(args, g, w_ic, w_lt, per_step / 4, nth)
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            r = oracle_rates(args, g, w_ic, w_lt, per_step, nth)
+            secs += time.perf_counter() - t0
+            vals.append(mix_rate(r, 7, 2))
+        config = config_dict(args, g, world)
+        timed = ("per step: oracle RR-set generation, IC and LT sets of NodeSelection ids, "
+                 f"about 1 s each, rate weighted 7:2, {nth} threads")
+        data = "synthetic (seeded R-MAT, no dataset)"
     v = statistics.mean(vals)
-    return {"impl": "reference", "metric": "RR sets/s (TIM+ end to end: IC + LT)", "value": v,
+    return {"impl": "reference", "metric": METRIC, "timed": timed, "value": v,
             "unit": "RR sets/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": secs * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "u32/int64 (FP64 for kappa)",
-            "data": "synthetic (seeded R-MAT, no dataset)",
-            "config": config_dict(args, g, world),
+            "vs_baseline": None, "dtype": "u32/int64 (FP64 for kappa)", "data": data,
+            "config": config,
             "cpu_baseline": {"value": v, "unit": "RR sets/s", "cores": nth, "kind": "oracle",
-                             "sample": "per step: oracle RR-set generation, IC and LT sets of "
-                                       "NodeSelection ids, about 1 s each, rate weighted 7:2"},
+                             "sample": timed},
             "e2e": {"value": v, "unit": "RR sets/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
 
@@ -486,66 +585,160 @@ def run_sample_only(args):
             "GTEPS (in-edges examined)": width / (ms / 1e3) / 1e9, "passes": passes}
 
 
-def run_c3(args):
-    """TIM+ on the largest configuration: directed Chung-Lu, 41.6M nodes, 1.4B edges,
-    exponent 2.1, IC trivalency (p per edge from {0.1, 0.01, 0.001}), k = 50, eps = 0.2,
-    l = 1, drawn and loaded on the device. --steps runs after --warmup, each timed by
-    CUDA events on the library's stream (the graph, 11 GB as G^T, is far larger than L2)."""
+def c3_config(world: int, n: int, m: int) -> dict:
+    return {"workload": "TIM+ on a directed Chung-Lu graph of Twitter's size (41.6M nodes, "
+                        "1.4B edges, exponent 2.1), IC trivalency p in {0.1, 0.01, 0.001}, "
+                        "k=50, eps=0.2, l=1; a step = G^T build from the device out-CSR + TIM+",
+            "n": n, "m": m, "k": 50, "eps": 0.2, "ell": 1.0, "models": ["IC"],
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
+            "l2": f"inputs larger than L2 (G^T about 11 GB), and {L2_FLUSH_BYTES >> 20} MiB "
+                  f"written between timed steps"}
+
+
+def c3_graph(device):
+    """The largest configuration's graph and trivalency weights, drawn on `device`."""
+    g = inputs.chung_lu_c3_device(seed=1, device=device)
+    return g, inputs.trivalency_device(g, seed=2)
+
+
+def run_c3_line(args):
+    """The headline: TIM+ on the largest configuration (see the module comment)."""
     import torch
 
     from paper_1404_0900_gb300 import tim
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = init_dist(world, "nccl")
+    seed = args.seed + rank
+    k, eps, ell = 50, 0.2, args.ell
+    stream = torch.cuda.Stream(device=device)
     torch.cuda.set_stream(stream)
-    k, eps = 50, 0.2
     t0 = time.perf_counter()
-    g = inputs.chung_lu_c3_device(seed=1)
-    w = inputs.trivalency_device(g, seed=2)
+    g, w = c3_graph(device)
     torch.cuda.synchronize()
     gen_s = time.perf_counter() - t0
     n, m = g.n, g.m
-    with tim.Engine(0, stream) as eng:
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=device)
+    eng = tim.Engine(local, stream)
+
+    def step():
+        tim.tim_load_graph_device(eng.ctx, n, m, g.rowptr, g.dst, w, tim.TIM_IC)
+        return tim.tim_run(eng.ctx, k, eps, ell, seed)
+
+    tim.tim_load_graph_device(eng.ctx, n, m, g.rowptr, g.dst, w, tim.TIM_IC)
+    tuning = tim.tim_autotune(eng.ctx, 200_000, seed)
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    tim.tim_get_profile(eng.ctx, reset=True)
+    launches0 = tim.tim_launch_count(eng.ctx)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    total_ms, total_sets, runs = 0.0, 0, []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        tim.tim_load_graph_device(eng.ctx, g.n, g.m, g.rowptr, g.dst, w, tim.TIM_IC)
+        seeds, frac, st = step()
         e1.record(stream)
         e1.synchronize()
-        load_ms = e0.elapsed_time(e1)
-        del g, w
-        torch.cuda.empty_cache()
-        tuning = tim.tim_autotune(eng.ctx, 200_000, args.seed)
-        for _ in range(args.warmup):
-            tim.tim_run(eng.ctx, k, eps, args.ell, args.seed)
-        clocks = ClockSampler(0)
-        clocks.start()
-        runs = []
-        launches0 = tim.tim_launch_count(eng.ctx)
+        total_ms += e0.elapsed_time(e1)
+        total_sets += st["sets_total"]
+        runs.append(st)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    launches = tim.tim_launch_count(eng.ctx) - launches0
+    prof = tim.tim_get_profile(eng.ctx)
+    sec, sets_all = reduce_step_results(dist, device, total_ms / 1e3, float(total_sets))
+
+    # end to end through the public API with host buffers (pinned), copies timed
+    e2e, host = None, None
+    if not args.no_e2e or (rank == 0 and not args.no_cpu_baseline):
+        host = (g.rowptr.cpu().pin_memory(), g.dst.cpu().pin_memory(), w.cpu().pin_memory())
+    del g, w
+    torch.cuda.empty_cache()
+    if not args.no_e2e:
+        h_rowptr, h_dst, h_w = host
+        h_seeds = torch.zeros(k, dtype=torch.int32).pin_memory()
+
+        def step_host():
+            tim.lib().tim_load_graph(eng.ctx, n, m, tim._ptr(h_rowptr), tim._ptr(h_dst),
+                                     tim._ptr(h_w), tim.TIM_IC)
+            _, _, st = tim.tim_run(eng.ctx, k, eps, ell, seed, seeds_out=h_seeds.numpy())
+            return st["sets_total"]
+
+        step_host()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t_ms, e_sets = 0.0, 0
         for _ in range(args.steps):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            seeds, frac, st = tim.tim_run(eng.ctx, k, eps, args.ell, args.seed)
-            e1.record(stream)
-            e1.synchronize()
-            runs.append((e0.elapsed_time(e1), st))
-        launches = tim.tim_launch_count(eng.ctx) - launches0
-        clk = clocks.stop()
-    ms = sum(r[0] for r in runs)
-    st = runs[-1][1]
-    return {"mode": "c3", "metric": "RR sets/s (TIM+ end to end, IC trivalency)",
-            "value": sum(r[1]["sets_total"] for r in runs) / (ms / 1e3), "unit": "RR sets/s",
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-            "higher_is_better": True, "data": "synthetic (seeded Chung-Lu, no dataset)",
-            "config": {"workload": "TIM+ on a directed Chung-Lu graph (exponent 2.1), IC "
-                                   "trivalency {0.1, 0.01, 0.001}, k=50, eps=0.2, l=1",
-                       "n": n, "m": m, "k": k, "eps": eps, "ell": args.ell,
-                       "l2": "inputs larger than L2"},
-            "phases_ms": {x: st[x] for x in ("ms_kpt", "ms_refine", "ms_select_sample",
-                                             "ms_select_greedy")},
-            "kpt_round": st["kpt_round"], "kpt_star": st["kpt_star"], "kpt_plus": st["kpt_plus"],
-            "theta": st["theta"], "sets_total": st["sets_total"],
-            "members_select": st["members_select"], "width_total": st["width_total"],
-            "generate_s": gen_s, "load_ms": load_ms, "autotune": tuning, "clocks": clk,
-            "gpu_launches": launches}
+            flush.zero_()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            e_sets += step_host()
+            torch.cuda.synchronize()
+            t_ms += (time.perf_counter() - t1) * 1e3
+        esec, esets = reduce_step_results(dist, device, t_ms / 1e3, float(e_sets))
+        h2d = h_rowptr.numel() * 8 + h_dst.numel() * 4 + h_w.numel() * 4
+        e2e = {"value": esets / esec, "unit": "RR sets/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": k * 4, "ms_per_step": t_ms / args.steps}
+    eng.close()
+    del flush
+    torch.cuda.empty_cache()
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    st = runs[-1]
+    line = {
+        "metric": METRIC,
+        "value": sets_all / sec,
+        "unit": "RR sets/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u32/int64 (FP64 for kappa and theta)",
+        "data": "synthetic (seeded Chung-Lu drawn on the GPU, no dataset)",
+        "config": c3_config(world, n, m),
+        "gteps_examined": sum(prof[f"pass{i}_examined"] for i in (1, 2, 3)) / sec / 1e9,
+        "tim_plus_ms": statistics.mean(r["ms_total"] for r in runs),
+        "phases_ms": {x: st[x] for x in ("ms_kpt", "ms_refine", "ms_select_sample",
+                                         "ms_select_greedy")},
+        "kpt_round": st["kpt_round"], "kpt_star": st["kpt_star"], "kpt_plus": st["kpt_plus"],
+        "theta": st["theta"], "sets_per_step": st["sets_total"],
+        "members_select": st["members_select"],
+        "roofline": sampler_roofline(prof),
+        "sampler_profile": prof,
+        "autotune": tuning,
+        "generate_s": gen_s,
+        "clocks": clk,
+        "gpu_launches": launches,
+        "e2e": e2e,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_c3(args, n, host[0].numpy(), host[1].numpy(),
+                                               host[2].numpy())
+    del host
+    if world == 1 and not args.no_c2:
+        line["c2"] = run_c2_line(args, nested=True)
+    if not args.no_batch and world == 1:
+        line["batched_vs_plain"] = run_batch_compare(args)
+    if not args.no_learned and world == 1:
+        line["learned_vs_plain"] = run_learned_compare(args)
+    return line
 
 
 def run_spread(args):
@@ -795,13 +988,13 @@ def main(argv=None):
     if args.mode == "learned" and args.impl == "ours":
         print(json.dumps(run_learned_compare(args)), flush=True)
         return
-    if args.mode == "c3" and args.impl == "ours":
-        print(json.dumps(run_c3(args)), flush=True)
-        return
     if args.mode == "spread" and args.impl == "ours":
         print(json.dumps(run_spread(args)), flush=True)
         return
-    line = run_reference(args) if args.impl == "reference" else run_ours(args)
+    if args.impl == "reference":
+        line = run_reference(args)
+    else:
+        line = run_c3_line(args) if args.workload == "c3" else run_c2_line(args)
     if line is not None:
         print(json.dumps(line), flush=True)
 

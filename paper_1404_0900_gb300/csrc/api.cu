@@ -163,6 +163,8 @@ int tim_create(tim_ctx** out, int device, void* cuda_stream) {
         if (cudaEventCreate(&ctx->ev[i]) != cudaSuccess) rc = TIM_ERR_CUDA;
     for (int i = 0; rc == TIM_OK && i < 4; i++)
         if (cudaEventCreate(&ctx->kev[i]) != cudaSuccess) rc = TIM_ERR_CUDA;
+    for (int i = 0; rc == TIM_OK && i < 2; i++)
+        if (cudaEventCreate(&ctx->bev[i]) != cudaSuccess) rc = TIM_ERR_CUDA;
     if (rc != TIM_OK) {
         tim_destroy(ctx);
         return rc;
@@ -178,7 +180,7 @@ int tim_destroy(tim_ctx* ctx) {
     if (ctx->stream) cudaStreamSynchronize(ctx->stream);
     DevBuf* bufs[] = {&ctx->rowptr,   &ctx->src,        &ctx->thr,       &ctx->pool,
                       &ctx->node_thr,  &ctx->qtab,      &ctx->ld_keys,   &ctx->ld_vals,
-                      &ctx->ld_indeg,  &ctx->ld_lt_t,   &ctx->ld_lt_e,   &ctx->ld_nonuni,
+                      &ctx->ld_lt_t,   &ctx->ld_lt_e,   &ctx->ld_nonuni,
                       &ctx->ld_srcof,
                       &ctx->pool_sid, &ctx->set_start,  &ctx->set_len,   &ctx->set_width,
                       &ctx->counts,   &ctx->node_off,   &ctx->cursor,    &ctx->node_sets,
@@ -186,7 +188,8 @@ int tim_destroy(tim_ctx* ctx) {
                       &ctx->seeds_dev, &ctx->ovf_list,  &ctx->big_bitmap, &ctx->big_queue,
                       &ctx->ovf_list2, &ctx->arena,    &ctx->lt_col,    &ctx->greedy_bar,
                       &ctx->scratch_a, &ctx->scratch_b, &ctx->scratch_c, &ctx->scratch_d,
-                      &ctx->scratch_e, &ctx->scal,      &ctx->bulk_bitmap, &ctx->bulk_slot,
+                      &ctx->scratch_e, &ctx->scratch_f, &ctx->scal,     &ctx->bulk_bitmap,
+                      &ctx->bulk_slot, &ctx->bulk_bsum, &ctx->bulk_bar,
                       &ctx->bulk_F,    &ctx->bulk_M,    &ctx->bulk_ng,   &ctx->bulk_gp,
                       &ctx->bulk_scal, &ctx->batch,     &ctx->greedy_batch,
                       &ctx->out_rowptr, &ctx->out_rec,  &ctx->mc_bitmap, &ctx->mc_queue,
@@ -197,6 +200,8 @@ int tim_destroy(tim_ctx* ctx) {
         if (ctx->ev[i]) cudaEventDestroy(ctx->ev[i]);
     for (int i = 0; i < 4; i++)
         if (ctx->kev[i]) cudaEventDestroy(ctx->kev[i]);
+    for (int i = 0; i < 2; i++)
+        if (ctx->bev[i]) cudaEventDestroy(ctx->bev[i]);
     if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
     return TIM_OK;
@@ -334,6 +339,23 @@ int tim_load_graph_device(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_o
     // the build's temporaries and sort scratch stay allocated for the next load
     // (tim_destroy frees them)
     return tim_graph_build(ctx, n, m, d_out_rowptr, d_out_dst, d_edge_w, model);
+}
+
+int tim_get_graph(tim_ctx* ctx, uint64_t* rowptr, uint32_t* src, uint32_t* thr) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    DeviceGuard g(ctx->device);
+    const size_t n1 = (size_t)ctx->n + 1, m = (size_t)ctx->m;
+    if (rowptr)
+        CUDA_TRY(ctx, cudaMemcpyAsync(rowptr, ctx->rowptr.p, n1 * sizeof(uint64_t),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    if (src && m)
+        CUDA_TRY(ctx, cudaMemcpyAsync(src, ctx->src.p, m * sizeof(uint32_t),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    if (thr && m)
+        CUDA_TRY(ctx, cudaMemcpyAsync(thr, ctx->thr.p, m * sizeof(uint32_t),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+    return tim_sync(ctx);
 }
 
 int tim_load_graph(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* out_rowptr,

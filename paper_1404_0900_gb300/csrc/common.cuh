@@ -125,7 +125,7 @@ struct tim_ctx {
     int last_team = 1;
 
     // graph-load temporaries (graph.cu), kept between loads
-    DevBuf ld_keys, ld_vals, ld_indeg, ld_lt_t, ld_lt_e, ld_nonuni, ld_srcof;
+    DevBuf ld_keys, ld_vals, ld_lt_t, ld_lt_e, ld_nonuni, ld_srcof;
 
     // forward cascades (spread.cu): G as out-records {in-CSR position, destination},
     // built from G^T on first use; per-block visited bitmaps (kept all-zero between
@@ -134,13 +134,14 @@ struct tim_ctx {
     bool have_out = false, mc_clean = false;
 
     // generic scratch for scans and sorts
-    DevBuf scratch_a, scratch_b, scratch_c, scratch_d, scratch_e;
+    DevBuf scratch_a, scratch_b, scratch_c, scratch_d, scratch_e, scratch_f;
 
     DevBuf scal;
     DevScalars* h_scal = nullptr;  // pinned
 
     cudaEvent_t ev[8] = {};
     cudaEvent_t kev[4] = {};  // around the sampler's three tiers
+    cudaEvent_t bev[2] = {};  // around each persistent launch of the heavy-set pass
 
     // state of the last tim_kpt_estimate
     bool have_kpt = false;
@@ -210,10 +211,10 @@ static inline uint64_t make_sid(uint64_t phase, uint64_t round, uint64_t j) {
 int tim_scan_u32_to_u64(tim_ctx* ctx, const uint32_t* in, uint64_t* out, uint64_t count);
 // The same for uint64 counts (sums must stay below 2^64).
 int tim_scan_u64(tim_ctx* ctx, const unsigned long long* in, uint64_t* out, uint64_t count);
-// Stable LSD radix sort of (key, value) uint32 pairs by the low `bits` bits of key.
-// keys/vals are sorted in place (alternate buffers are taken from scratch).
-int tim_radix_sort_pairs(tim_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t count,
-                         int bits);
+// Stable LSD radix sort of (key, a, b) uint32 triples by the low `bits` bits of key,
+// in place (alternate buffers are taken from scratch).
+int tim_radix_sort_triples(tim_ctx* ctx, uint32_t* keys, uint32_t* va, uint32_t* vb,
+                           uint64_t count, int bits);
 
 // graph.cu
 int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,

@@ -2,9 +2,10 @@
 // in-edges of every node ascending by source, and the per-edge thresholds of the
 // diffusion model.
 //
-// Build: a stable radix sort of (destination, edge id) pairs turns the out-CSR (sorted
-// by source) into in-lists sorted by source; sources come from a binary search of
-// the out-CSR offsets.
+// Build: one pass writes (destination, source, weight bits) for every out-edge, in
+// out-CSR order (ascending source); a stable radix sort by destination of these triples
+// turns them into the in-lists, each ascending by source, with no gather afterwards;
+// the in-CSR offsets are the boundaries between destinations in the sorted keys.
 //   IC (Section 2.1): thr = floor(p * 2^32) for p < 1, 0xFFFFFFFF (always live) for
 //                     p >= 1; an in-edge is live iff its coin word < thr.
 //   LT (Section 6):   thr = inclusive prefix over the in-list of floor(b * 2^32),
@@ -24,15 +25,15 @@ __global__ void check_rowptr_kernel(const int64_t* __restrict__ rowptr, int64_t 
     }
 }
 
-// Sort input (destination, edge id) per out-CSR edge, and the source of every edge: one
-// warp per source node u strides over its out-edges. The offsets are checked by
-// check_rowptr_kernel only at the end of the load, so they are clamped to [0, m) here
-// (an invalid graph is rejected; its sources are never used).
-__global__ void keys_iota_kernel(const int64_t* __restrict__ rowptr,
-                                 const int32_t* __restrict__ dst, int64_t n, int64_t m,
-                                 uint32_t* __restrict__ keys, uint32_t* __restrict__ vals,
-                                 uint32_t* __restrict__ srcof, uint32_t* __restrict__ indeg,
-                                 int* __restrict__ err) {
+// Sort input per out-CSR edge e: key = destination, a = source, b = the weight's bits.
+// Destinations are checked here; one warp per source node u writes the source of its
+// out-edges (the offsets are checked by check_rowptr_kernel only at the end of the load,
+// so they are clamped to [0, m) here: an invalid graph is rejected and its sources are
+// never used).
+__global__ void edges_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ dst,
+                             const float* __restrict__ w, int64_t n, int64_t m,
+                             uint32_t* __restrict__ keys, uint32_t* __restrict__ srcs,
+                             uint32_t* __restrict__ wbits, int* __restrict__ err) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
         int32_t v = dst[e];
@@ -41,39 +42,65 @@ __global__ void keys_iota_kernel(const int64_t* __restrict__ rowptr,
             v = 0;
         }
         keys[e] = (uint32_t)v;
-        vals[e] = (uint32_t)e;
-        atomicAdd(&indeg[v], 1u);
+        wbits[e] = __float_as_uint(w[e]);
     }
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < n; u += nw) {
         const int64_t b = min(max(rowptr[u], (int64_t)0), m);
         const int64_t f = min(max(rowptr[u + 1], b), m);
-        for (int64_t e = b + lane; e < f; e += 32) srcof[e] = (uint32_t)u;
+        for (int64_t e = b + lane; e < f; e += 32) srcs[e] = (uint32_t)u;
     }
 }
 
-__global__ void fill_in_edges_kernel(const uint32_t* __restrict__ srcof, int64_t n, int64_t m,
-                                     const uint32_t* __restrict__ sorted_dst,
-                                     const uint32_t* __restrict__ sorted_eid,
-                                     const float* __restrict__ w, int model,
-                                     uint32_t* __restrict__ src, uint32_t* __restrict__ thr,
+// In-CSR offsets from the sorted destinations: position j starts the in-lists of the
+// nodes after its predecessor's destination up to its own; the nodes after the last
+// destination start at m.
+__global__ void rowptr_from_keys_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t m,
+                                        uint64_t* __restrict__ rowptr) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
+         j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = keys[j];
+        const int64_t prev = j > 0 ? (int64_t)keys[j - 1] : -1;
+        for (int64_t v = prev + 1; v <= k; v++) rowptr[v] = (uint64_t)j;
+        if (j == m - 1)
+            for (int64_t v = k + 1; v <= n; v++) rowptr[v] = (uint64_t)m;
+    }
+}
+
+#ifdef GRAPH_DEBUG
+__device__ unsigned long long graph_debug_first[4] = {~0ull, 0, 0, 0};
+#endif
+
+// Per in-edge (sorted position): its source, the self-loop and weight checks, and the
+// model's threshold from the weight carried through the sort.
+__global__ void fill_in_edges_kernel(const uint32_t* __restrict__ sorted_dst,
+                                     const uint32_t* __restrict__ sorted_src,
+                                     const uint32_t* __restrict__ sorted_wbits, int64_t n,
+                                     int64_t m, int model, uint32_t* __restrict__ src,
+                                     uint32_t* __restrict__ thr,
                                      unsigned long long* __restrict__ lt_t,
                                      int* __restrict__ err) {
     for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < m;
          pos += (int64_t)gridDim.x * blockDim.x) {
-        uint32_t e = sorted_eid[pos];
-        uint32_t v = sorted_dst[pos];
-        uint32_t u = srcof[e];
+        const uint32_t v = sorted_dst[pos];
+        uint32_t u = sorted_src[pos];
         if (u >= (uint64_t)n) {  // offsets that miss this edge (an invalid graph)
             atomicOr(err, TIM_DEV_ERR_GRAPH);
             u = 0;
         }
         if (u == v) atomicOr(err, TIM_DEV_ERR_GRAPH);
         src[pos] = u;
-        float p = w[e];
+        float p = __uint_as_float(sorted_wbits[pos]);
         if (!(p >= 0.0f && p <= 1.0f)) {
             atomicOr(err, TIM_DEV_ERR_WEIGHT);
+#ifdef GRAPH_DEBUG
+            if (atomicCAS(&graph_debug_first[0], ~0ull, (unsigned long long)pos) == ~0ull) {
+                graph_debug_first[1] = sorted_wbits[pos];
+                graph_debug_first[2] = u;
+                graph_debug_first[3] = v;
+            }
+#endif
             p = 0.0f;
         }
         double scaled = (double)p * 4294967296.0;  // exact: float -> double, times 2^32
@@ -199,50 +226,47 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
 
     // temporaries of the build, kept by the context so that reloading allocates nothing
     DevBuf& keys = ctx->ld_keys;
-    DevBuf& vals = ctx->ld_vals;
-    DevBuf& indeg = ctx->ld_indeg;
+    DevBuf& srcs = ctx->ld_vals;
+    DevBuf& wbits = ctx->ld_srcof;
     DevBuf& lt_t = ctx->ld_lt_t;
     DevBuf& lt_e = ctx->ld_lt_e;
     DevBuf& nonuni = ctx->ld_nonuni;
-    DevBuf& srcof = ctx->ld_srcof;
     int rc = TIM_OK;
     do {
         if ((rc = tim_ensure(ctx, keys, (size_t)(m + 1) * sizeof(uint32_t)))) break;
-        if ((rc = tim_ensure(ctx, vals, (size_t)(m + 1) * sizeof(uint32_t)))) break;
-        if ((rc = tim_ensure(ctx, indeg, (size_t)(n + 1) * sizeof(uint32_t)))) break;
-        if ((rc = tim_ensure(ctx, srcof, (size_t)(m + 1) * sizeof(uint32_t)))) break;
+        if ((rc = tim_ensure(ctx, srcs, (size_t)(m + 1) * sizeof(uint32_t)))) break;
+        if ((rc = tim_ensure(ctx, wbits, (size_t)(m + 1) * sizeof(uint32_t)))) break;
         if (model == TIM_LT &&
             (rc = tim_ensure(ctx, lt_t, (size_t)(m + 1) * sizeof(unsigned long long))))
-            break;
-        if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(indeg.p, 0, (size_t)(n + 1) * 4, ctx->stream),
-                                 "memset")))
             break;
         check_rowptr_kernel<<<G, T, 0, ctx->stream>>>(d_rowptr, n, m, &ds->err);
         ctx->launches++;
         if (m > 0) {
-            keys_iota_kernel<<<G, T, 0, ctx->stream>>>(d_rowptr, d_dst, n, m, (uint32_t*)keys.p,
-                                                       (uint32_t*)vals.p, (uint32_t*)srcof.p,
-                                                       (uint32_t*)indeg.p, &ds->err);
+            edges_kernel<<<G, T, 0, ctx->stream>>>(d_rowptr, d_dst, d_w, n, m, (uint32_t*)keys.p,
+                                                   (uint32_t*)srcs.p, (uint32_t*)wbits.p,
+                                                   &ds->err);
             ctx->launches++;
             int bits = 0;
             while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
-            if ((rc = tim_radix_sort_pairs(ctx, (uint32_t*)keys.p, (uint32_t*)vals.p, (uint64_t)m,
-                                           bits)))
+            if ((rc = tim_radix_sort_triples(ctx, (uint32_t*)keys.p, (uint32_t*)srcs.p,
+                                             (uint32_t*)wbits.p, (uint64_t)m, bits)))
                 break;
-        }
-        if ((rc = tim_scan_u32_to_u64(ctx, (const uint32_t*)indeg.p, (uint64_t*)ctx->rowptr.p,
-                                      (uint64_t)n)))
-            break;
-        if (m > 0) {
+            rowptr_from_keys_kernel<<<G, T, 0, ctx->stream>>>((const uint32_t*)keys.p, n, m,
+                                                              (uint64_t*)ctx->rowptr.p);
+            ctx->launches++;
             fill_in_edges_kernel<<<G, T, 0, ctx->stream>>>(
-                (const uint32_t*)srcof.p, n, m, (const uint32_t*)keys.p, (const uint32_t*)vals.p, d_w,
-                model,
-                (uint32_t*)ctx->src.p, (uint32_t*)ctx->thr.p, (unsigned long long*)lt_t.p,
+                (const uint32_t*)keys.p, (const uint32_t*)srcs.p, (const uint32_t*)wbits.p, n, m,
+                model, (uint32_t*)ctx->src.p, (uint32_t*)ctx->thr.p, (unsigned long long*)lt_t.p,
                 &ds->err);
             ctx->launches++;
             check_dups_kernel<<<G, T, 0, ctx->stream>>>((const uint32_t*)keys.p,
                                                         (const uint32_t*)ctx->src.p, m, &ds->err);
             ctx->launches++;
+        } else if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(ctx->rowptr.p, 0,
+                                                             (size_t)(n + 1) * sizeof(uint64_t),
+                                                             ctx->stream),
+                                        "memset"))) {
+            break;
         }
         if ((rc = tim_ensure(ctx, nonuni, (size_t)(n + 1)))) break;
         if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(nonuni.p, 0, (size_t)(n + 1), ctx->stream),
@@ -295,6 +319,8 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
         if ((rc = tim_read_scalars(ctx))) break;
     } while (0);
     if (rc) return rc;
+    if (ctx->h_scal->err & TIM_DEV_ERR_BOUNDS)
+        return tim_fail(ctx, TIM_ERR_CUDA, "graph build: an index check of the sort failed");
     if (ctx->h_scal->err & TIM_DEV_ERR_WEIGHT)
         return tim_fail(ctx, TIM_ERR_ARG, "invalid edge weights for the model");
     if (ctx->h_scal->err & TIM_DEV_ERR_GRAPH)
@@ -306,3 +332,11 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
     ctx->have_graph = true;
     return TIM_OK;
 }
+
+#ifdef GRAPH_DEBUG
+extern "C" int tim_debug_graph_first(unsigned long long* out) {
+    return cudaMemcpyFromSymbol(out, graph_debug_first, sizeof graph_debug_first) == cudaSuccess
+               ? 0
+               : -1;
+}
+#endif

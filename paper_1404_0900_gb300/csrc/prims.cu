@@ -1,5 +1,7 @@
 // prims.cu -- device primitives: exclusive scan and a stable LSD radix sort of
-// (key, value) pairs. Used to build G^T and the node -> RR-set index.
+// (key, value, value) triples. Used to build G^T.
+#include <utility>
+
 #include "common.cuh"
 
 namespace {
@@ -107,74 +109,120 @@ __global__ void scan_apply_kernel(const TIn* __restrict__ in, uint64_t count,
 // ---------------------------------------------------------------- radix sort
 
 constexpr int RS_WARPS = 8;
-constexpr int RS_ROUNDS = 8;
-constexpr int RS_TILE = RS_WARPS * RS_ROUNDS * 32;  // 2048 keys per block
-constexpr int RS_BINS = 256;
+constexpr int RS_ROUNDS = 16;
+constexpr int RS_TILE = RS_WARPS * RS_ROUNDS * 32;  // 4096 keys per block
+constexpr int RS_MAXBINS = 256;
+// dynamic shared memory of the scatter: the tile's keys and two value arrays in digit
+// order, per-warp digit counts, the tile's digit starts
+constexpr size_t RS_SMEM = (size_t)RS_TILE * 3 * sizeof(uint32_t) +
+                           (size_t)RS_WARPS * RS_MAXBINS * sizeof(uint32_t) +
+                           RS_MAXBINS * sizeof(uint32_t);
 
 __global__ void radix_hist_kernel(const uint32_t* __restrict__ keys, uint64_t count, int shift,
-                                  uint64_t ntiles, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[RS_BINS];
-    for (int i = threadIdx.x; i < RS_BINS; i += blockDim.x) h[i] = 0;
+                                  uint32_t mask, uint64_t ntiles, uint32_t* __restrict__ hist) {
+    __shared__ uint32_t h[RS_MAXBINS];
+    for (int i = threadIdx.x; i <= (int)mask; i += blockDim.x) h[i] = 0;
     __syncthreads();
-    uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
+    const uint64_t base = (uint64_t)blockIdx.x * RS_TILE;
     for (int i = threadIdx.x; i < RS_TILE; i += blockDim.x) {
-        uint64_t idx = base + i;
-        if (idx < count) atomicAdd(&h[(keys[idx] >> shift) & (RS_BINS - 1)], 1u);
+        const uint64_t idx = base + i;
+        if (idx < count) atomicAdd(&h[(keys[idx] >> shift) & mask], 1u);
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x)
+    for (int d = threadIdx.x; d <= (int)mask; d += blockDim.x)
         hist[(uint64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
-// Stable scatter of one tile: warp w owns keys [w*256, (w+1)*256) of the tile, taken
-// 32 at a time in order; equal digits are ranked by __match_any_sync, so the order of
-// equal digits is the input order.
+// Stable scatter of one tile of (key, a, b): warp w owns elements [w*512, (w+1)*512) of
+// the tile, taken 32 at a time in order, ranked among equal digits by __match_any_sync
+// (so equal digits keep the input order). The tile is first rearranged in shared memory
+// into digit order, then written out so that consecutive threads write consecutive
+// positions of each digit's run (coalesced stores).
 __global__ void __launch_bounds__(RS_WARPS * 32)
-radix_scatter_kernel(const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-                     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out,
-                     uint64_t count, int shift, uint64_t ntiles,
-                     const uint64_t* __restrict__ offsets) {
-    __shared__ uint32_t run[RS_WARPS][RS_BINS];
+radix_scatter3_kernel(const uint32_t* __restrict__ k_in, const uint32_t* __restrict__ a_in,
+                      const uint32_t* __restrict__ b_in, uint32_t* __restrict__ k_out,
+                      uint32_t* __restrict__ a_out, uint32_t* __restrict__ b_out,
+                      uint64_t count, int shift, uint32_t mask, uint64_t ntiles,
+                      const uint64_t* __restrict__ offsets, int* __restrict__ err) {
+    extern __shared__ uint32_t rs_smem[];
+    uint32_t* sk = rs_smem;
+    uint32_t* sa = sk + RS_TILE;
+    uint32_t* sb = sa + RS_TILE;
+    uint32_t* run = sb + RS_TILE;              // [RS_WARPS][RS_MAXBINS]
+    uint32_t* dstart = run + RS_WARPS * RS_MAXBINS;  // [RS_MAXBINS]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    for (int i = threadIdx.x; i < RS_WARPS * RS_BINS; i += blockDim.x) (&run[0][0])[i] = 0;
+    const uint32_t nbins = mask + 1;
+    for (int i = threadIdx.x; i < RS_WARPS * RS_MAXBINS; i += blockDim.x) run[i] = 0;
     __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1u;
-    uint32_t kk[RS_ROUNDS], vv[RS_ROUNDS], rank[RS_ROUNDS];
-    uint64_t base = (uint64_t)blockIdx.x * RS_TILE + (uint64_t)w * (RS_ROUNDS * 32);
+    const uint64_t tile0 = (uint64_t)blockIdx.x * RS_TILE;
+    const uint64_t base = tile0 + (uint64_t)w * (RS_ROUNDS * 32);
+    uint32_t kk[RS_ROUNDS], aa[RS_ROUNDS], bb[RS_ROUNDS], rank[RS_ROUNDS];
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; r++) {
-        uint64_t idx = base + (uint64_t)r * 32 + lane;
-        bool valid = idx < count;
-        kk[r] = valid ? keys_in[idx] : 0u;
-        vv[r] = valid ? vals_in[idx] : 0u;
-        uint32_t d = (kk[r] >> shift) & (RS_BINS - 1);
-        uint32_t tag = valid ? d : (RS_BINS + lane);
-        uint32_t peers = __match_any_sync(0xffffffffu, tag);
-        uint32_t before = (valid ? run[w][d] : 0u);
+        const uint64_t idx = base + (uint64_t)r * 32 + lane;
+        const bool valid = idx < count;
+        kk[r] = valid ? k_in[idx] : 0u;
+        aa[r] = valid ? a_in[idx] : 0u;
+        bb[r] = valid ? b_in[idx] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < RS_ROUNDS; r++) {
+        const uint64_t idx = base + (uint64_t)r * 32 + lane;
+        const bool valid = idx < count;
+        const uint32_t d = (kk[r] >> shift) & mask;
+        const uint32_t tag = valid ? d : (RS_MAXBINS + lane);
+        const uint32_t peers = __match_any_sync(0xffffffffu, tag);
+        const uint32_t before = valid ? run[w * RS_MAXBINS + d] : 0u;
         rank[r] = before + __popc(peers & lt_mask);
         __syncwarp();
-        if (valid && (peers & lt_mask) == 0) run[w][d] = before + __popc(peers);
+        if (valid && (peers & lt_mask) == 0) run[w * RS_MAXBINS + d] = before + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    for (int d = threadIdx.x; d < RS_BINS; d += blockDim.x) {
+    // per digit: prefix over the warps, and the digit's count in the tile
+    uint32_t dcount = 0;
+    if (threadIdx.x < nbins) {
         uint32_t acc = 0;
         for (int ww = 0; ww < RS_WARPS; ww++) {
-            uint32_t t = run[ww][d];
-            run[ww][d] = acc;
+            const uint32_t t = run[ww * RS_MAXBINS + threadIdx.x];
+            run[ww * RS_MAXBINS + threadIdx.x] = acc;
             acc += t;
         }
+        dcount = acc;
     }
+    unsigned long long tot;
+    const unsigned long long ds = block_excl_scan(dcount, &tot);  // nbins <= blockDim.x
+    if (threadIdx.x < nbins) dstart[threadIdx.x] = (uint32_t)ds;
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < RS_ROUNDS; r++) {
-        uint64_t idx = base + (uint64_t)r * 32 + lane;
+        const uint64_t idx = base + (uint64_t)r * 32 + lane;
         if (idx < count) {
-            uint32_t d = (kk[r] >> shift) & (RS_BINS - 1);
-            uint64_t pos = offsets[(uint64_t)d * ntiles + blockIdx.x] + run[w][d] + rank[r];
-            keys_out[pos] = kk[r];
-            vals_out[pos] = vv[r];
+            const uint32_t d = (kk[r] >> shift) & mask;
+            const uint32_t lp = dstart[d] + run[w * RS_MAXBINS + d] + rank[r];
+            if (lp < RS_TILE) {
+                sk[lp] = kk[r];
+                sa[lp] = aa[r];
+                sb[lp] = bb[r];
+            } else {
+                atomicOr(err, TIM_DEV_ERR_BOUNDS);
+            }
         }
+    }
+    __syncthreads();
+    const uint32_t n_tile = (uint32_t)min((uint64_t)RS_TILE, count - tile0);
+    for (uint32_t i = threadIdx.x; i < n_tile; i += blockDim.x) {
+        const uint32_t k = sk[i];
+        const uint32_t d = (k >> shift) & mask;
+        const uint64_t pos = offsets[(uint64_t)d * ntiles + blockIdx.x] + (i - dstart[d]);
+        if (i < dstart[d] || pos >= count) {  // cannot happen for a consistent tile
+            atomicOr(err, TIM_DEV_ERR_BOUNDS);
+            continue;
+        }
+        k_out[pos] = k;
+        a_out[pos] = sa[i];
+        b_out[pos] = sb[i];
     }
 }
 
@@ -207,37 +255,48 @@ int tim_scan_u64(tim_ctx* ctx, const unsigned long long* in, uint64_t* out, uint
     return scan_to_u64<unsigned long long>(ctx, in, out, count);
 }
 
-int tim_radix_sort_pairs(tim_ctx* ctx, uint32_t* keys, uint32_t* vals, uint64_t count, int bits) {
+int tim_radix_sort_triples(tim_ctx* ctx, uint32_t* keys, uint32_t* va, uint32_t* vb,
+                           uint64_t count, int bits) {
     if (count <= 1 || bits <= 0) return TIM_OK;
-    uint64_t ntiles = (count + RS_TILE - 1) / RS_TILE;
-    uint64_t nh = ntiles * RS_BINS;
+    // passes of at most 8 bits, the digit width spread evenly over them (26 bits: four
+    // passes of 7 bits; fewer bins make longer runs per tile)
+    const int passes = (bits + 7) / 8;
+    const int width = (bits + passes - 1) / passes;
+    const uint32_t mask = (1u << width) - 1u;
+    const uint64_t ntiles = (count + RS_TILE - 1) / RS_TILE;
+    const uint64_t nh = ntiles * (mask + 1);
     TIM_TRY(tim_ensure(ctx, ctx->scratch_a, count * sizeof(uint32_t)));
     TIM_TRY(tim_ensure(ctx, ctx->scratch_b, count * sizeof(uint32_t)));
+    TIM_TRY(tim_ensure(ctx, ctx->scratch_f, count * sizeof(uint32_t)));
     TIM_TRY(tim_ensure(ctx, ctx->scratch_c, nh * sizeof(uint32_t)));
     TIM_TRY(tim_ensure(ctx, ctx->scratch_d, (nh + 1) * sizeof(uint64_t)));
-    uint32_t* k_alt = (uint32_t*)ctx->scratch_a.p;
-    uint32_t* v_alt = (uint32_t*)ctx->scratch_b.p;
+    CUDA_TRY(ctx, cudaFuncSetAttribute(radix_scatter3_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM));
     uint32_t* hist = (uint32_t*)ctx->scratch_c.p;
     uint64_t* offs = (uint64_t*)ctx->scratch_d.p;
-    uint32_t *kin = keys, *vin = vals, *kout = k_alt, *vout = v_alt;
-    int passes = (bits + 7) / 8;
+    uint32_t *kin = keys, *ain = va, *bin = vb;
+    uint32_t *kout = (uint32_t*)ctx->scratch_a.p, *aout = (uint32_t*)ctx->scratch_b.p,
+             *bout = (uint32_t*)ctx->scratch_f.p;
     for (int p = 0; p < passes; p++) {
-        int shift = 8 * p;
-        radix_hist_kernel<<<(unsigned)ntiles, 256, 0, ctx->stream>>>(kin, count, shift, ntiles,
-                                                                     hist);
+        const int shift = width * p;
+        radix_hist_kernel<<<(unsigned)ntiles, 256, 0, ctx->stream>>>(kin, count, shift, mask,
+                                                                     ntiles, hist);
         LAUNCH_CHECK(ctx, "radix_hist_kernel");
         TIM_TRY(tim_scan_u32_to_u64(ctx, hist, offs, nh));
-        radix_scatter_kernel<<<(unsigned)ntiles, RS_WARPS * 32, 0, ctx->stream>>>(
-            kin, vin, kout, vout, count, shift, ntiles, offs);
-        LAUNCH_CHECK(ctx, "radix_scatter_kernel");
-        uint32_t* t;
-        t = kin; kin = kout; kout = t;
-        t = vin; vin = vout; vout = t;
+        radix_scatter3_kernel<<<(unsigned)ntiles, RS_WARPS * 32, RS_SMEM, ctx->stream>>>(
+            kin, ain, bin, kout, aout, bout, count, shift, mask, ntiles, offs,
+            &tim_dscal(ctx)->err);
+        LAUNCH_CHECK(ctx, "radix_scatter3_kernel");
+        std::swap(kin, kout);
+        std::swap(ain, aout);
+        std::swap(bin, bout);
     }
     if (kin != keys) {
         CUDA_TRY(ctx, cudaMemcpyAsync(keys, kin, count * sizeof(uint32_t),
                                       cudaMemcpyDeviceToDevice, ctx->stream));
-        CUDA_TRY(ctx, cudaMemcpyAsync(vals, vin, count * sizeof(uint32_t),
+        CUDA_TRY(ctx, cudaMemcpyAsync(va, ain, count * sizeof(uint32_t),
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
+        CUDA_TRY(ctx, cudaMemcpyAsync(vb, bin, count * sizeof(uint32_t),
                                       cudaMemcpyDeviceToDevice, ctx->stream));
     }
     return TIM_OK;

@@ -874,13 +874,18 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
         if (persistent) {
             CUDA_TRY(ctx, cudaMemsetAsync(a.bar, 0, sizeof(GridBarrier), ctx->stream));
             void* args[] = {&a};
+            cudaEventRecord(ctx->bev[0], ctx->stream);
             CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)bulk_levels_kernel, dim3(GP),
                                                       dim3(256), args, EXPAND_SMEM,
                                                       ctx->stream));
             LAUNCH_CHECK(ctx, "bulk_levels_kernel");
+            cudaEventRecord(ctx->bev[1], ctx->stream);
             CUDA_TRY(ctx, cudaMemcpyAsync(&hb, a.bs, sizeof hb, cudaMemcpyDeviceToHost,
                                           ctx->stream));
             TIM_TRY(tim_sync(ctx));
+            float kms = 0.f;
+            cudaEventElapsedTime(&kms, ctx->bev[0], ctx->bev[1]);
+            ctx->prof.pass3_ms_kernel += kms;
             if (hb.err & TIM_DEV_ERR_TIMEOUT) {
                 ctx->bulk_bitmap_clean = false;
                 return tim_fail(ctx, TIM_ERR_TIMEOUT, "heavy-set grid barrier timed out");

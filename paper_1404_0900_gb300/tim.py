@@ -65,7 +65,7 @@ class tim_profile(C.Structure):
         ("pass3_examined", C.c_uint64),
         ("pass3_batches", C.c_uint64), ("pass3_levels", C.c_uint64),
         ("pass3_ms_offsets", C.c_double), ("pass3_ms_expand", C.c_double),
-        ("pass3_ms_wait", C.c_double),
+        ("pass3_ms_wait", C.c_double), ("pass3_ms_kernel", C.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -105,6 +105,7 @@ _SIGS = {
     "tim_last_error_message": (C.c_char_p, [_P]),
     "tim_load_graph": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, C.c_int]),
     "tim_load_graph_device": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, C.c_int]),
+    "tim_get_graph": (C.c_int, [_P, _P, _P, _P]),
     "tim_sample_rr": (C.c_int, [_P, C.c_uint64, C.c_uint64, C.c_uint64, _P]),
     "tim_get_rr": (C.c_int, [_P, _P, _P, C.c_uint64, _P]),
     "tim_rr_size": (C.c_int, [_P, _P, _P]),
@@ -196,10 +197,17 @@ def _check(ctx, rc: int):
 
 # ---------------------------------------------------------------- the calls
 
+# cudaStreamLegacy: the legacy default stream as an explicit handle
+CUDA_STREAM_LEGACY = 0x1
+
+
 def tim_create(device: int = 0, stream=None):
-    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (own stream)."""
+    """stream: a torch.cuda.Stream, a raw cudaStream_t int, or None (the context creates
+    its own stream). A torch stream whose handle is 0 is the legacy default stream: it
+    is passed as cudaStreamLegacy, so that the context's work is ordered after the work
+    torch queued there (handle 0 alone would mean "create an own stream")."""
     if stream is not None and hasattr(stream, "cuda_stream"):
-        stream = stream.cuda_stream
+        stream = stream.cuda_stream or CUDA_STREAM_LEGACY
     h = _P()
     rc = lib().tim_create(C.byref(h), device, _P(stream) if stream else None)
     if rc != TIM_OK:
@@ -223,6 +231,16 @@ def tim_load_graph_device(ctx, n: int, m: int, d_rowptr, d_dst, d_weight, model:
     """Device arrays: torch CUDA tensors (int64, int32, float32) or raw pointers."""
     _check(ctx, lib().tim_load_graph_device(ctx, n, m, _ptr(d_rowptr), _ptr(d_dst),
                                             _ptr(d_weight), model))
+
+
+def tim_get_graph(ctx, n: int, m: int):
+    """G^T of the loaded graph: (rowptr uint64[n+1], src uint32[m], thr uint32[m])."""
+    rowptr = np.zeros(n + 1, dtype=np.uint64)
+    src = np.zeros(max(m, 1), dtype=np.uint32)
+    thr = np.zeros(max(m, 1), dtype=np.uint32)
+    _check(ctx, lib().tim_get_graph(ctx, rowptr.ctypes.data_as(_P), src.ctypes.data_as(_P),
+                                    thr.ctypes.data_as(_P)))
+    return rowptr, src[:m], thr[:m]
 
 
 def tim_sample_rr(ctx, theta: int, seed: int, first_set_id: int) -> int:

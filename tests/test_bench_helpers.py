@@ -29,8 +29,24 @@ def test_mix_rate_is_a_harmonic_weighting():
 def test_default_command_line_is_one_gpu_within_minutes():
     a = bench.parse_args([])
     assert a.gpus == 1 and a.impl == "ours" and a.mode == "timplus"
+    assert a.workload == "c3"  # the largest configuration is the headline
     assert a.warmup >= 3 and 1 <= a.steps <= 10
+    # the nested R-MAT line
     assert a.scale == 20 and a.k == 50 and a.eps == 0.1 and a.ell == 1.0
+
+
+def test_roofline_takes_the_pass_with_most_kernel_time():
+    p = {f"pass{i}_{k}": 0 for i in (1, 2, 3) for k in ("ms", "launches", "members", "sets",
+                                                          "examined")}
+    p.update({"pass1_ms": 5.0, "pass1_launches": 2, "pass2_ms": 7.0, "pass2_launches": 2,
+              "pass3_ms": 40.0, "pass3_launches": 3, "pass3_batches": 4, "pass3_ms_kernel": 20.0,
+              "pass3_members": 100, "pass3_sets": 10, "pass3_examined": 1000})
+    r = bench.sampler_roofline(p)
+    assert r["kernel"].startswith("bulk_levels_kernel") and r["launches"] == 4
+    # the heavy pass's persistent launches alone: 20 ms over 4 launches
+    assert r["ms_per_launch"] == 5.0
+    alg = bench.sampler_bytes(p, 3)
+    assert abs(r["achieved"] - alg / 0.020 / 1e9) < 1e-9 and r["bytes_per_launch"] == alg / 4
 
 
 def test_dram_bytes_per_member_are_from_a_capture_or_null():

@@ -6,8 +6,9 @@ The graph is drawn on the device, loaded through the C ABI from device memory, a
 copied to the host -- loaded into the oracle, which builds its own G^T. Compared bit for
 bit: a spread of RR sets and the heaviest ones the GPU drew (up to ~10^6 members, the
 level-synchronous third pass), and TIM+ end to end (stopping round, KPT*, R' greedy,
-theta', KPT+, theta, seeds, covered count). The module takes a few minutes: the oracle
-transposes 1.4B edges and runs TIM+ on all host threads."""
+theta', KPT+, theta, seeds, covered count), and G^T itself against the oracle's
+transpose. The module takes a few minutes: the oracle transposes 1.4B edges and runs
+TIM+ on all host threads."""
 import numpy as np
 import pytest
 
@@ -36,12 +37,17 @@ def c3():
     eng.close()
 
 
-def test_c3_graph_shape(c3):
-    _, og, shape = c3
+def test_c3_graph_shape_and_transpose(c3):
+    eng, og, shape = c3
     assert shape["n"] == 41_600_000 and shape["m"] == 1_400_000_000
     assert og.n == shape["n"] and og.m == shape["m"]
     # power law with exponent 2.1: hubs of millions of in- and out-edges
     assert shape["max_indeg"] > 10**6 and shape["max_outdeg"] > 10**6
+    # G^T (offsets, sources, thresholds) bit for bit against the oracle's transpose
+    rowptr, src, thr = tim.tim_get_graph(eng.ctx, og.n, og.m)
+    assert np.array_equal(rowptr, og.rowptr.astype(np.uint64))
+    assert np.array_equal(src, og.src[:og.m].astype(np.uint32))
+    assert np.array_equal(thr, og.thr[:og.m])
 
 
 def test_c3_rr_sets_spread_and_heaviest(c3):

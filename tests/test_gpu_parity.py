@@ -412,3 +412,57 @@ def test_grid_barrier_timeout_is_reported_and_the_context_recovers(eng):
     roff, rmem, _ = O.sample(oh, 5, sid0, 20000)
     rseeds, rcov, _ = O.greedy(h.n, roff, rmem, 10)
     assert np.array_equal(seeds, rseeds) and cov == rcov
+
+
+def _oracle_graph_arrays(og):
+    return og.rowptr.astype(np.uint64), og.src[:og.m].astype(np.uint32), og.thr[:og.m]
+
+
+@pytest.mark.parametrize("name", ["rmat12_wc", "rmat10_tri", "rmat13_mixed", "star", "chain",
+                                  "rand_p1"])
+@pytest.mark.parametrize("model", [O.IC, O.LT])
+def test_graph_load_equals_the_oracle_transpose(eng, name, model):
+    """Row A1 directly: the in-CSR offsets, sources (ascending per in-list) and thresholds
+    of G^T bit for bit against the oracle's own transpose (Table 1)."""
+    g, kind = GRAPHS[name]()
+    w = _weights(g, kind, model)
+    og = _load(eng, g, w, model)
+    rowptr, src, thr = tim.tim_get_graph(eng.ctx, g.n, g.m)
+    r0, s0, t0 = _oracle_graph_arrays(og)
+    assert np.array_equal(rowptr, r0) and np.array_equal(src, s0) and np.array_equal(thr, t0)
+
+
+@pytest.mark.parametrize("n", [(1 << 20) + 3, 1 << 21, (1 << 21) + 1, 3 << 21])
+def test_graph_load_key_widths(eng, n):
+    """Node counts around powers of two change the number of sort passes (odd and even)."""
+    rng = np.random.default_rng(n)
+    m = 200_000
+    g = inputs.csr_from_pairs(n, rng.integers(0, n, m), rng.integers(0, n, m))
+    w = inputs.uniform_random(g, 0.0, 1.0, seed=4)
+    og = _load(eng, g, w, O.IC)
+    rowptr, src, thr = tim.tim_get_graph(eng.ctx, g.n, g.m)
+    r0, s0, t0 = _oracle_graph_arrays(og)
+    assert np.array_equal(rowptr, r0) and np.array_equal(src, s0) and np.array_equal(thr, t0)
+
+
+def test_device_load_on_the_default_stream_follows_pending_work():
+    """An engine on torch's default stream (handle 0) runs on that stream: a device load
+    right after the kernels that produce its inputs, with no synchronisation, sees
+    their results."""
+    import torch
+    g = inputs.rmat(16, seed=8)
+    w = inputs.trivalency(g, seed=9)
+    og = O.load_graph(g.n, g.rowptr, g.dst, w, O.IC)
+    with tim.Engine(0, torch.cuda.current_stream()) as e:
+        for _ in range(2):
+            d_rowptr = torch.from_numpy(g.rowptr).cuda()
+            d_dst = torch.from_numpy(g.dst).cuda()
+            d_w = torch.from_numpy(w).cuda()
+            # a long chain of work on the default stream that ends in the weights
+            for _ in range(200):
+                d_w = d_w * 1.0 + 0.0
+            tim.tim_load_graph_device(e.ctx, g.n, g.m, d_rowptr, d_dst, d_w, tim.TIM_IC)
+            rowptr, src, thr = tim.tim_get_graph(e.ctx, g.n, g.m)
+            r0, s0, t0 = _oracle_graph_arrays(og)
+            assert np.array_equal(rowptr, r0) and np.array_equal(src, s0)
+            assert np.array_equal(thr, t0)

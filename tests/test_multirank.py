@@ -59,8 +59,8 @@ def test_reference_arm_prints_once_from_rank_zero():
     # the oracle reference arm at N = 2: rank 0 prints one JSON line, rank 1 exits at once
     code = (
         "import bench\n"
-        "bench.main(['--impl', 'reference', '--gpus', '2', '--steps', '1', '--warmup', '1',"
-        " '--scale', '12'])\n")
+        "bench.main(['--impl', 'reference', '--workload', 'c2', '--gpus', '2', '--steps', '1',"
+        " '--warmup', '1', '--scale', '12'])\n")
     outs = _run_ranks(code, timeout=300.0)
     lines0 = [l for l in outs[0].splitlines() if l.startswith("{")]
     lines1 = [l for l in outs[1].splitlines() if l.startswith("{")]
