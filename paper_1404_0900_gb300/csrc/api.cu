@@ -10,6 +10,7 @@
 
 #include <algorithm>
 #include <array>
+#include <chrono>
 #include <cstdio>
 #include <vector>
 
@@ -841,6 +842,202 @@ int tim_run(tim_ctx* ctx, int k, double eps, double ell, uint64_t seed, int32_t*
             double* covered_fraction, tim_stats* stats, uint64_t theta_override) {
     return run_common(ctx, true, k, eps, ell, seed, seeds, covered_fraction, stats, theta_override,
                       nullptr);
+}
+
+int tim_select_begin(tim_ctx* ctx) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    DeviceGuard g(ctx->device);
+    TIM_TRY(tim_greedy_begin(ctx));
+    ctx->select_open = true;
+    return TIM_OK;
+}
+
+int tim_select_counts(tim_ctx* ctx, int32_t* counts) {
+    if (!ctx || !counts) return TIM_ERR_ARG;
+    if (!ctx->select_open) return tim_fail(ctx, TIM_ERR_STATE, "call tim_select_begin first");
+    DeviceGuard g(ctx->device);
+    CUDA_TRY(ctx, cudaMemcpyAsync(counts, ctx->counts.p, (size_t)ctx->n * sizeof(int32_t),
+                                  cudaMemcpyDeviceToHost, ctx->stream));
+    return tim_sync(ctx);
+}
+
+int tim_select_take(tim_ctx* ctx, int32_t node, uint64_t* newly_covered) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (!ctx->select_open) return tim_fail(ctx, TIM_ERR_STATE, "call tim_select_begin first");
+    if (node < 0 || node >= ctx->n) return tim_fail(ctx, TIM_ERR_ARG, "node out of range");
+    DeviceGuard g(ctx->device);
+    return tim_greedy_take(ctx, node, newly_covered);
+}
+
+// ------------------------------------------------------------ one shard of a query
+//
+// Set ids [lo, hi) of a phase with c sets owned by `rank` of `world`.
+static void shard_range(uint64_t c, int rank, int world, uint64_t* lo, uint64_t* hi) {
+    *lo = (uint64_t)((unsigned __int128)c * (unsigned)rank / (unsigned)world);
+    *hi = (uint64_t)((unsigned __int128)c * (unsigned)(rank + 1) / (unsigned)world);
+}
+
+struct Reducer {
+    tim_allreduce_fn fn;
+    void* user;
+    int operator()(tim_ctx* ctx, int64_t* data, uint64_t count) const {
+        if (fn(user, data, count) != 0)
+            return tim_fail(ctx, TIM_ERR_ARG, "the all-reduce callback failed");
+        return TIM_OK;
+    }
+};
+
+// Exact sum of a 128-bit value over the ranks: four 32-bit limbs summed as int64
+// (no overflow below 2^31 ranks), then the carries.
+static int allreduce_u128(tim_ctx* ctx, const Reducer& red, unsigned __int128* v) {
+    int64_t limb[4];
+    for (int i = 0; i < 4; i++) limb[i] = (int64_t)(uint32_t)(*v >> (32 * i));
+    TIM_TRY(red(ctx, limb, 4));
+    unsigned __int128 t = 0;
+    for (int i = 0; i < 4; i++) t += (unsigned __int128)(uint64_t)limb[i] << (32 * i);
+    *v = t;
+    return TIM_OK;
+}
+
+// The greedy of Algorithm 1 over the union of the ranks' stores: per round, the
+// coverage counts summed over the ranks, the node with the largest sum (ties: the
+// smallest id; chosen nodes excluded), which every rank then covers in its own store.
+static int greedy_sharded(tim_ctx* ctx, const Reducer& red, int k, int32_t* seeds,
+                          uint64_t* covered) {
+    const int64_t n = ctx->n;
+    TIM_TRY(tim_greedy_begin(ctx));
+    std::vector<int32_t> c32((size_t)n);
+    std::vector<int64_t> c64((size_t)n);
+    std::vector<uint8_t> chosen((size_t)n, 0);
+    uint64_t local = 0;
+    for (int r = 0; r < k; r++) {
+        CUDA_TRY(ctx, cudaMemcpyAsync(c32.data(), ctx->counts.p, (size_t)n * sizeof(int32_t),
+                                      cudaMemcpyDeviceToHost, ctx->stream));
+        TIM_TRY(tim_sync(ctx));
+        for (int64_t v = 0; v < n; v++) c64[v] = c32[v];
+        TIM_TRY(red(ctx, c64.data(), (uint64_t)n));
+        int64_t best = -1;
+        for (int64_t v = 0; v < n; v++)
+            if (!chosen[v] && (best < 0 || std::max<int64_t>(c64[v], 0) >
+                                               std::max<int64_t>(c64[best], 0)))
+                best = v;
+        chosen[best] = 1;
+        seeds[r] = (int32_t)best;
+        uint64_t fresh = 0;
+        TIM_TRY(tim_greedy_take(ctx, (int32_t)best, &fresh));
+        local += fresh;
+    }
+    int64_t tot = (int64_t)local;
+    TIM_TRY(red(ctx, &tot, 1));
+    *covered = (uint64_t)tot;
+    return TIM_OK;
+}
+
+int tim_run_sharded(tim_ctx* ctx, int k, double eps, double ell, uint64_t seed, int rank,
+                    int world, tim_allreduce_fn allreduce, void* user, int32_t* seeds,
+                    double* covered_fraction, tim_stats* stats) {
+    if (!ctx || !seeds || !allreduce) return TIM_ERR_ARG;
+    if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
+    if (k < 1 || k > ctx->n || !(eps > 0.0) || !(ell > 0.0))
+        return tim_fail(ctx, TIM_ERR_ARG, "need 1 <= k <= n, eps > 0, l > 0");
+    if (world < 1 || rank < 0 || rank >= world)
+        return tim_fail(ctx, TIM_ERR_ARG, "need 0 <= rank < world");
+    DeviceGuard g(ctx->device);
+    const auto t0 = std::chrono::steady_clock::now();
+    const Reducer red{allreduce, user};
+    const int64_t n = ctx->n;
+    const uint64_t tag = (uint64_t)ctx->query_tag << 32;
+    tim_stats s{};
+    uint64_t lo, hi, sets = 0;
+    // Algorithm 2: this rank's share of each round, the exact kappa sum over all ranks
+    double kpt_star = 1.0;
+    int stop = 0, last = 0;
+    const int rounds = tim_host_rounds(n);
+    ctx->n_sets = ctx->members = 0;
+    for (int i = 1; i <= rounds; i++) {
+        const uint64_t c = tim_host_c_i(n, ell, i);
+        shard_range(c, rank, world, &lo, &hi);
+        SampleRequest req;
+        req.seed = seed;
+        req.sid0 = make_sid(1, (uint64_t)i, tag) + lo;
+        req.count = hi - lo;
+        req.flags = SAMPLE_EMIT | SAMPLE_KAPPA;
+        req.k = k;
+        SampleResult res;
+        TIM_TRY(tim_sample(ctx, req, &res));
+        unsigned __int128 S = res.ksum;
+        TIM_TRY(allreduce_u128(ctx, red, &S));
+        last = i;
+        sets += c;
+        if (S > ((unsigned __int128)c << (63 - i))) {
+            kpt_star = (double)n * ldexp((double)S, -63) / (2.0 * (double)c);
+            stop = i;
+            break;
+        }
+    }
+    // Algorithm 3: greedy on R' (every rank holds its share of the last round's sets)
+    std::vector<int32_t> sp((size_t)k);
+    uint64_t unused = 0;
+    TIM_TRY(greedy_sharded(ctx, red, k, sp.data(), &unused));
+    TIM_TRY(tim_ensure(ctx, ctx->seeds_dev, (size_t)k * sizeof(int32_t)));
+    CUDA_TRY(ctx, cudaMemcpyAsync(ctx->seeds_dev.p, sp.data(), (size_t)k * sizeof(int32_t),
+                                  cudaMemcpyHostToDevice, ctx->stream));
+    TIM_TRY(tim_mark_seeds(ctx, (const int32_t*)ctx->seeds_dev.p, k));
+    const double ep = tim_host_eps_prime(eps, k, ell);
+    const double lp = tim_host_lambda_prime(n, ep, ell);
+    const uint64_t theta_p = (uint64_t)ceil(lp / kpt_star);
+    shard_range(theta_p, rank, world, &lo, &hi);
+    {
+        SampleRequest req;
+        req.seed = seed;
+        req.sid0 = make_sid(2, 0, tag) + lo;
+        req.count = hi - lo;
+        req.flags = SAMPLE_COVER;
+        req.seed_mark = (const uint32_t*)ctx->seed_mark.p;
+        SampleResult res;
+        TIM_TRY(tim_sample(ctx, req, &res));
+        int64_t cov = (int64_t)res.covered;
+        TIM_TRY(red(ctx, &cov, 1));
+        s.covered_prime = (uint64_t)cov;
+    }
+    sets += theta_p;
+    const double f = (double)s.covered_prime / (double)theta_p;
+    s.kpt_prime = f * (double)n / (1.0 + ep);
+    s.kpt_plus = std::max(s.kpt_prime, kpt_star);
+    // Algorithm 1: this rank's share of the theta sets, the greedy over all ranks
+    s.lambda = tim_host_lambda(n, k, eps, ell);
+    const uint64_t theta = (uint64_t)ceil(s.lambda / s.kpt_plus);
+    shard_range(theta, rank, world, &lo, &hi);
+    {
+        SampleRequest req;
+        req.seed = seed;
+        req.sid0 = make_sid(3, 0, tag) + lo;
+        req.count = hi - lo;
+        req.flags = SAMPLE_EMIT;
+        SampleResult res;
+        TIM_TRY(tim_sample(ctx, req, &res));
+        int64_t memb = (int64_t)res.members;
+        TIM_TRY(red(ctx, &memb, 1));
+        s.members_select = (uint64_t)memb;
+    }
+    sets += theta;
+    uint64_t cov = 0;
+    TIM_TRY(greedy_sharded(ctx, red, k, seeds, &cov));
+    ctx->have_kpt = false;
+    s.kpt_round = stop;
+    s.kpt_last_round = last;
+    s.kpt_star = kpt_star;
+    s.eps_prime = ep;
+    s.theta_prime = theta_p;
+    s.theta = theta;
+    s.covered = cov;
+    s.sets_total = sets;
+    s.ms_total = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0)
+                     .count();
+    if (covered_fraction) *covered_fraction = theta ? (double)cov / (double)theta : 0.0;
+    if (stats) *stats = s;
+    return TIM_OK;
 }
 
 int tim_run_learned(tim_ctx* ctx, tim_mlp* mlp, int k, double eps, double ell, uint64_t seed,

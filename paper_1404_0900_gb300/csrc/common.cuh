@@ -143,6 +143,8 @@ struct tim_ctx {
     cudaEvent_t kev[4] = {};  // around the sampler's three tiers
     cudaEvent_t bev[2] = {};  // around each persistent launch of the heavy-set pass
 
+    // a stepwise greedy is open on the store (tim_select_begin)
+    bool select_open = false;
     // state of the last tim_kpt_estimate
     bool have_kpt = false;
     int kpt_round = 0, kpt_last_round = 0;
@@ -258,6 +260,9 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed);
 int tim_build_index(tim_ctx* ctx);
 int tim_greedy(tim_ctx* ctx, int k, int32_t* host_seeds, uint64_t* covered);
 int tim_mark_seeds(tim_ctx* ctx, const int32_t* d_seeds, int k);
+// Stepwise greedy on the store: index and reset, then one caller-chosen node at a time.
+int tim_greedy_begin(tim_ctx* ctx);
+int tim_greedy_take(tim_ctx* ctx, int32_t v, uint64_t* newly_covered);
 // Greedy of Algorithm 1 for several queries (each on its own context's store) with
 // shared launches, optionally captured into one CUDA graph; seeds stay in each
 // context's seeds_dev, host copies where host_seeds[i] is not NULL.

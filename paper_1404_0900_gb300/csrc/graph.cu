@@ -210,6 +210,7 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
     if (model != TIM_IC && model != TIM_LT) return tim_fail(ctx, TIM_ERR_ARG, "unknown model");
     ctx->have_graph = false;
     ctx->have_kpt = false;
+    ctx->select_open = false;
     ctx->have_feat = false;
     ctx->have_out = false;
     ctx->n_sets = ctx->members = 0;

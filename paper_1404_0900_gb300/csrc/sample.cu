@@ -1583,6 +1583,7 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
         if (emit) {
             ctx->n_sets = count;
             ctx->members = h.pool_used;
+            ctx->select_open = false;
         }
         return TIM_OK;
     }

@@ -97,6 +97,8 @@ __global__ void argmax_kernel(const int* __restrict__ counts, const uint8_t* __r
     }
 }
 
+__global__ void set_key_kernel(unsigned long long* key, unsigned long long value) { *key = value; }
+
 __global__ void cover_kernel(const unsigned long long* __restrict__ best,
                              const uint64_t* __restrict__ node_off,
                              const uint32_t* __restrict__ node_sets,
@@ -308,6 +310,37 @@ __global__ void mark_seeds_kernel(const int32_t* __restrict__ seeds, int k,
         uint32_t u = (uint32_t)seeds[i];
         atomicOr(&mark[u >> 5], 1u << (u & 31));
     }
+}
+
+// Stepwise greedy: the caller chooses each node (for example from coverage counts summed
+// over several contexts), the context covers that node's sets of its own store.
+int tim_greedy_begin(tim_ctx* ctx) {
+    TIM_TRY(tim_build_index(ctx));
+    TIM_TRY(tim_ensure(ctx, ctx->covered, ctx->n_sets + 1));
+    TIM_TRY(tim_ensure(ctx, ctx->chosen, (uint64_t)ctx->n + 1));
+    TIM_TRY(tim_ensure(ctx, ctx->best, sizeof(unsigned long long)));
+    TIM_TRY(tim_ensure(ctx, ctx->seeds_dev, sizeof(int32_t)));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->covered.p, 0, ctx->n_sets + 1, ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->chosen.p, 0, (uint64_t)ctx->n + 1, ctx->stream));
+    return TIM_OK;
+}
+
+int tim_greedy_take(tim_ctx* ctx, int32_t v, uint64_t* newly_covered) {
+    // the key cover_kernel decodes: any count, node v
+    const unsigned long long key = (1ull << 32) | (unsigned long long)(~(uint32_t)v);
+    TIM_TRY(tim_zero_scalars(ctx));
+    DevScalars* ds = tim_dscal(ctx);
+    set_key_kernel<<<1, 1, 0, ctx->stream>>>((unsigned long long*)ctx->best.p, key);
+    LAUNCH_CHECK(ctx, "set_key_kernel");
+    cover_kernel<<<(unsigned)(ctx->num_sms * 2), 256, 0, ctx->stream>>>(
+        (const unsigned long long*)ctx->best.p, (const uint64_t*)ctx->node_off.p,
+        (const uint32_t*)ctx->node_sets.p, (const uint64_t*)ctx->set_start.p,
+        (const uint32_t*)ctx->set_len.p, (const uint32_t*)ctx->pool.p, (uint8_t*)ctx->covered.p,
+        (int*)ctx->counts.p, (uint8_t*)ctx->chosen.p, (int32_t*)ctx->seeds_dev.p, &ds->covered);
+    LAUNCH_CHECK(ctx, "cover_kernel");
+    TIM_TRY(tim_read_scalars(ctx));
+    if (newly_covered) *newly_covered = ctx->h_scal->covered;
+    return TIM_OK;
 }
 
 int tim_mark_seeds(tim_ctx* ctx, const int32_t* d_seeds, int k) {

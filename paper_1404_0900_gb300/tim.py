@@ -134,6 +134,11 @@ _SIGS = {
     "tim_node_select_noalloc": (C.c_int, [C.c_int, _P, C.c_int64, C.c_uint64, _P, _P, C.c_int,
                                           _P, _P]),
     "tim_graph_features": (C.c_int, [_P, _P]),
+    "tim_select_begin": (C.c_int, [_P]),
+    "tim_select_counts": (C.c_int, [_P, _P]),
+    "tim_select_take": (C.c_int, [_P, C.c_int32, _P]),
+    "tim_run_sharded": (C.c_int, [_P, C.c_int, C.c_double, C.c_double, C.c_uint64, C.c_int,
+                                  C.c_int, _P, _P, _P, _P, _P]),
     "tim_mlp_create": (C.c_int, [C.POINTER(_P), _P, C.c_int]),
     "tim_mlp_destroy": (C.c_int, [_P]),
     "tim_mlp_param_count": (C.c_uint64, [_P]),
@@ -241,6 +246,56 @@ def tim_get_graph(ctx, n: int, m: int):
     _check(ctx, lib().tim_get_graph(ctx, rowptr.ctypes.data_as(_P), src.ctypes.data_as(_P),
                                     thr.ctypes.data_as(_P)))
     return rowptr, src[:m], thr[:m]
+
+
+def tim_select_begin(ctx):
+    _check(ctx, lib().tim_select_begin(ctx))
+
+
+def tim_select_counts(ctx, n: int) -> np.ndarray:
+    counts = np.zeros(max(n, 1), dtype=np.int32)
+    _check(ctx, lib().tim_select_counts(ctx, counts.ctypes.data_as(_P)))
+    return counts[:n]
+
+
+def tim_select_take(ctx, node: int) -> int:
+    newly = C.c_uint64()
+    _check(ctx, lib().tim_select_take(ctx, node, C.byref(newly)))
+    return newly.value
+
+
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_int64), C.c_uint64)
+
+
+def torch_allreduce(dist):
+    """An all-reduce for tim_run_sharded over a torch.distributed process group: sums an
+    int64 numpy array in place (gloo on host memory)."""
+    import torch
+
+    def reduce(arr: np.ndarray):
+        t = torch.from_numpy(arr)
+        dist.all_reduce(t)
+    return reduce
+
+
+def tim_run_sharded(ctx, k: int, eps: float, ell: float, seed: int, rank: int, world: int,
+                    allreduce):
+    """TIM+ for one query over `world` ranks by set id; allreduce(arr) sums an int64 numpy
+    array over the ranks in place. Returns (seeds, covered_fraction, stats dict)."""
+    def cb(user, data, count):
+        try:
+            allreduce(np.ctypeslib.as_array(data, shape=(count,)))
+            return 0
+        except Exception:  # reported by the library as a failed call
+            return -1
+    fn = ALLREDUCE_FN(cb)
+    seeds = np.zeros(k, dtype=np.int32)
+    frac = C.c_double()
+    st = tim_stats()
+    _check(ctx, lib().tim_run_sharded(ctx, k, eps, ell, seed, rank, world,
+                                      C.cast(fn, _P), None, seeds.ctypes.data_as(_P),
+                                      C.byref(frac), C.byref(st)))
+    return seeds, frac.value, st.as_dict()
 
 
 def tim_sample_rr(ctx, theta: int, seed: int, first_set_id: int) -> int:
