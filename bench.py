@@ -39,7 +39,11 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # workload the bench times, divided by the members that pass produced; the traffic of
 # one launch is scaled from it by members. None where no capture of the current kernel
 # exists.
-DRAM_BYTES_PER_MEMBER = {1: None, 2: None, 3: None}
+DRAM_BYTES_PER_MEMBER = {
+    # profiles/sampler_dram_c3.md
+    "c3": {1: 382.7, 2: 779.8, 3: 597.0},
+    "c2": {1: None, 2: None, 3: None},
+}
 FALLBACK_HBM_GBS = 6800.0
 METRIC = "RR sets/s (TIM+ end to end, graph load included)"
 L2_FLUSH_BYTES = 512 << 20
@@ -78,6 +82,10 @@ def parse_args(argv=None):
                         "--scale), for profiling; spread: forward Monte-Carlo spread of "
                         "TIM+'s seeds (--cascades) against the RR estimate")
     p.add_argument("--theta", type=int, default=1_000_000)
+    p.add_argument("--graph", choices=["rmat", "chunglu-tenth"], default="rmat",
+                   help="--mode sample: R-MAT --scale (weighted cascade or LT 1/indeg), or the "
+                        "largest configuration's graph at a tenth of its size (4.16M nodes, "
+                        "140M edges, IC trivalency), drawn on the GPU")
     p.add_argument("--cascades", type=int, default=10_000)
     p.add_argument("--model", choices=["ic", "lt"], default="ic")
     return p.parse_args(argv)
@@ -302,7 +310,7 @@ def run_c2_line(args, nested: bool = False):
     torch.cuda.empty_cache()
 
     # roofline of the dominant kernel: the IC sampler pass with the most device time
-    roofline = sampler_roofline(prof_ic)
+    roofline = sampler_roofline(prof_ic, "c2")
     ic = per_model[tim.TIM_IC][-1]
     lt = per_model[tim.TIM_LT][-1]
     line = {
@@ -358,7 +366,7 @@ def sampler_bytes(p: dict, i: int) -> float:
             + 4.0 * p[f"pass{i}_members"] + 8.0 * p[f"pass{i}_sets"])
 
 
-def sampler_roofline(p: dict) -> dict:
+def sampler_roofline(p: dict, workload: str) -> dict:
     """Roofline of the IC sampler pass with the most device time. Its time is the
     pass's own kernels (for the heavy-set pass: the persistent launches alone), its
     bytes the algorithmic bytes of sampler_bytes, per launch (heavy pass: per batch)."""
@@ -381,7 +389,7 @@ def sampler_roofline(p: dict) -> dict:
     else:
         peak, src = FALLBACK_HBM_GBS, "fallback"
     achieved = alg / (ms / 1e3) / 1e9 if ms > 0 else 0.0
-    ratio = DRAM_BYTES_PER_MEMBER.get(dom)
+    ratio = DRAM_BYTES_PER_MEMBER.get(workload, {}).get(dom)
     return {"kernel": names[dom], "bound": "hbm", "achieved": achieved, "peak": peak,
             "peak_source": src, "unit": "GB/s", "frac": achieved / peak,
             "bytes_per_launch": alg / n, "ms_per_launch": ms / n, "launches": n,
@@ -545,16 +553,24 @@ def run_sample_only(args):
     import torch
 
     from paper_1404_0900_gb300 import tim
-    g = inputs.rmat(args.scale, seed=1)
     model = tim.TIM_IC if args.model == "ic" else tim.TIM_LT
-    w = inputs.weighted_cascade(g) if model == tim.TIM_IC else inputs.lt_inverse_indegree(g)
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     sid0 = 3 << 56
     with tim.Engine(0, stream) as eng:
-        tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, model)
+        if args.graph == "chunglu-tenth":
+            model = tim.TIM_IC
+            dg = inputs.chung_lu_device(4_160_000, 175_000_000, 2.1, seed=1,
+                                        m_exact=140_000_000)
+            w = inputs.trivalency_device(dg, seed=2)
+            tim.tim_load_graph_device(eng.ctx, dg.n, dg.m, dg.rowptr, dg.dst, w, model)
+            del dg, w
+        else:
+            g = inputs.rmat(args.scale, seed=1)
+            w = inputs.weighted_cascade(g) if model == tim.TIM_IC else inputs.lt_inverse_indegree(g)
+            tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, model)
         for _ in range(args.warmup):
             tim.tim_sample_rr(eng.ctx, args.theta, args.seed, sid0)
         tim.tim_get_profile(eng.ctx, reset=True)
@@ -579,7 +595,8 @@ def run_sample_only(args):
                               "examined": prof[f"pass{i}_examined"], "algorithmic_bytes": b,
                               "GB/s": b / (t / 1e3) / 1e9 if t > 0 else 0.0}
     width = sum(prof[f"pass{i}_width"] for i in (1, 2, 3))
-    return {"mode": "sample", "model": args.model, "scale": args.scale, "theta": args.theta,
+    return {"mode": "sample", "model": args.model, "graph": args.graph, "scale": args.scale,
+            "theta": args.theta,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
             "RR sets/s": args.theta * args.steps / (ms / 1e3),
             "GTEPS (in-edges examined)": width / (ms / 1e3) / 1e9, "passes": passes}
@@ -720,7 +737,7 @@ def run_c3_line(args):
         "kpt_round": st["kpt_round"], "kpt_star": st["kpt_star"], "kpt_plus": st["kpt_plus"],
         "theta": st["theta"], "sets_per_step": st["sets_total"],
         "members_select": st["members_select"],
-        "roofline": sampler_roofline(prof),
+        "roofline": sampler_roofline(prof, "c3"),
         "sampler_profile": prof,
         "autotune": tuning,
         "generate_s": gen_s,

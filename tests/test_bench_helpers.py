@@ -41,7 +41,7 @@ def test_roofline_takes_the_pass_with_most_kernel_time():
     p.update({"pass1_ms": 5.0, "pass1_launches": 2, "pass2_ms": 7.0, "pass2_launches": 2,
               "pass3_ms": 40.0, "pass3_launches": 3, "pass3_batches": 4, "pass3_ms_kernel": 20.0,
               "pass3_members": 100, "pass3_sets": 10, "pass3_examined": 1000})
-    r = bench.sampler_roofline(p)
+    r = bench.sampler_roofline(p, "c2")
     assert r["kernel"].startswith("bulk_levels_kernel") and r["launches"] == 4
     # the heavy pass's persistent launches alone: 20 ms over 4 launches
     assert r["ms_per_launch"] == 5.0
@@ -50,6 +50,7 @@ def test_roofline_takes_the_pass_with_most_kernel_time():
 
 
 def test_dram_bytes_per_member_are_from_a_capture_or_null():
-    for i in (1, 2, 3):
-        v = bench.DRAM_BYTES_PER_MEMBER.get(i)
-        assert v is None or 1.0 < v < 10_000.0
+    for wl in ("c3", "c2"):
+        for i in (1, 2, 3):
+            v = bench.DRAM_BYTES_PER_MEMBER[wl].get(i)
+            assert v is None or 1.0 < v < 10_000.0
