@@ -2,9 +2,10 @@
 
 Pure Python, written straight from the paper's definitions, used to pin the oracle:
 
-  spread_ic / spread_lt  -- E[I(S)] (Section 2.1; live-edge view of Section 2.2 and the
-                            triggering model of Section 4.2), by enumerating every
-                            random graph g with its probability.
+  spread                 -- E[I(S)] (Section 2.1; live-edge view of Section 2.2 and the
+                            triggering model of Section 4.2: IC, LT or a general
+                            triggering distribution), by enumerating every random graph g
+                            with its probability.
   rr_distribution        -- the exact distribution of a random RR set (Definitions 1-2)
   kpt_exact              -- KPT = E[I(S*)] for S* = k draws from the in-degree
                             distribution V (Section 3.2, before Lemma 5)
@@ -72,19 +73,44 @@ def lt_worlds(n, edges):
         yield pr, live
 
 
-def worlds(n, edges, model):
+def trig_worlds(n, options):
+    """Every choice of a general triggering model (Section 4.2) with its probability:
+    options[v] = [(probability, [in-neighbours u ...]), ...]; node v picks one option, or
+    none with 1 - the sum of its probabilities; the live edges are u -> v for the picked
+    option's u."""
+    choices = []
+    for v in range(n):
+        opts = list(options[v]) if v < len(options) else []
+        rest = 1.0 - sum(p for p, _ in opts)
+        ch = [(p, us) for p, us in opts if p > 0.0]
+        if rest > 0.0:
+            ch.append((rest, []))
+        choices.append(ch)
+    for combo in itertools.product(*choices):
+        pr = 1.0
+        live = []
+        for v, (p, us) in enumerate(combo):
+            pr *= p
+            live.extend((u, v) for u in us)
+        yield pr, live
+
+
+def worlds(n, edges, model, options=None):
+    if model == 2:
+        return trig_worlds(n, options)
     return ic_worlds(edges) if model == 0 else lt_worlds(n, edges)
 
 
-def spread(n, edges, seeds, model=0):
+def spread(n, edges, seeds, model=0, options=None):
     """E[I(S)]: expected number of nodes reachable from S in a random graph g."""
-    return sum(pr * len(_reach_from(n, live, seeds)) for pr, live in worlds(n, edges, model))
+    return sum(pr * len(_reach_from(n, live, seeds))
+               for pr, live in worlds(n, edges, model, options))
 
 
-def rr_distribution(n, edges, model=0):
+def rr_distribution(n, edges, model=0, options=None):
     """Exact distribution of a random RR set: {frozenset R: probability}."""
     dist = {}
-    for pr, live in worlds(n, edges, model):
+    for pr, live in worlds(n, edges, model, options):
         rev = [(v, u) for u, v in live]
         for root in range(n):
             r = frozenset(_reach_from(n, rev, [root]))

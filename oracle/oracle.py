@@ -24,7 +24,7 @@ import numpy as np
 
 from . import build as _build
 
-IC, LT = 0, 1
+IC, LT, TRIG = 0, 1, 2
 PHASE_KPT, PHASE_REFINE, PHASE_SELECT = 1, 2, 3
 
 _lib = None
@@ -46,32 +46,33 @@ def lib():
             "or_transpose": (i32, [i64, i64, P, P, P, P, P, P]),
             "or_ic_thresholds": (i32, [i64, P, P]),
             "or_lt_thresholds": (i32, [i64, P, P, P]),
-            "or_rr_by_definition": (i64, [P, P, P, i64, i64, i32, u64, u64, P, P]),
-            "or_rr_one": (i64, [P, P, P, i64, i64, i32, u64, u64, P, P]),
-            "or_rr_one_mode": (i64, [P, P, P, i64, i64, i32, i32, u64, u64, P, P]),
-            "or_rr_by_definition_mode": (i64, [P, P, P, i64, i64, i32, i32, u64, u64, P, P]),
-            "or_sample_mode": (i64, [P, P, P, i64, i64, i32, i32, u64, u64, i64, P, P, i64, P,
+            "or_rr_by_definition": (i64, [P, P, P, i64, i64, i32, P, u64, u64, P, P]),
+            "or_rr_one": (i64, [P, P, P, i64, i64, i32, P, u64, u64, P, P]),
+            "or_rr_one_mode": (i64, [P, P, P, i64, i64, i32, P, i32, u64, u64, P, P]),
+            "or_rr_by_definition_mode": (i64, [P, P, P, i64, i64, i32, P, i32, u64, u64, P, P]),
+            "or_sample_mode": (i64, [P, P, P, i64, i64, i32, P, i32, u64, u64, i64, P, P, i64, P,
                                      i32]),
             "or_kappa": (dbl, [i64, i64, i32]),
             "or_kappa_fixed": (u64, [dbl]),
-            "or_sample": (i64, [P, P, P, i64, i64, i32, u64, u64, i64, P, P, i64, P, i32]),
-            "or_kappa_sum": (i32, [P, P, P, i64, i64, i32, i32, u64, u64, i64, P, P, P, i32]),
+            "or_sample": (i64, [P, P, P, i64, i64, i32, P, u64, u64, i64, P, P, i64, P, i32]),
+            "or_kappa_sum": (i32, [P, P, P, i64, i64, i32, P, i32, u64, u64, i64, P, P, P, i32]),
             "or_log_binom": (dbl, [i64, i64]),
             "or_lambda": (dbl, [i64, i32, dbl, dbl]),
             "or_eps_prime": (dbl, [dbl, i32, dbl]),
             "or_lambda_prime": (dbl, [i64, dbl, dbl]),
             "or_c_i": (i64, [i64, dbl, i32]),
             "or_kpt_rounds": (i32, [i64]),
-            "or_kpt_estimate": (i32, [P, P, P, i64, i64, i32, i32, dbl, u64, u64, i32,
+            "or_kpt_estimate": (i32, [P, P, P, i64, i64, i32, P, i32, dbl, u64, u64, i32,
                                       P, P, P, P, P, P]),
             "or_greedy": (i64, [i64, i64, P, P, i32, P, P]),
-            "or_covered_count": (i64, [P, P, P, i64, i64, i32, u64, u64, i64, P, i32]),
+            "or_covered_count": (i64, [P, P, P, i64, i64, i32, P, u64, u64, i64, P, i32]),
             "or_skip_q": (u64, [u32, i32]),
             "or_skip_bit": (i32, [u64, u64]),
             "or_skip_live": (i64, [u64, u64, i64, i64, u32, P]),
+            "or_trig_build": (i32, [i64, i64, P, P, P, P, P, P, P, P, P]),
             "or_out_positions": (i32, [i64, i64, P, P, P, P, P]),
-            "or_cascade_one": (i64, [P, P, P, i64, i64, i32, P, P, P, u64, u64, P, i32, P]),
-            "or_spread_mc": (i64, [P, P, P, i64, i64, i32, P, P, P, u64, u64, i64, P, i32, P,
+            "or_cascade_one": (i64, [P, P, P, i64, i64, i32, P, P, P, P, u64, u64, P, i32, P]),
+            "or_spread_mc": (i64, [P, P, P, i64, i64, i32, P, P, P, P, u64, u64, i64, P, i32, P,
                                    i32]),
         }
         for name, (res, args) in sig.items():
@@ -187,6 +188,7 @@ class OracleGraph:
     thr: np.ndarray  # uint32[m]
     in_w: np.ndarray  # float32[m]
     out: tuple | None = None  # (out_rowptr, out_pos, pos_dst), built on first use
+    trig: object = None  # triggering model: (or_trig structure, the arrays it points to)
 
     def indeg(self) -> np.ndarray:
         return np.diff(self.rowptr)
@@ -205,7 +207,8 @@ class OracleGraph:
         return self.out
 
     def args(self):
-        return (_p(self.rowptr), _p(self.src), _p(self.thr), self.n, self.m, self.model)
+        t = C.byref(self.trig[0]) if self.trig is not None else None
+        return (_p(self.rowptr), _p(self.src), _p(self.thr), self.n, self.m, self.model, t)
 
 
 def load_graph(n: int, rowptr, dst, weight, model: int) -> OracleGraph:
@@ -229,6 +232,44 @@ def load_graph(n: int, rowptr, dst, weight, model: int) -> OracleGraph:
     if rc != 0:
         raise ValueError(f"invalid weights (code {rc})")
     return OracleGraph(n, m, model, in_rowptr, in_src, thr, in_w)
+
+
+class or_trig(C.Structure):
+    _fields_ = [("node_opt", C.c_void_p), ("opt_cum", C.c_void_p), ("opt_off", C.c_void_p),
+                ("opt_pos", C.c_void_p)]
+
+
+def load_graph_triggering(n: int, rowptr, dst, opt_rowptr, opt_prob, opt_edge_rowptr,
+                          opt_edges) -> OracleGraph:
+    """G^T with a triggering model (Section 4.2): node v picks option o in opt_rowptr[v] ..
+    opt_rowptr[v+1] with probability opt_prob[o] (none with the rest); option o is the set
+    of out-CSR edges opt_edges[opt_edge_rowptr[o] .. opt_edge_rowptr[o+1]) into v."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    m = int(dst.shape[0])
+    in_rowptr = np.zeros(n + 1, dtype=np.int64)
+    in_src = np.zeros(max(m, 1), dtype=np.int32)
+    in_w = np.zeros(max(m, 1), dtype=np.float32)
+    rc = lib().or_transpose(n, m, _p(rowptr), _p(dst), None, _p(in_rowptr), _p(in_src), _p(in_w))
+    if rc != 0:
+        raise ValueError(f"invalid graph (code {rc})")
+    orow = np.ascontiguousarray(opt_rowptr, dtype=np.int64)
+    oprob = np.ascontiguousarray(opt_prob, dtype=np.float32)
+    oer = np.ascontiguousarray(opt_edge_rowptr, dtype=np.int64)
+    oe = np.ascontiguousarray(opt_edges, dtype=np.int64)
+    if orow.shape[0] != n + 1 or oer.shape[0] != oprob.shape[0] + 1:
+        raise ValueError("triggering arrays of the wrong length")
+    cum = np.zeros(max(oprob.shape[0], 1), dtype=np.uint32)
+    pos = np.zeros(max(oe.shape[0], 1), dtype=np.int64)
+    if oe.shape[0] == 0:
+        oe = np.zeros(1, dtype=np.int64)
+    rc = lib().or_trig_build(n, m, _p(rowptr), _p(dst), _p(in_rowptr), _p(orow), _p(oprob),
+                             _p(oer), _p(oe), _p(cum), _p(pos))
+    if rc != 0:
+        raise ValueError(f"invalid triggering distribution (code {rc})")
+    t = or_trig(orow.ctypes.data, cum.ctypes.data, oer.ctypes.data, pos.ctypes.data)
+    thr = np.zeros(max(m, 1), dtype=np.uint32)
+    return OracleGraph(n, m, TRIG, in_rowptr, in_src, thr, in_w, trig=(t, orow, cum, oer, pos))
 
 
 # ------------------------------------------------------------------- RR sets

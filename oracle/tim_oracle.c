@@ -79,6 +79,7 @@ typedef unsigned __int128 u128;
 
 #define MODEL_IC 0
 #define MODEL_LT 1
+#define MODEL_TRIG 2
 
 #define PHASE_KPT 1ull
 #define PHASE_REFINE 2ull
@@ -190,6 +191,64 @@ int or_transpose(int64_t n, int64_t m, const int64_t* out_rowptr, const int32_t*
     return OR_OK;
 }
 
+/* Triggering distribution on G^T from its description on G: node v has options
+ * opt_rowptr[v] .. opt_rowptr[v+1]; option o has probability opt_prob[o] and the
+ * out-CSR edge ids opt_edges[opt_edge_rowptr[o] .. opt_edge_rowptr[o+1]), each an edge
+ * into v, distinct within the option. Writes the options' cumulative thresholds
+ * (inclusive prefix of floor(pi * 2^32) over v's options, saturated at 2^32 - 1) and their
+ * in-CSR positions. The in-CSR position of an out-edge is found by replaying the
+ * transpose: in-lists are filled in out-CSR order. A node's probabilities must lie in
+ * [0, 1] and sum to at most 1 + 1e-5. */
+int or_trig_build(int64_t n, int64_t m, const int64_t* out_rowptr, const int32_t* out_dst,
+                  const int64_t* in_rowptr, const int64_t* opt_rowptr, const float* opt_prob,
+                  const int64_t* opt_edge_rowptr, const int64_t* opt_edges, uint32_t* opt_cum,
+                  int64_t* opt_pos) {
+    int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
+    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n + 1));
+    if (!pos || !cur) {
+        free(pos);
+        free(cur);
+        return OR_ERR_OOM;
+    }
+    for (int64_t v = 0; v <= n; v++) cur[v] = v < n ? in_rowptr[v] : 0;
+    for (int64_t u = 0; u < n; u++)
+        for (int64_t e = out_rowptr[u]; e < out_rowptr[u + 1]; e++) pos[e] = cur[out_dst[e]]++;
+    free(cur);
+    int rc = OR_OK;
+    if (opt_rowptr[0] != 0) rc = OR_ERR_ARG;
+    for (int64_t v = 0; v < n && rc == OR_OK; v++) {
+        if (opt_rowptr[v + 1] < opt_rowptr[v]) {
+            rc = OR_ERR_ARG;
+            break;
+        }
+        double tot = 0.0;
+        uint64_t acc = 0;
+        for (int64_t o = opt_rowptr[v]; o < opt_rowptr[v + 1] && rc == OR_OK; o++) {
+            double p = (double)opt_prob[o];
+            if (!(p >= 0.0 && p <= 1.0) || opt_edge_rowptr[o + 1] < opt_edge_rowptr[o]) {
+                rc = OR_ERR_ARG;
+                break;
+            }
+            tot += p;
+            acc += (uint64_t)floor(p * 4294967296.0);
+            opt_cum[o] = acc > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)acc;
+            for (int64_t i = opt_edge_rowptr[o]; i < opt_edge_rowptr[o + 1]; i++) {
+                int64_t e = opt_edges[i];
+                if (e < 0 || e >= m || out_dst[e] != v) {
+                    rc = OR_ERR_ARG;
+                    break;
+                }
+                opt_pos[i] = pos[e];
+                for (int64_t i2 = opt_edge_rowptr[o]; i2 < i; i2++)
+                    if (opt_edges[i2] == e) rc = OR_ERR_ARG;  /* repeated edge */
+            }
+        }
+        if (tot > 1.0 + 1e-5) rc = OR_ERR_ARG;
+    }
+    free(pos);
+    return rc;
+}
+
 /* IC live-edge threshold of each in-edge: live iff word < thr (p >= 1: always). */
 int or_ic_thresholds(int64_t m, const float* in_w, uint32_t* thr) {
     for (int64_t j = 0; j < m; j++) {
@@ -220,6 +279,17 @@ int or_lt_thresholds(int64_t n, const int64_t* in_rowptr, const float* in_w, uin
     return OR_OK;
 }
 
+/* A triggering model (Section 4.2) on G^T: node v picks option o in node_opt[v] ..
+ * node_opt[v+1] with probability pi_o (none with the rest); option o activates v through
+ * the in-edges at in-CSR positions opt_pos[opt_off[o] .. opt_off[o+1]). opt_cum holds the
+ * inclusive prefix of floor(pi * 2^32) over v's options, saturated at 2^32 - 1. */
+typedef struct {
+    const int64_t* node_opt;
+    const uint32_t* opt_cum;
+    const int64_t* opt_off;
+    const int64_t* opt_pos;
+} or_trig;
+
 typedef struct {
     int64_t n, m;
     const int64_t* rowptr; /* in-CSR offsets, n+1 */
@@ -227,6 +297,7 @@ typedef struct {
     const uint32_t* thr;   /* IC thresholds or LT cumulative thresholds, m */
     int model;
     int per_edge; /* 1: one coin per in-edge in every IC list (no geometric skipping) */
+    const or_trig* trig; /* MODEL_TRIG only */
 } or_graph;
 
 static int64_t indeg(const or_graph* g, int64_t v) { return g->rowptr[v + 1] - g->rowptr[v]; }
@@ -342,6 +413,15 @@ static int64_t lt_pick(const or_graph* g, uint64_t seed, uint64_t sid, int64_t v
     return -1;
 }
 
+/* Triggering option of v for RR set sid (Section 4.2): the same draw as the LT pick,
+ * the first option whose cumulative threshold exceeds it; -1 for none. */
+static int64_t trig_pick(const or_graph* g, uint64_t seed, uint64_t sid, int64_t v) {
+    uint32_t x = or_lt_word(seed, sid, v);
+    for (int64_t o = g->trig->node_opt[v]; o < g->trig->node_opt[v + 1]; o++)
+        if (x < g->trig->opt_cum[o]) return o;
+    return -1;
+}
+
 /* One random RR set by randomised BFS from a uniform root (Section 3.1,
  * "Implementation"; triggering form of Section 4.2). members[] doubles as the BFS
  * queue; mark[] is an n-byte scratch array that is all-zero on entry and on exit.
@@ -376,6 +456,16 @@ static int64_t rr_bfs(const or_graph* g, uint64_t seed, uint64_t sid, int32_t* m
                     members[tail++] = u;
                 }
             }
+        } else if (g->model == MODEL_TRIG) {
+            int64_t o = trig_pick(g, seed, sid, v);
+            if (o >= 0)
+                for (int64_t e = g->trig->opt_off[o]; e < g->trig->opt_off[o + 1]; e++) {
+                    int32_t u = g->src[g->trig->opt_pos[e]];
+                    if (!mark[u]) {
+                        mark[u] = 1;
+                        members[tail++] = u;
+                    }
+                }
         } else {
             int64_t j = lt_pick(g, seed, sid, v);
             if (j >= 0) {
@@ -398,10 +488,10 @@ static int64_t rr_bfs(const or_graph* g, uint64_t seed, uint64_t sid, int32_t* m
  * repeated passes over that list until nothing changes. Independent of any search
  * order. Returns |R|; members are written in ascending id order. */
 int64_t or_rr_by_definition_mode(const int64_t* rowptr, const int32_t* src,
-                                 const uint32_t* thr, int64_t n, int64_t m, int model,
+                                 const uint32_t* thr, int64_t n, int64_t m, int model, const or_trig* trig,
                                  int per_edge, uint64_t seed, uint64_t sid, int32_t* members,
                                  int64_t* width) {
-    or_graph g = {n, m, rowptr, src, thr, model, per_edge};
+    or_graph g = {n, m, rowptr, src, thr, model, per_edge, trig};
     int64_t* lu = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
     int64_t* lv = (int64_t*)malloc(sizeof(int64_t) * (size_t)(m > 0 ? m : 1));
     uint8_t* in_r = (uint8_t*)calloc((size_t)n, 1);
@@ -427,6 +517,14 @@ int64_t or_rr_by_definition_mode(const int64_t* rowptr, const int32_t* src,
             for (int64_t j = rowptr[v]; j < rowptr[v + 1]; j++)
                 if (ic_live(or_ic_word(seed, sid, j), thr[j])) {
                     lu[nl] = src[j];
+                    lv[nl] = v;
+                    nl++;
+                }
+        } else if (model == MODEL_TRIG) {
+            int64_t o = trig_pick(&g, seed, sid, v);
+            if (o >= 0)
+                for (int64_t e = trig->opt_off[o]; e < trig->opt_off[o + 1]; e++) {
+                    lu[nl] = src[trig->opt_pos[e]];
                     lv[nl] = v;
                     nl++;
                 }
@@ -463,16 +561,17 @@ int64_t or_rr_by_definition_mode(const int64_t* rowptr, const int32_t* src,
 }
 
 int64_t or_rr_by_definition(const int64_t* rowptr, const int32_t* src, const uint32_t* thr,
-                            int64_t n, int64_t m, int model, uint64_t seed, uint64_t sid,
+                            int64_t n, int64_t m, int model, const or_trig* trig, uint64_t seed, uint64_t sid,
                             int32_t* members, int64_t* width) {
-    return or_rr_by_definition_mode(rowptr, src, thr, n, m, model, 0, seed, sid, members, width);
+    return or_rr_by_definition_mode(rowptr, src, thr, n, m, model, trig, 0, seed, sid, members,
+                                    width);
 }
 
 /* One RR set by BFS, exported for single-set checks (per_edge: see skip_list). */
 int64_t or_rr_one_mode(const int64_t* rowptr, const int32_t* src, const uint32_t* thr,
-                       int64_t n, int64_t m, int model, int per_edge, uint64_t seed,
+                       int64_t n, int64_t m, int model, const or_trig* trig, int per_edge, uint64_t seed,
                        uint64_t sid, int32_t* members, int64_t* width) {
-    or_graph g = {n, m, rowptr, src, thr, model, per_edge};
+    or_graph g = {n, m, rowptr, src, thr, model, per_edge, trig};
     uint8_t* mark = (uint8_t*)calloc((size_t)n, 1);
     if (!mark) return OR_ERR_OOM;
     int64_t r = rr_bfs(&g, seed, sid, members, mark, width);
@@ -481,9 +580,9 @@ int64_t or_rr_one_mode(const int64_t* rowptr, const int32_t* src, const uint32_t
 }
 
 int64_t or_rr_one(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
-                  int64_t m, int model, uint64_t seed, uint64_t sid, int32_t* members,
+                  int64_t m, int model, const or_trig* trig, uint64_t seed, uint64_t sid, int32_t* members,
                   int64_t* width) {
-    return or_rr_one_mode(rowptr, src, thr, n, m, model, 0, seed, sid, members, width);
+    return or_rr_one_mode(rowptr, src, thr, n, m, model, trig, 0, seed, sid, members, width);
 }
 
 /* ---------------------------------------------------------- kappa, Eq. 6 */
@@ -557,10 +656,10 @@ static int set_threads(int nthreads) {
  * and the caller retries with a bigger buffer. Sets are independent, so chunks of
  * set ids may run on several host threads; the result does not depend on it. */
 int64_t or_sample_mode(const int64_t* rowptr, const int32_t* src, const uint32_t* thr,
-                       int64_t n, int64_t m, int model, int per_edge, uint64_t seed,
+                       int64_t n, int64_t m, int model, const or_trig* trig, int per_edge, uint64_t seed,
                        uint64_t sid0, int64_t count, int64_t* off, int32_t* mem,
                        int64_t mem_cap, int64_t* widths, int nthreads) {
-    or_graph g = {n, m, rowptr, src, thr, model, per_edge};
+    or_graph g = {n, m, rowptr, src, thr, model, per_edge, trig};
     if (count < 0) return OR_ERR_ARG;
     off[0] = 0;
     if (count == 0) return 0;
@@ -630,18 +729,18 @@ int64_t or_sample_mode(const int64_t* rowptr, const int32_t* src, const uint32_t
 }
 
 int64_t or_sample(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
-                  int64_t m, int model, uint64_t seed, uint64_t sid0, int64_t count,
+                  int64_t m, int model, const or_trig* trig, uint64_t seed, uint64_t sid0, int64_t count,
                   int64_t* off, int32_t* mem, int64_t mem_cap, int64_t* widths, int nthreads) {
-    return or_sample_mode(rowptr, src, thr, n, m, model, 0, seed, sid0, count, off, mem, mem_cap,
-                          widths, nthreads);
+    return or_sample_mode(rowptr, src, thr, n, m, model, trig, 0, seed, sid0, count, off, mem,
+                          mem_cap, widths, nthreads);
 }
 
 /* Sum of kappa over RR sets sid0 .. sid0+count-1 in 2^-63 fixed point, as a
  * 128-bit integer split into (hi, lo). Optionally returns sum of widths. */
 int or_kappa_sum(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
-                 int64_t m, int model, int k, uint64_t seed, uint64_t sid0, int64_t count,
+                 int64_t m, int model, const or_trig* trig, int k, uint64_t seed, uint64_t sid0, int64_t count,
                  uint64_t* sum_hi, uint64_t* sum_lo, int64_t* width_sum, int nthreads) {
-    or_graph g = {n, m, rowptr, src, thr, model};
+    or_graph g = {n, m, rowptr, src, thr, model, 0, trig};
     nthreads = set_threads(nthreads);
     u128 total = 0;
     int64_t wtot = 0;
@@ -722,7 +821,7 @@ int or_kpt_rounds(int64_t n) {
  * KPT*. Also returns the last executed round (the R' of Algorithm 3) and that
  * round's exact fixed-point kappa sum and set count. */
 int or_kpt_estimate(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
-                    int64_t m, int model, int k, double ell, uint64_t seed, uint64_t tag,
+                    int64_t m, int model, const or_trig* trig, int k, double ell, uint64_t seed, uint64_t tag,
                     int nthreads,
                     double* kpt_star, int* stop_round, int* last_round, int64_t* last_c,
                     uint64_t* last_sum_hi, uint64_t* last_sum_lo) {
@@ -735,7 +834,7 @@ int or_kpt_estimate(const int64_t* rowptr, const int32_t* src, const uint32_t* t
     for (int i = 1; i <= rounds; i++) {
         int64_t c = or_c_i(n, ell, i);
         uint64_t hi, lo;
-        int rc = or_kappa_sum(rowptr, src, thr, n, m, model, k, seed,
+        int rc = or_kappa_sum(rowptr, src, thr, n, m, model, trig, k, seed,
                               or_make_sid(PHASE_KPT, i, tag << 32), c, &hi, &lo, NULL, nthreads);
         if (rc) return rc;
         *last_round = i;
@@ -802,9 +901,9 @@ int64_t or_greedy(int64_t n, int64_t n_sets, const int64_t* off, const int32_t* 
 /* Number of RR sets sid0 .. sid0+count-1 that intersect the node set `in_s`
  * (n bytes, 1 = member): the covered count of Algorithm 3. */
 int64_t or_covered_count(const int64_t* rowptr, const int32_t* src, const uint32_t* thr,
-                         int64_t n, int64_t m, int model, uint64_t seed, uint64_t sid0,
+                         int64_t n, int64_t m, int model, const or_trig* trig, uint64_t seed, uint64_t sid0,
                          int64_t count, const uint8_t* in_s, int nthreads) {
-    or_graph g = {n, m, rowptr, src, thr, model};
+    or_graph g = {n, m, rowptr, src, thr, model, 0, trig};
     nthreads = set_threads(nthreads);
     int64_t cov = 0;
     int fail = 0;
@@ -884,8 +983,18 @@ static int64_t cascade(const or_graph* g, const int64_t* out_rowptr, const int64
             int64_t j = out_pos[e];
             int32_t v = pos_dst[j];
             if (mark[v]) continue;
-            int kept = g->model == MODEL_IC ? ic_live(or_ic_word(seed, sid, j), g->thr[j])
-                                            : lt_pick(g, seed, sid, v) == j;
+            int kept;
+            if (g->model == MODEL_IC) {
+                kept = ic_live(or_ic_word(seed, sid, j), g->thr[j]);
+            } else if (g->model == MODEL_TRIG) {
+                int64_t o = trig_pick(g, seed, sid, v);
+                kept = 0;
+                if (o >= 0)
+                    for (int64_t e = g->trig->opt_off[o]; e < g->trig->opt_off[o + 1]; e++)
+                        if (g->trig->opt_pos[e] == j) kept = 1;
+            } else {
+                kept = lt_pick(g, seed, sid, v) == j;
+            }
             if (kept) {
                 mark[v] = 1;
                 queue[tail++] = v;
@@ -899,10 +1008,10 @@ static int64_t cascade(const or_graph* g, const int64_t* out_rowptr, const int64
 /* The activated nodes of one cascade (sid) into members[] (capacity n); returns their
  * count. */
 int64_t or_cascade_one(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
-                       int64_t m, int model, const int64_t* out_rowptr, const int64_t* out_pos,
+                       int64_t m, int model, const or_trig* trig, const int64_t* out_rowptr, const int64_t* out_pos,
                        const int32_t* pos_dst, uint64_t seed, uint64_t sid, const int32_t* seeds,
                        int k, int32_t* members) {
-    or_graph g = {n, m, rowptr, src, thr, model};
+    or_graph g = {n, m, rowptr, src, thr, model, 0, trig};
     for (int i = 0; i < k; i++)
         if (seeds[i] < 0 || seeds[i] >= n) return OR_ERR_ARG;
     uint8_t* mark = (uint8_t*)calloc((size_t)n, 1);
@@ -916,10 +1025,10 @@ int64_t or_cascade_one(const int64_t* rowptr, const int32_t* src, const uint32_t
  * the total over all cascades (an exact integer; the estimate of E[I(S)] is
  * total / count) or an error code. */
 int64_t or_spread_mc(const int64_t* rowptr, const int32_t* src, const uint32_t* thr, int64_t n,
-                     int64_t m, int model, const int64_t* out_rowptr, const int64_t* out_pos,
+                     int64_t m, int model, const or_trig* trig, const int64_t* out_rowptr, const int64_t* out_pos,
                      const int32_t* pos_dst, uint64_t seed, uint64_t sid0, int64_t count,
                      const int32_t* seeds, int k, int64_t* counts, int nthreads) {
-    or_graph g = {n, m, rowptr, src, thr, model};
+    or_graph g = {n, m, rowptr, src, thr, model, 0, trig};
     for (int i = 0; i < k; i++)
         if (seeds[i] < 0 || seeds[i] >= n) return OR_ERR_ARG;
     nthreads = set_threads(nthreads);

@@ -199,6 +199,57 @@ def uniform_random(g: Graph, lo: float = 0.0, hi: float = 1.0, seed: int = 1) ->
     return rng.uniform(lo, hi, size=g.m).astype(np.float32)
 
 
+# ----------------------------------------------------- triggering distributions
+#
+# A triggering distribution (Section 4.2) as arrays over the out-CSR of G:
+#   opt_rowptr      int64[n+1]   options of node v: opt_rowptr[v] .. opt_rowptr[v+1]
+#   opt_prob        float32[k]   probability of each option (a node's sum <= 1)
+#   opt_edge_rowptr int64[k+1]   edges of option o: opt_edge_rowptr[o] .. [o+1]
+#   opt_edges       int64[..]    out-CSR edge ids, each an edge into the option's node
+
+def _in_edges_by_node(g: Graph):
+    """Out-CSR edge ids into each node, ascending by source (edge id order)."""
+    order = np.argsort(g.dst, kind="stable")
+    starts = np.zeros(g.n + 1, dtype=np.int64)
+    np.cumsum(np.bincount(g.dst, minlength=g.n), out=starts[1:])
+    return order.astype(np.int64), starts
+
+
+def triggering_from_lt(g: Graph, w: np.ndarray):
+    """The LT model as a triggering distribution: node v picks the single in-edge e with
+    probability w[e], its options in the order of their sources."""
+    order, starts = _in_edges_by_node(g)
+    return (starts, np.asarray(w, dtype=np.float32)[order],
+            np.arange(g.m + 1, dtype=np.int64), order)
+
+
+def triggering_random(g: Graph, max_options: int = 3, max_size: int = 4,
+                      mass=(0.5, 1.0), seed: int = 1):
+    """Random triggering distributions: a node with in-edges gets 1..max_options options,
+    each a uniform random subset of 1..max_size of its in-edges (distinct within the
+    option), with probabilities drawn uniformly and scaled to a total mass drawn from
+    `mass` (the rest: no in-edge)."""
+    rng = _rng(seed)
+    order, starts = _in_edges_by_node(g)
+    orow = [0]
+    probs, erow, edges = [], [0], []
+    for v in range(g.n):
+        ins = order[starts[v]:starts[v + 1]]
+        if ins.size:
+            k = int(rng.integers(1, max_options + 1))
+            r = rng.random(k)
+            r *= rng.uniform(mass[0], mass[1]) / r.sum()
+            for i in range(k):
+                size = int(rng.integers(1, min(max_size, ins.size) + 1))
+                pick = np.sort(rng.choice(ins.size, size=size, replace=False))
+                edges.extend(ins[pick].tolist())
+                erow.append(len(edges))
+                probs.append(r[i])
+        orow.append(len(probs))
+    return (np.array(orow, dtype=np.int64), np.array(probs, dtype=np.float32),
+            np.array(erow, dtype=np.int64), np.array(edges, dtype=np.int64))
+
+
 # ------------------------------------------------------------ small hand graphs
 
 def star_in(n: int) -> Graph:
