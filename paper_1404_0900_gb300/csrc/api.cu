@@ -191,6 +191,8 @@ int tim_destroy(tim_ctx* ctx) {
                       &ctx->scratch_a, &ctx->scratch_b, &ctx->scratch_c, &ctx->scratch_d,
                       &ctx->scratch_e, &ctx->scratch_f, &ctx->scal,     &ctx->bulk_bitmap,
                       &ctx->bulk_slot, &ctx->bulk_bsum, &ctx->bulk_bar,
+                      &ctx->node_opt, &ctx->opt_cum, &ctx->opt_off, &ctx->opt_pos,
+                      &ctx->opt_node, &ctx->ld_posof,
                       &ctx->bulk_F,    &ctx->bulk_M,    &ctx->bulk_ng,   &ctx->bulk_gp,
                       &ctx->bulk_scal, &ctx->batch,     &ctx->greedy_batch,
                       &ctx->out_rowptr, &ctx->out_rec,  &ctx->mc_bitmap, &ctx->mc_queue,
@@ -336,6 +338,8 @@ int tim_load_graph_device(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_o
     if (!ctx) return TIM_ERR_ARG;
     if (!d_out_rowptr || (m > 0 && (!d_out_dst || !d_edge_w)))
         return tim_fail(ctx, TIM_ERR_ARG, "null graph array");
+    if (model == TIM_TRIG)
+        return tim_fail(ctx, TIM_ERR_ARG, "triggering models load with tim_load_graph_triggering");
     DeviceGuard g(ctx->device);
     // the build's temporaries and sort scratch stay allocated for the next load
     // (tim_destroy frees them)
@@ -357,6 +361,96 @@ int tim_get_graph(tim_ctx* ctx, uint64_t* rowptr, uint32_t* src, uint32_t* thr) 
         CUDA_TRY(ctx, cudaMemcpyAsync(thr, ctx->thr.p, m * sizeof(uint32_t),
                                       cudaMemcpyDeviceToHost, ctx->stream));
     return tim_sync(ctx);
+}
+
+int tim_load_graph_triggering(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* out_rowptr,
+                              const int32_t* out_dst, const int64_t* opt_rowptr,
+                              const float* opt_prob, const int64_t* opt_edge_rowptr,
+                              const int64_t* opt_edges) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (!out_rowptr || (m > 0 && !out_dst) || !opt_rowptr || !opt_edge_rowptr || n < 2 || m < 0)
+        return tim_fail(ctx, TIM_ERR_ARG, "invalid graph arguments");
+    // the option structure: offsets start at 0 and never decrease; an option lists each
+    // edge once (the edges' range and destinations are checked on the device)
+    if (opt_rowptr[0] != 0) return tim_fail(ctx, TIM_ERR_ARG, "opt_rowptr[0] must be 0");
+    for (int64_t v = 0; v < n; v++)
+        if (opt_rowptr[v + 1] < opt_rowptr[v])
+            return tim_fail(ctx, TIM_ERR_ARG, "opt_rowptr must not decrease");
+    const int64_t n_opts = opt_rowptr[n];
+    if (n_opts > 0 && !opt_prob) return tim_fail(ctx, TIM_ERR_ARG, "null opt_prob");
+    if (opt_edge_rowptr[0] != 0) return tim_fail(ctx, TIM_ERR_ARG, "opt_edge_rowptr[0] must be 0");
+    for (int64_t o = 0; o < n_opts; o++)
+        if (opt_edge_rowptr[o + 1] < opt_edge_rowptr[o])
+            return tim_fail(ctx, TIM_ERR_ARG, "opt_edge_rowptr must not decrease");
+    const int64_t n_ent = opt_edge_rowptr[n_opts];
+    if (n_ent > 0 && !opt_edges) return tim_fail(ctx, TIM_ERR_ARG, "null opt_edges");
+    if (n_ent >= 0xFFFFFFF0ll) return tim_fail(ctx, TIM_ERR_ARG, "too many option entries");
+    {
+        std::vector<int64_t> tmp;
+        for (int64_t o = 0; o < n_opts; o++) {
+            tmp.assign(opt_edges + opt_edge_rowptr[o], opt_edges + opt_edge_rowptr[o + 1]);
+            std::sort(tmp.begin(), tmp.end());
+            if (std::adjacent_find(tmp.begin(), tmp.end()) != tmp.end())
+                return tim_fail(ctx, TIM_ERR_ARG, "an option lists an edge twice");
+        }
+    }
+    DeviceGuard g(ctx->device);
+    DevBuf r, d, prob, edges;
+    int rc = TIM_OK;
+    do {
+        if ((rc = tim_ensure(ctx, r, (size_t)(n + 1) * sizeof(int64_t)))) break;
+        if ((rc = tim_ensure(ctx, d, (size_t)(m + 1) * sizeof(int32_t)))) break;
+        if ((rc = tim_ensure(ctx, prob, (size_t)(n_opts + 1) * sizeof(float)))) break;
+        if ((rc = tim_ensure(ctx, edges, (size_t)(n_ent + 1) * sizeof(int64_t)))) break;
+        if ((rc = tim_cuda_check(ctx, cudaMemcpyAsync(r.p, out_rowptr, (size_t)(n + 1) * 8,
+                                                      cudaMemcpyHostToDevice, ctx->stream),
+                                 "copy rowptr")))
+            break;
+        if (m > 0 && (rc = tim_cuda_check(ctx, cudaMemcpyAsync(d.p, out_dst, (size_t)m * 4,
+                                                               cudaMemcpyHostToDevice,
+                                                               ctx->stream),
+                                          "copy dst")))
+            break;
+        if ((rc = tim_graph_build(ctx, n, m, (const int64_t*)r.p, (const int32_t*)d.p, nullptr,
+                                  TIM_TRIG)))
+            break;
+        ctx->have_graph = false;
+        if ((rc = tim_ensure(ctx, ctx->node_opt, (size_t)(n + 1) * sizeof(uint64_t)))) break;
+        if ((rc = tim_ensure(ctx, ctx->opt_off, (size_t)(n_opts + 1) * sizeof(uint64_t)))) break;
+        if ((rc = tim_ensure(ctx, ctx->opt_pos, (size_t)(n_ent + 1) * sizeof(uint32_t)))) break;
+        if ((rc = tim_cuda_check(ctx, cudaMemcpyAsync(ctx->node_opt.p, opt_rowptr,
+                                                      (size_t)(n + 1) * 8,
+                                                      cudaMemcpyHostToDevice, ctx->stream),
+                                 "copy options")))
+            break;
+        if ((rc = tim_cuda_check(ctx, cudaMemcpyAsync(ctx->opt_off.p, opt_edge_rowptr,
+                                                      (size_t)(n_opts + 1) * 8,
+                                                      cudaMemcpyHostToDevice, ctx->stream),
+                                 "copy option offsets")))
+            break;
+        if (n_opts > 0 &&
+            (rc = tim_cuda_check(ctx, cudaMemcpyAsync(prob.p, opt_prob, (size_t)n_opts * 4,
+                                                      cudaMemcpyHostToDevice, ctx->stream),
+                                 "copy option probabilities")))
+            break;
+        if (n_ent > 0 &&
+            (rc = tim_cuda_check(ctx, cudaMemcpyAsync(edges.p, opt_edges, (size_t)n_ent * 8,
+                                                      cudaMemcpyHostToDevice, ctx->stream),
+                                 "copy option edges")))
+            break;
+        if ((rc = tim_trig_build(ctx, (const int32_t*)d.p, (const uint64_t*)ctx->node_opt.p,
+                                 (const float*)prob.p, (uint64_t)n_opts,
+                                 (const uint64_t*)ctx->opt_off.p, (const int64_t*)edges.p,
+                                 (uint64_t)n_ent)))
+            break;
+        ctx->have_graph = true;
+    } while (0);
+    cudaStreamSynchronize(ctx->stream);
+    tim_free(r);
+    tim_free(d);
+    tim_free(prob);
+    tim_free(edges);
+    return rc;
 }
 
 int tim_load_graph(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* out_rowptr,
@@ -1066,6 +1160,10 @@ static int run_batch(tim_query* qs, int nq, uint64_t seed, int plus, tim_mlp* ml
         tim_ctx* c = qs[i].ctx;
         if (!c || !c->have_graph) return tim_fail(owner, TIM_ERR_STATE, "query without a graph");
         if (c->device != owner->device) return tim_fail(owner, TIM_ERR_ARG, "queries on several devices");
+        if (c->model == TIM_TRIG)
+            return tim_fail(owner, TIM_ERR_ARG,
+                            "batched queries take IC and LT graphs; a triggering-model graph runs "
+                            "one query at a time");
         if (qs[i].k < 1 || qs[i].k > c->n || !(qs[i].eps > 0.0) || !(qs[i].ell > 0.0) ||
             !qs[i].seeds || qs[i].tag > 0xFFFF)
             return tim_fail(owner, TIM_ERR_ARG, "need 1 <= k <= n, eps > 0, l > 0, seeds, tag < 65536");

@@ -62,6 +62,10 @@ struct tim_ctx {
     DevBuf src;     // uint32[m + 4]
     DevBuf thr;     // uint32[m + 4] IC thresholds or LT inclusive cumulative thresholds
     DevBuf qtab;      // IC: per skip-rule node, Q_0..Q_31 of its geometric gaps (u64[32])
+    // triggering model: options of node v at node_opt[v] .. node_opt[v+1] (u64[n+1]);
+    // per option its inclusive cumulative threshold (u32) and its in-edges at opt_off[o]
+    // .. opt_off[o+1] (u64) as in-CSR positions opt_pos (u32)
+    DevBuf node_opt, opt_cum, opt_off, opt_pos, opt_node;
     DevBuf node_thr;  // IC: uint64[n], low word = threshold shared by all in-edges of v,
                       // bit 32 set when they do share one (empty in-lists included),
                       // bits 33..63 = 1 + index of the node's qtab entry (skip rule)
@@ -126,6 +130,7 @@ struct tim_ctx {
 
     // graph-load temporaries (graph.cu), kept between loads
     DevBuf ld_keys, ld_vals, ld_lt_t, ld_lt_e, ld_nonuni, ld_srcof;
+    DevBuf ld_posof;  // triggering model: in-CSR position of every out-CSR edge
 
     // forward cascades (spread.cu): G as out-records {in-CSR position, destination},
     // built from G^T on first use; per-block visited bitmaps (kept all-zero between
@@ -221,6 +226,12 @@ int tim_radix_sort_triples(tim_ctx* ctx, uint32_t* keys, uint32_t* va, uint32_t*
 // graph.cu
 int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
                     const int32_t* d_dst, const float* d_w, int model);
+// Triggering options on the graph just built (model TIM_TRIG): cumulative thresholds and
+// in-CSR positions (ascending within each option) into the context (node_opt, opt_off,
+// opt_pos already hold the offsets and room for the n_ent positions).
+int tim_trig_build(tim_ctx* ctx, const int32_t* d_out_dst, const uint64_t* d_node_opt,
+                   const float* d_opt_prob, uint64_t n_opts, const uint64_t* d_opt_off,
+                   const int64_t* d_opt_edges, uint64_t n_ent);
 
 // sample.cu
 enum : int { SAMPLE_EMIT = 1, SAMPLE_KAPPA = 2, SAMPLE_COVER = 4 };

@@ -25,13 +25,14 @@ __global__ void check_rowptr_kernel(const int64_t* __restrict__ rowptr, int64_t 
     }
 }
 
-// Sort input per out-CSR edge e: key = destination, a = source, b = the weight's bits.
+// Sort input per out-CSR edge e: key = destination, a = source, b = the weight's bits
+// (the triggering model, which has no per-edge weight: the edge id e).
 // Destinations are checked here; one warp per source node u writes the source of its
 // out-edges (the offsets are checked by check_rowptr_kernel only at the end of the load,
 // so they are clamped to [0, m) here: an invalid graph is rejected and its sources are
 // never used).
 __global__ void edges_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ dst,
-                             const float* __restrict__ w, int64_t n, int64_t m,
+                             const float* __restrict__ w, int64_t n, int64_t m,  // w null: ids
                              uint32_t* __restrict__ keys, uint32_t* __restrict__ srcs,
                              uint32_t* __restrict__ wbits, int* __restrict__ err) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
@@ -42,7 +43,7 @@ __global__ void edges_kernel(const int64_t* __restrict__ rowptr, const int32_t* 
             v = 0;
         }
         keys[e] = (uint32_t)v;
-        wbits[e] = __float_as_uint(w[e]);
+        wbits[e] = w ? __float_as_uint(w[e]) : (uint32_t)e;
     }
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -68,10 +69,6 @@ __global__ void rowptr_from_keys_kernel(const uint32_t* __restrict__ keys, int64
     }
 }
 
-#ifdef GRAPH_DEBUG
-__device__ unsigned long long graph_debug_first[4] = {~0ull, 0, 0, 0};
-#endif
-
 // Per in-edge (sorted position): its source, the self-loop and weight checks, and the
 // model's threshold from the weight carried through the sort.
 __global__ void fill_in_edges_kernel(const uint32_t* __restrict__ sorted_dst,
@@ -80,7 +77,7 @@ __global__ void fill_in_edges_kernel(const uint32_t* __restrict__ sorted_dst,
                                      int64_t m, int model, uint32_t* __restrict__ src,
                                      uint32_t* __restrict__ thr,
                                      unsigned long long* __restrict__ lt_t,
-                                     int* __restrict__ err) {
+                                     uint32_t* __restrict__ posof, int* __restrict__ err) {
     for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < m;
          pos += (int64_t)gridDim.x * blockDim.x) {
         const uint32_t v = sorted_dst[pos];
@@ -91,16 +88,14 @@ __global__ void fill_in_edges_kernel(const uint32_t* __restrict__ sorted_dst,
         }
         if (u == v) atomicOr(err, TIM_DEV_ERR_GRAPH);
         src[pos] = u;
+        if (model == TIM_TRIG) {  // no weight; record where out-edge e landed
+            thr[pos] = 0u;
+            posof[sorted_wbits[pos]] = (uint32_t)pos;
+            continue;
+        }
         float p = __uint_as_float(sorted_wbits[pos]);
         if (!(p >= 0.0f && p <= 1.0f)) {
             atomicOr(err, TIM_DEV_ERR_WEIGHT);
-#ifdef GRAPH_DEBUG
-            if (atomicCAS(&graph_debug_first[0], ~0ull, (unsigned long long)pos) == ~0ull) {
-                graph_debug_first[1] = sorted_wbits[pos];
-                graph_debug_first[2] = u;
-                graph_debug_first[3] = v;
-            }
-#endif
             p = 0.0f;
         }
         double scaled = (double)p * 4294967296.0;  // exact: float -> double, times 2^32
@@ -171,6 +166,8 @@ __global__ void node_thr_kernel(const uint64_t* __restrict__ rowptr, int64_t n, 
         if (model == TIM_IC) {
             const uint32_t t0 = b > a ? thr[a] : 0u;
             node_thr[v] = (unsigned long long)t0 | (nonuni[v] ? 0ull : (1ull << 32));
+        } else if (model == TIM_TRIG) {
+            node_thr[v] = 0ull;
         } else {
             const unsigned long long t0 = b > a ? lt_t[a] : 0ull;
             const bool same = b > a && !nonuni[v] && t0 <= 0xFFFFFFFFull;
@@ -201,13 +198,123 @@ __global__ void skip_tables_kernel(const uint64_t* __restrict__ rowptr, int64_t 
     }
 }
 
+// Triggering model, per node v: the inclusive cumulative threshold of each of its
+// options (floor(p * 2^32) summed in option order, saturated at 2^32 - 1), the node of
+// each option, and the checks p in [0, 1] and sum p <= 1 + 1e-5.
+__global__ void trig_node_kernel(const uint64_t* __restrict__ node_opt, int64_t n,
+                                 const float* __restrict__ opt_prob,
+                                 uint32_t* __restrict__ opt_cum, uint32_t* __restrict__ opt_node,
+                                 int* __restrict__ err) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        double tot = 0.0;
+        unsigned long long acc = 0;
+        for (uint64_t o = node_opt[v]; o < node_opt[v + 1]; o++) {
+            const float p = opt_prob[o];
+            if (!(p >= 0.0f && p <= 1.0f)) {
+                atomicOr(err, TIM_DEV_ERR_WEIGHT);
+                continue;
+            }
+            tot += (double)p;
+            acc += (unsigned long long)((double)p * 4294967296.0);  // floor: p >= 0
+            opt_cum[o] = acc > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)acc;
+            opt_node[o] = (uint32_t)v;
+        }
+        if (tot > 1.0 + 1e-5) atomicOr(err, TIM_DEV_ERR_WEIGHT);
+    }
+}
+
+// Triggering model, per option o: the in-CSR positions of its out-CSR edge ids, each of
+// which must end in the option's node, and the option of every entry (the sort key that
+// groups the entries again after they are sorted by position).
+__global__ void trig_pos_kernel(uint64_t n_opts, const uint64_t* __restrict__ opt_off,
+                                const int64_t* __restrict__ opt_edges,
+                                const uint32_t* __restrict__ opt_node,
+                                const int32_t* __restrict__ out_dst, int64_t m,
+                                const uint32_t* __restrict__ posof,
+                                uint32_t* __restrict__ opt_pos, uint32_t* __restrict__ opt_of,
+                                int* __restrict__ err) {
+    for (uint64_t o = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; o < n_opts;
+         o += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = opt_node[o];
+        for (uint64_t i = opt_off[o]; i < opt_off[o + 1]; i++) {
+            const int64_t e = opt_edges[i];
+            opt_of[i] = (uint32_t)o;
+            if (e < 0 || e >= m || (uint32_t)out_dst[e] != v) {
+                atomicOr(err, TIM_DEV_ERR_GRAPH);
+                opt_pos[i] = 0u;
+                continue;
+            }
+            opt_pos[i] = posof[e];
+        }
+    }
+}
+
+int bit_length(uint64_t x) {
+    int b = 0;
+    while (x) {
+        b++;
+        x >>= 1;
+    }
+    return b;
+}
+
 }  // namespace
+
+int tim_trig_build(tim_ctx* ctx, const int32_t* d_out_dst, const uint64_t* d_node_opt,
+                   const float* d_opt_prob, uint64_t n_opts, const uint64_t* d_opt_off,
+                   const int64_t* d_opt_edges, uint64_t n_ent) {
+    const int64_t n = ctx->n, m = ctx->m;
+    TIM_TRY(tim_zero_scalars(ctx));
+    DevScalars* ds = tim_dscal(ctx);
+    TIM_TRY(tim_ensure(ctx, ctx->opt_cum, (n_opts + 1) * sizeof(uint32_t)));
+    TIM_TRY(tim_ensure(ctx, ctx->opt_node, (n_opts + 1) * sizeof(uint32_t)));
+    const unsigned G = (unsigned)(ctx->num_sms * 8);
+    trig_node_kernel<<<G, 256, 0, ctx->stream>>>(d_node_opt, n, d_opt_prob,
+                                                 (uint32_t*)ctx->opt_cum.p,
+                                                 (uint32_t*)ctx->opt_node.p, &ds->err);
+    LAUNCH_CHECK(ctx, "trig_node_kernel");
+    if (n_opts) {
+        DevBuf of, pad;
+        int rc = tim_ensure(ctx, of, (n_ent + 1) * sizeof(uint32_t));
+        if (rc == TIM_OK) rc = tim_ensure(ctx, pad, (n_ent + 1) * sizeof(uint32_t));
+        if (rc == TIM_OK) {
+            trig_pos_kernel<<<G, 256, 0, ctx->stream>>>(
+                n_opts, d_opt_off, d_opt_edges, (const uint32_t*)ctx->opt_node.p, d_out_dst, m,
+                (const uint32_t*)ctx->ld_posof.p, (uint32_t*)ctx->opt_pos.p, (uint32_t*)of.p,
+                &ds->err);
+            rc = tim_cuda_check(ctx, cudaGetLastError(), "trig_pos_kernel");
+            ctx->launches++;
+        }
+        // each option's positions ascending (by position, then stably by option): the
+        // forward cascades test an in-edge's membership by binary search; the RR walk
+        // does not depend on the order
+        if (rc == TIM_OK)
+            rc = tim_radix_sort_triples(ctx, (uint32_t*)ctx->opt_pos.p, (uint32_t*)of.p,
+                                        (uint32_t*)pad.p, n_ent, bit_length((uint64_t)m));
+        if (rc == TIM_OK)
+            rc = tim_radix_sort_triples(ctx, (uint32_t*)of.p, (uint32_t*)ctx->opt_pos.p,
+                                        (uint32_t*)pad.p, n_ent, bit_length(n_opts));
+        if (rc == TIM_OK) rc = tim_cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sort");
+        tim_free(of);
+        tim_free(pad);
+        TIM_TRY(rc);
+    }
+    TIM_TRY(tim_read_scalars(ctx));
+    if (ctx->h_scal->err & TIM_DEV_ERR_WEIGHT)
+        return tim_fail(ctx, TIM_ERR_ARG, "invalid triggering probabilities");
+    if (ctx->h_scal->err)
+        return tim_fail(ctx, TIM_ERR_ARG, "a triggering option lists an edge that does not end "
+                                          "in its node");
+    return TIM_OK;
+}
 
 int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
                     const int32_t* d_dst, const float* d_w, int model) {
     if (n < 2 || n > 0x7FFFFFFFll || m < 0 || m > 0xFFFFFFF0ll)
         return tim_fail(ctx, TIM_ERR_ARG, "n must be in [2, 2^31) and m in [0, 2^32 - 16)");
-    if (model != TIM_IC && model != TIM_LT) return tim_fail(ctx, TIM_ERR_ARG, "unknown model");
+    if (model != TIM_IC && model != TIM_LT && model != TIM_TRIG)
+        return tim_fail(ctx, TIM_ERR_ARG, "unknown model");
     ctx->have_graph = false;
     ctx->have_kpt = false;
     ctx->select_open = false;
@@ -255,10 +362,13 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
             rowptr_from_keys_kernel<<<G, T, 0, ctx->stream>>>((const uint32_t*)keys.p, n, m,
                                                               (uint64_t*)ctx->rowptr.p);
             ctx->launches++;
+            if (model == TIM_TRIG &&
+                (rc = tim_ensure(ctx, ctx->ld_posof, (size_t)(m + 1) * sizeof(uint32_t))))
+                break;
             fill_in_edges_kernel<<<G, T, 0, ctx->stream>>>(
                 (const uint32_t*)keys.p, (const uint32_t*)srcs.p, (const uint32_t*)wbits.p, n, m,
                 model, (uint32_t*)ctx->src.p, (uint32_t*)ctx->thr.p, (unsigned long long*)lt_t.p,
-                &ds->err);
+                (uint32_t*)ctx->ld_posof.p, &ds->err);
             ctx->launches++;
             check_dups_kernel<<<G, T, 0, ctx->stream>>>((const uint32_t*)keys.p,
                                                         (const uint32_t*)ctx->src.p, m, &ds->err);
@@ -283,7 +393,7 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
                 (const unsigned long long*)lt_t.p, (const uint64_t*)lt_e.p, (uint32_t*)ctx->thr.p,
                 (uint8_t*)nonuni.p, &ds->err);
             ctx->launches++;
-        } else if (m > 0) {
+        } else if (m > 0 && model == TIM_IC) {
             ic_nonuniform_kernel<<<G, T, 0, ctx->stream>>>(
                 (const uint64_t*)ctx->rowptr.p, (const uint32_t*)keys.p, m,
                 (const uint32_t*)ctx->thr.p, (uint8_t*)nonuni.p);
@@ -334,10 +444,3 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
     return TIM_OK;
 }
 
-#ifdef GRAPH_DEBUG
-extern "C" int tim_debug_graph_first(unsigned long long* out) {
-    return cudaMemcpyFromSymbol(out, graph_debug_first, sizeof graph_debug_first) == cudaSuccess
-               ? 0
-               : -1;
-}
-#endif

@@ -21,7 +21,8 @@
 // In-lists of at least BIG_GROUPS groups (hubs) are streamed by the whole team one at
 // a time with two groups in flight per lane; the rest of a frontier is flattened.
 // Tier 3: sets beyond tier 2's queue: IC goes to the batched level-synchronous pass of
-//   sample_bulk.cu; LT (a chain) is walked by one warp per set with a visited bitmap.
+//   sample_bulk.cu; LT (a chain) is walked by one warp per set with a visited bitmap; a
+//   general triggering model's set is expanded level by level by one block per set.
 //
 // Per set the kernels can (flags): EMIT the members into the RR-set store, sum KAPPA
 // (Eq. 6) in 2^-63 fixed point, and test COVER (does the set meet a given seed set;
@@ -80,6 +81,11 @@ struct SampleArgs {
     unsigned long long width_budget2; // tier 2 IC: in-edges one team may examine per set
     int chunk;                        // sets claimed per work-counter increment
     uint32_t* lt_col;                 // tier 1 LT: per-thread member columns
+    // triggering model: options of each node, their cumulative thresholds, their in-edges
+    const uint64_t* node_opt;
+    const uint32_t* opt_cum;
+    const uint64_t* opt_off;
+    const uint32_t* opt_pos;
 };
 
 __device__ __forceinline__ uint4 draw(const SampleArgs& a, uint64_t sid, uint32_t elem,
@@ -235,7 +241,7 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
     }
     team_sync<T>(team);
     unsigned long long width = 0, live = 0, work = 0, exam = 0;
-    if (MODEL == TIM_IC) {
+    if constexpr (MODEL == TIM_IC) {
         const uint32_t s0 = (uint32_t)sid, s1 = (uint32_t)(sid >> 32);
         const uint4* thr4 = reinterpret_cast<const uint4*>(a.thr);
         int head = 0;
@@ -399,6 +405,77 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                     if (m) flags |= follow_live<C, A>(a, g, m, hash, queue, slot, ctl);
                     flags = __reduce_or_sync(0xffffffffu, flags);
                 }
+            }
+            team_sync<T>(team);
+            head += nb;
+        }
+    } else if constexpr (MODEL == TIM_TRIG) {
+        // a general triggering model (Section 4.2): every reached node picks one option
+        // with the LT draw (the first whose cumulative threshold exceeds it) and the
+        // option's in-edges are followed, flattened over the lanes
+        const uint32_t s0 = (uint32_t)sid, s1 = (uint32_t)(sid >> 32);
+        int head = 0;
+        for (int guard = 0; guard < C::Q + 1; guard++) {
+            int tail, stat;
+            if (T == 1) {
+                tail = __shfl_sync(0xffffffffu, vctl[0], 0);
+                stat = __shfl_sync(0xffffffffu, vctl[1], 0);
+            } else {
+                tail = vctl[0];
+                stat = vctl[1];
+                team_sync<T>(team);
+            }
+            if (stat || head >= tail) break;
+            const int nb = min(32, tail - head);
+            uint64_t beg = 0, end = 0, ob = 0, oe = 0;
+            if (lane < nb) {
+                const uint32_t v = queue[head + lane];
+                beg = __ldg(a.rowptr + v);
+                end = __ldg(a.rowptr + v + 1);
+                const uint64_t o0 = __ldg(a.node_opt + v), o1 = __ldg(a.node_opt + v + 1);
+                if (o1 > o0) {
+                    const uint32_t x = philox4x32_10(s0, s1, v, TIM_TAG_LT, K).x;
+                    const uint64_t o = lane_lt_search(a.opt_cum, o0, o1, x);
+                    if (o < o1) {
+                        ob = __ldg(a.opt_off + o);
+                        oe = __ldg(a.opt_off + o + 1);
+                    }
+                }
+            }
+            width += __reduce_add_sync(0xffffffffu, (unsigned)(end - beg));
+            const uint32_t ne = (uint32_t)(oe - ob);
+            uint32_t incl = ne;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+            const uint32_t excl = incl - ne;
+            if (wt == 0 && lane == 0) exam += total;
+            int flags = 0;
+            for (uint32_t base = wt * 32; base < total && !(flags & 3); base += 32 * T) {
+                const uint32_t t = base + lane;
+                int own = 0;  // number of lanes whose inclusive count is <= t
+#pragma unroll
+                for (int sft = 16; sft > 0; sft >>= 1) {
+                    const uint32_t ic = __shfl_sync(0xffffffffu, incl, own + sft - 1);
+                    if (ic <= t) own += sft;
+                }
+                const uint64_t o_b = __shfl_sync(0xffffffffu, ob, own);
+                const uint32_t o_x = __shfl_sync(0xffffffffu, excl, own);
+                if (t < total) {
+                    live++;
+                    const uint32_t u = __ldg(a.src + __ldg(a.opt_pos + o_b + (t - o_x)));
+                    const int r = set_insert<C>(hash, queue, slot, ctl, u);
+                    if (r == INS_FULL) {
+                        flags |= 1;
+                    } else if (r == INS_NEW && cover && marked(a.seed_mark, u)) {
+                        atomicOr(&ctl[1], ST_COVERED);
+                        flags |= 2;
+                    }
+                }
+                flags = __reduce_or_sync(0xffffffffu, flags);
             }
             team_sync<T>(team);
             head += nb;
@@ -916,6 +993,162 @@ __global__ void __launch_bounds__(BIG_THREADS) rr_lt_chain_kernel(SampleArgs a) 
     }
 }
 
+// ------------------------------------------------- tier 3 (triggering model)
+
+// One CTA per listed set, level-synchronous: the warps claim 32 queued nodes of the
+// current level at a time, each lane draws its node's option, and the options' in-edges
+// are flattened over the lanes; a new member sets its bit in the slot's visited bitmap
+// (n bits) and takes the next entry of the slot's queue (n entries). A level ends when
+// every warp has drained it; the set ends at an empty level (or, COVER, at the first
+// member in the seed set).
+__global__ void __launch_bounds__(BIG_THREADS) rr_trig_big_kernel(SampleArgs a) {
+    __shared__ unsigned long long s_j, s_base;
+    __shared__ unsigned long long s_width[BIG_THREADS / 32];
+    __shared__ unsigned s_head, s_tail;
+    __shared__ int s_status;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    uint32_t* bitmap = a.big_bitmap + (uint64_t)blockIdx.x * a.big_words;
+    uint32_t* queue = a.big_queue + (uint64_t)blockIdx.x * a.n;
+    const bool emit = a.flags & SAMPLE_EMIT, kap = a.flags & SAMPLE_KAPPA,
+               cover = a.flags & SAMPLE_COVER;
+    volatile int* vstatus = &s_status;
+    unsigned long long k_lo = 0, k_hi = 0, wsum = 0, cov = 0, live = 0, memb = 0;
+    const unsigned nlist = min(((volatile unsigned*)&a.ds->cnt2)[0], a.list_cap);
+    for (;;) {
+        if (tid == 0) s_j = atomicAdd(&a.ds->next3, 1ull);
+        __syncthreads();
+        const unsigned long long idx = s_j;
+        if (idx >= nlist) break;
+        const uint64_t j = a.list2[idx];
+        const uint64_t sid = a.sid0 + j;
+        const uint32_t s0 = (uint32_t)sid, s1 = (uint32_t)(sid >> 32);
+        const uint32_t root = rr_root(sid, a.n, a.K);
+        if (tid == 0) {
+            atomicOr(&bitmap[root >> 5], 1u << (root & 31));
+            queue[0] = root;
+            s_tail = 1;
+            s_head = 0;
+            s_status = (cover && marked(a.seed_mark, root)) ? ST_COVERED : 0;
+        }
+        __syncthreads();
+        unsigned long long width = 0;
+        unsigned lvl_end = 1;
+        // at most n levels: every level but the last adds a member
+        for (uint64_t level = 0; level <= a.n; level++) {
+            for (;;) {
+                unsigned h0 = 0;
+                if (lane == 0) h0 = atomicAdd(&s_head, 32u);
+                h0 = __shfl_sync(0xffffffffu, h0, 0);
+                if (h0 >= lvl_end || *vstatus) break;
+                const unsigned nb = min(32u, lvl_end - h0);
+                uint64_t beg = 0, end = 0, ob = 0, oe = 0;
+                if (lane < nb) {
+                    const uint32_t v = queue[h0 + lane];
+                    beg = __ldg(a.rowptr + v);
+                    end = __ldg(a.rowptr + v + 1);
+                    const uint64_t o0 = __ldg(a.node_opt + v), o1 = __ldg(a.node_opt + v + 1);
+                    if (o1 > o0) {
+                        const uint32_t x = draw(a, sid, v, TIM_TAG_LT).x;
+                        const uint64_t o = lane_lt_search(a.opt_cum, o0, o1, x);
+                        if (o < o1) {
+                            ob = __ldg(a.opt_off + o);
+                            oe = __ldg(a.opt_off + o + 1);
+                        }
+                    }
+                }
+                width += __reduce_add_sync(0xffffffffu, (unsigned)(end - beg));
+                const uint32_t ne = (uint32_t)(oe - ob);
+                uint32_t incl = ne;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+                const uint32_t excl = incl - ne;
+                for (uint32_t base = 0; base < total; base += 32) {
+                    const uint32_t t = base + lane;
+                    int own = 0;
+#pragma unroll
+                    for (int sft = 16; sft > 0; sft >>= 1) {
+                        const uint32_t ic = __shfl_sync(0xffffffffu, incl, own + sft - 1);
+                        if (ic <= t) own += sft;
+                    }
+                    const uint64_t o_b = __shfl_sync(0xffffffffu, ob, own);
+                    const uint32_t o_x = __shfl_sync(0xffffffffu, excl, own);
+                    if (t < total) {
+                        live++;
+                        const uint32_t u = __ldg(a.src + __ldg(a.opt_pos + o_b + (t - o_x)));
+                        const uint32_t bit = 1u << (u & 31);
+                        if (!(atomicOr(&bitmap[u >> 5], bit) & bit)) {
+                            queue[atomicAdd(&s_tail, 1u)] = u;
+                            if (cover && marked(a.seed_mark, u)) atomicOr(&s_status, ST_COVERED);
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+            const unsigned next_end = s_tail;
+            const bool done = s_status || next_end == lvl_end;
+            __syncthreads();  // every thread has read s_tail and s_status
+            if (done) break;
+            if (tid == 0) s_head = lvl_end;
+            lvl_end = next_end;
+            __syncthreads();
+        }
+        if (lane == 0) s_width[wid] = width;
+        __syncthreads();
+        const unsigned tail = s_tail;
+        if (tid == 0) {
+            width = 0;
+            for (int w = 0; w < BIG_THREADS / 32; w++) width += s_width[w];
+            s_width[0] = width;
+            wsum += width;
+            memb += tail;
+            if (s_status & ST_COVERED) cov++;
+            if (kap) {
+                const unsigned long long kf = kappa_fixed(kappa_fp64(width, a.m, a.k));
+                k_lo += kf;
+                if (k_lo < kf) k_hi++;
+            }
+            if (emit) s_base = atomicAdd(&a.ds->pool_used, (unsigned long long)tail);
+        }
+        __syncthreads();
+        if (emit) {
+            const unsigned long long base = s_base;
+            if (base + tail <= a.pool_cap) {
+                for (unsigned i = tid; i < tail; i += BIG_THREADS) {
+                    a.pool[base + i] = queue[i];
+                    a.pool_sid[base + i] = (uint32_t)j;
+                }
+                if (tid == 0) {
+                    a.set_start[j] = base;
+                    a.set_len[j] = tail;
+                    a.set_width[j] = s_width[0];
+                }
+            } else if (tid == 0) {
+                atomicOr(&a.ds->err, TIM_DEV_ERR_POOL);
+            }
+        }
+        for (unsigned i = tid; i < tail; i += BIG_THREADS) {
+            const uint32_t u = queue[i];
+            atomicAnd(&bitmap[u >> 5], ~(1u << (u & 31)));
+        }
+        __syncthreads();
+    }
+    live = warp_sum_u64(live);
+    if (lane == 0 && live) atomicAdd(&a.ds->live[2], live);
+    if (tid == 0) {
+        if (kap && (k_lo || k_hi)) atomic_add_u128(&a.ds->ksum_lo, &a.ds->ksum_hi, k_lo, k_hi);
+        if (wsum) {
+            atomicAdd(&a.ds->wsum, wsum);
+            atomicAdd(&a.ds->width[2], wsum);
+        }
+        if (cov) atomicAdd(&a.ds->covered, cov);
+        if (memb) atomicAdd(&a.ds->memb[2], memb);
+    }
+}
+
 template <int MODEL, class C, int TIER, int T>
 int occupancy(size_t smem) {
     int nb = 0;
@@ -934,6 +1167,9 @@ int launch_tier1(tim_ctx* ctx, const SampleArgs& a, unsigned grid, size_t smem) 
     if (ctx->model == TIM_IC) {
         rr_team_kernel<TIM_IC, Tier1, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
         LAUNCH_CHECK(ctx, "rr_team_kernel (tier 1)");
+    } else if (ctx->model == TIM_TRIG) {
+        rr_team_kernel<TIM_TRIG, Tier1, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
+        LAUNCH_CHECK(ctx, "rr_team_kernel (tier 1, triggering)");
     } else {
         int nb = 0;
         CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, rr_lt_lane_kernel,
@@ -950,9 +1186,11 @@ int launch_tier1(tim_ctx* ctx, const SampleArgs& a, unsigned grid, size_t smem) 
 }
 
 int launch_tier2(tim_ctx* ctx, const SampleArgs& a, unsigned grid, int T) {
-    if (ctx->model == TIM_LT || T == 1) {
+    if (ctx->model != TIM_IC || T == 1) {
         if (ctx->model == TIM_IC)
             rr_team_kernel<TIM_IC, Tier2, 2, 1><<<grid, WARPS * 32, 0, ctx->stream>>>(a);
+        else if (ctx->model == TIM_TRIG)
+            rr_team_kernel<TIM_TRIG, Tier2, 2, 1><<<grid, WARPS * 32, 0, ctx->stream>>>(a);
         else
             rr_team_kernel<TIM_LT, Tier2, 2, 1><<<grid, WARPS * 32, 0, ctx->stream>>>(a);
     } else if (T == 2) {
@@ -1440,10 +1678,12 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
 
     // tier 2 arena: one slot per resident warp, hash regions kept EMPTY between sets
     const size_t smem1 = (size_t)WARPS * Tier1::WORDS * sizeof(uint32_t);
-    const int nb1 = ctx->model == TIM_IC ? occupancy<TIM_IC, Tier1, 1, 1>(smem1)
-                                         : occupancy<TIM_LT, Tier1, 1, 1>(smem1);
-    const int nb2 = ctx->model == TIM_IC ? occupancy<TIM_IC, Tier2, 2, 1>(0)
-                                         : occupancy<TIM_LT, Tier2, 2, 1>(0);
+    const int nb1 = ctx->model == TIM_IC     ? occupancy<TIM_IC, Tier1, 1, 1>(smem1)
+                    : ctx->model == TIM_TRIG ? occupancy<TIM_TRIG, Tier1, 1, 1>(smem1)
+                                             : occupancy<TIM_LT, Tier1, 1, 1>(smem1);
+    const int nb2 = ctx->model == TIM_IC     ? occupancy<TIM_IC, Tier2, 2, 1>(0)
+                    : ctx->model == TIM_TRIG ? occupancy<TIM_TRIG, Tier2, 2, 1>(0)
+                                             : occupancy<TIM_LT, Tier2, 2, 1>(0);
     const unsigned grid1 = (unsigned)(ctx->num_sms * nb1);
     const unsigned grid2 = (unsigned)(ctx->num_sms * nb2);
     const size_t arena_bytes = (size_t)grid2 * WARPS * Tier2::WORDS * sizeof(uint32_t);
@@ -1453,10 +1693,11 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->arena.p, 0xFF, ctx->arena.bytes, ctx->stream));
         ctx->arena_clean = true;
     }
-    // tier 3 LT slots: a bitmap of n bits and a queue of n entries each, at most ~2 GiB
+    // tier 3 LT and triggering slots: a bitmap of n bits and a queue of n entries each,
+    // at most ~2 GiB
     const uint64_t words = (uint64_t)(ctx->n + 31) / 32 + 1;
     int slots = 0;
-    if (ctx->model == TIM_LT) {
+    if (ctx->model != TIM_IC) {
         const uint64_t per_slot = (words + (uint64_t)ctx->n) * sizeof(uint32_t);
         slots = ctx->num_sms;
         const uint64_t budget = 2ull << 30;
@@ -1499,6 +1740,10 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
     a.width_budget = ctx->width_budget;
     a.width_budget2 = ctx->width_budget2;
     a.chunk = std::max(1, ctx->chunk);
+    a.node_opt = (const uint64_t*)ctx->node_opt.p;
+    a.opt_cum = (const uint32_t*)ctx->opt_cum.p;
+    a.opt_off = (const uint64_t*)ctx->opt_off.p;
+    a.opt_pos = (const uint32_t*)ctx->opt_pos.p;
     for (int attempt = 0; attempt < 4; attempt++) {
         a.pool = (uint32_t*)ctx->pool.p;
         a.pool_sid = (uint32_t*)ctx->pool_sid.p;
@@ -1529,6 +1774,9 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
                 const unsigned n3 = std::min(ctx->h_scal->cnt2, list_cap);
                 TIM_TRY(tim_bulk_ic(ctx, req, a.list2, n3, a.pool, a.pool_sid, a.pool_cap, a.ds,
                                     &live3));
+            } else if (ctx->model == TIM_TRIG) {
+                rr_trig_big_kernel<<<slots, BIG_THREADS, 0, ctx->stream>>>(a);
+                LAUNCH_CHECK(ctx, "rr_trig_big_kernel");
             } else {
                 rr_lt_chain_kernel<<<slots, BIG_THREADS, 0, ctx->stream>>>(a);
                 LAUNCH_CHECK(ctx, "rr_lt_chain_kernel");
@@ -1684,6 +1932,10 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
         tim_ctx* c = qs[i].ctx;
         if (!c || !c->have_graph) return tim_fail(owner, TIM_ERR_STATE, "query without a graph");
         if (c->device != owner->device) return tim_fail(owner, TIM_ERR_ARG, "queries on several devices");
+        if (c->model == TIM_TRIG)
+            return tim_fail(owner, TIM_ERR_ARG,
+                            "the multi-query sampler takes IC and LT graphs; a triggering-model "
+                            "graph runs one query at a time");
         const uint64_t count = qs[i].req.count;
         if (count > 0xFFFFFFF0ull) return tim_fail(owner, TIM_ERR_ARG, "too many RR sets in one call");
         prefix[i] = total_ic;

@@ -6,9 +6,10 @@
 // Cascade c walks the world of set id sid = first_set_id + c with the keys of the RR
 // sets: the IC in-edge at in-CSR position j is kept iff word (j & 3) of Philox(seed;
 // sid, j >> 2, TAG_IC) is below its threshold (one coin per in-edge, also in lists that
-// RR sampling treats by geometric skipping), and under LT node v keeps the in-edge that
-// word 0 of Philox(seed; sid, v, TAG_LT) picks. Where no list is skipped, the RR set of
-// sid is then exactly the set of nodes that reach its root in this cascade's world.
+// RR sampling treats by geometric skipping), under LT node v keeps the in-edge that
+// word 0 of Philox(seed; sid, v, TAG_LT) picks, and under a general triggering model the
+// in-edges of the option that the same word picks. Where no list is skipped, the RR set
+// of sid is then exactly the set of nodes that reach its root in this cascade's world.
 //
 // The walk needs G itself: out-records {in-CSR position, destination} grouped by
 // source, built from G^T on first use. One block per cascade: its visited bitmap (n
@@ -64,6 +65,11 @@ struct McArgs {
     uint64_t words;
     uint32_t* counts;              // per cascade
     unsigned long long* scal;      // [0] next cascade, [1] total activated
+    // triggering model: options per node, cumulative thresholds, sorted in-CSR positions
+    const uint64_t* node_opt;
+    const uint32_t* opt_cum;
+    const uint64_t* opt_off;
+    const uint32_t* opt_pos;
 };
 
 // Does v keep in-edge j in the world of sid (LT)?
@@ -75,6 +81,26 @@ __device__ __forceinline__ bool lt_kept(const McArgs& a, uint32_t s0, uint32_t s
     const uint64_t p = (nt >> 32) ? lt_uniform_pick(nt, beg, end, x)
                                   : lane_lt_search(a.thr, beg, end, x);
     return p == (uint64_t)j;
+}
+
+// Does v keep in-edge j in the world of sid (triggering model)? v picks its option with
+// the RR walk's draw; j is kept iff it is among the option's positions (ascending).
+__device__ __forceinline__ bool trig_kept(const McArgs& a, uint32_t s0, uint32_t s1, uint32_t v,
+                                          uint32_t j) {
+    const uint64_t o0 = __ldg(a.node_opt + v), o1 = __ldg(a.node_opt + v + 1);
+    if (o1 == o0) return false;
+    const uint32_t x = philox4x32_10(s0, s1, v, TIM_TAG_LT, a.K).x;
+    const uint64_t o = lane_lt_search(a.opt_cum, o0, o1, x);
+    if (o >= o1) return false;
+    uint64_t lo = __ldg(a.opt_off + o), hi = __ldg(a.opt_off + o + 1);
+    for (int it = 0; it < 40 && lo < hi; it++) {  // first position >= j
+        const uint64_t mid = lo + ((hi - lo) >> 1);
+        if (__ldg(a.opt_pos + mid) < j)
+            lo = mid + 1;
+        else
+            hi = mid;
+    }
+    return lo < __ldg(a.opt_off + o + 1) && __ldg(a.opt_pos + lo) == j;
 }
 
 __global__ void __launch_bounds__(MC_THREADS) mc_cascade_kernel(McArgs a) {
@@ -126,6 +152,8 @@ __global__ void __launch_bounds__(MC_THREADS) mc_cascade_kernel(McArgs a) {
                                          : (j & 3) == 2 ? x.z : x.w;
                         const uint32_t t = __ldg(a.thr + j);
                         kept = t == 0xFFFFFFFFu || w < t;
+                    } else if (a.model == TIM_TRIG) {
+                        kept = trig_kept(a, s0, s1, v, j);
                     } else {
                         kept = lt_kept(a, s0, s1, v, j);
                     }
@@ -227,6 +255,10 @@ extern "C" int tim_spread_mc(tim_ctx* ctx, const int32_t* seeds, int k, uint64_t
     a.words = words;
     a.counts = (uint32_t*)ctx->mc_counts.p;
     a.scal = (unsigned long long*)ctx->mc_scal.p;
+    a.node_opt = (const uint64_t*)ctx->node_opt.p;
+    a.opt_cum = (const uint32_t*)ctx->opt_cum.p;
+    a.opt_off = (const uint64_t*)ctx->opt_off.p;
+    a.opt_pos = (const uint32_t*)ctx->opt_pos.p;
     ctx->mc_clean = false;
     mc_cascade_kernel<<<(unsigned)slots, MC_THREADS, 0, ctx->stream>>>(a);
     LAUNCH_CHECK(ctx, "mc_cascade_kernel");

@@ -250,6 +250,17 @@ def triggering_random(g: Graph, max_options: int = 3, max_size: int = 4,
             np.array(erow, dtype=np.int64), np.array(edges, dtype=np.int64))
 
 
+def triggering_all_in(g: Graph, p: float):
+    """One option per node with in-edges: all of them, with probability p (the node's
+    in-edges are live together or not at all)."""
+    order, starts = _in_edges_by_node(g)
+    has = np.diff(starts) > 0
+    orow = np.zeros(g.n + 1, dtype=np.int64)
+    np.cumsum(has, out=orow[1:])
+    erow = np.concatenate([[0], starts[1:][has]]).astype(np.int64)
+    return orow, np.full(int(has.sum()), p, dtype=np.float32), erow, order
+
+
 # ------------------------------------------------------------ small hand graphs
 
 def star_in(n: int) -> Graph:

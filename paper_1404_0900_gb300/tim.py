@@ -14,7 +14,7 @@ import numpy as np
 
 from . import build as _build
 
-TIM_IC, TIM_LT = 0, 1
+TIM_IC, TIM_LT, TIM_TRIG = 0, 1, 2
 TIM_OK = 0
 TIM_ERR_ARG, TIM_ERR_OOM, TIM_ERR_OVERFLOW = -1, -2, -3
 TIM_ERR_TIMEOUT, TIM_ERR_CUDA, TIM_ERR_STATE = -4, -5, -6
@@ -105,6 +105,8 @@ _SIGS = {
     "tim_last_error_message": (C.c_char_p, [_P]),
     "tim_load_graph": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, C.c_int]),
     "tim_load_graph_device": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, C.c_int]),
+    "tim_load_graph_triggering": (C.c_int, [_P, C.c_int64, C.c_int64, _P, _P, _P, _P, _P,
+                                            _P]),
     "tim_get_graph": (C.c_int, [_P, _P, _P, _P]),
     "tim_sample_rr": (C.c_int, [_P, C.c_uint64, C.c_uint64, C.c_uint64, _P]),
     "tim_get_rr": (C.c_int, [_P, _P, _P, C.c_uint64, _P]),
@@ -236,6 +238,22 @@ def tim_load_graph_device(ctx, n: int, m: int, d_rowptr, d_dst, d_weight, model:
     """Device arrays: torch CUDA tensors (int64, int32, float32) or raw pointers."""
     _check(ctx, lib().tim_load_graph_device(ctx, n, m, _ptr(d_rowptr), _ptr(d_dst),
                                             _ptr(d_weight), model))
+
+
+def tim_load_graph_triggering(ctx, n: int, rowptr, dst, opt_rowptr, opt_prob, opt_edge_rowptr,
+                              opt_edges):
+    """G (out-CSR) and each node's triggering options (Section 4.2): node v's options
+    opt_rowptr[v] .. opt_rowptr[v+1], option o with probability opt_prob[o] and the out-CSR
+    edge ids opt_edges[opt_edge_rowptr[o] .. opt_edge_rowptr[o+1])."""
+    rowptr = np.ascontiguousarray(rowptr, dtype=np.int64)
+    dst = np.ascontiguousarray(dst, dtype=np.int32)
+    opt_rowptr = np.ascontiguousarray(opt_rowptr, dtype=np.int64)
+    opt_prob = np.ascontiguousarray(opt_prob, dtype=np.float32)
+    opt_edge_rowptr = np.ascontiguousarray(opt_edge_rowptr, dtype=np.int64)
+    opt_edges = np.ascontiguousarray(opt_edges, dtype=np.int64)
+    _check(ctx, lib().tim_load_graph_triggering(ctx, n, dst.shape[0], _ptr(rowptr), _ptr(dst),
+                                                _ptr(opt_rowptr), _ptr(opt_prob),
+                                                _ptr(opt_edge_rowptr), _ptr(opt_edges)))
 
 
 def tim_get_graph(ctx, n: int, m: int):

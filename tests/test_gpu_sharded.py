@@ -36,10 +36,14 @@ for name, (scale, kind, model, k, eps) in json.loads(sys.argv[1]).items():
     g = inputs.rmat(scale, seed=6)
     if kind == "tri":
         w = inputs.trivalency(g, seed=2)
-    else:
+    elif kind != "trig":
         w = inputs.weighted_cascade(g) if model == 0 else inputs.lt_inverse_indegree(g)
     with tim.Engine(0) as eng:
-        tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, model)
+        if kind == "trig":
+            tim.tim_load_graph_triggering(eng.ctx, g.n, g.rowptr, g.dst,
+                                          *inputs.triggering_random(g, seed=3))
+        else:
+            tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, model)
         seeds, frac, st = tim.tim_run_sharded(eng.ctx, k, eps, 1.0, 23, rank, world, red)
     out[name] = {"seeds": seeds.tolist(), "frac": frac,
                  **{x: st[x] for x in ("kpt_round", "kpt_star", "theta_prime",
@@ -51,7 +55,7 @@ print(json.dumps({"rank": rank, "out": out}))
 """
 
 CASES = {"wc_ic": (14, "wc", 0, 20, 0.3), "lt": (14, "wc", 1, 10, 0.5),
-         "tri_ic": (13, "tri", 0, 8, 0.5)}
+         "tri_ic": (13, "tri", 0, 8, 0.5), "triggering": (13, "trig", 2, 8, 0.5)}
 
 
 def _free_port() -> int:
@@ -79,6 +83,8 @@ def _run_ranks(world: int):
 
 def _graph(scale, kind, model):
     g = inputs.rmat(scale, seed=6)
+    if kind == "trig":
+        return g, inputs.triggering_random(g, seed=3)
     if kind == "tri":
         return g, inputs.trivalency(g, seed=2)
     return g, inputs.weighted_cascade(g) if model == O.IC else inputs.lt_inverse_indegree(g)
@@ -90,9 +96,13 @@ def test_sharded_tim_plus_equals_one_context_and_the_oracle(world):
     for name, (scale, kind, model, k, eps) in CASES.items():
         g, w = _graph(scale, kind, model)
         with tim.Engine(0) as eng:
-            tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, model)
+            if kind == "trig":
+                tim.tim_load_graph_triggering(eng.ctx, g.n, g.rowptr, g.dst, *w)
+                og = O.load_graph_triggering(g.n, g.rowptr, g.dst, *w)
+            else:
+                tim.tim_load_graph(eng.ctx, g.n, g.rowptr, g.dst, w, model)
+                og = O.load_graph(g.n, g.rowptr, g.dst, w, model)
             seeds, frac, st = tim.tim_run(eng.ctx, k, eps, 1.0, 23)
-        og = O.load_graph(g.n, g.rowptr, g.dst, w, model)
         ref = O.tim_plus(og, k, eps, 1.0, 23)
         assert np.array_equal(seeds, ref.seeds) and st["theta"] == ref.theta
         for o in outs:
