@@ -192,7 +192,8 @@ int tim_destroy(tim_ctx* ctx) {
                       &ctx->scratch_e, &ctx->scratch_f, &ctx->scal,     &ctx->bulk_bitmap,
                       &ctx->bulk_slot, &ctx->bulk_bsum, &ctx->bulk_bar,
                       &ctx->node_opt, &ctx->opt_cum, &ctx->opt_off, &ctx->opt_pos,
-                      &ctx->opt_node, &ctx->ld_posof,
+                      &ctx->opt_node, &ctx->ld_posof, &ctx->ld_in_r, &ctx->ld_in_d,
+                      &ctx->ld_in_w,
                       &ctx->bulk_F,    &ctx->bulk_M,    &ctx->bulk_ng,   &ctx->bulk_gp,
                       &ctx->bulk_scal, &ctx->batch,     &ctx->greedy_batch,
                       &ctx->out_rowptr, &ctx->out_rec,  &ctx->mc_bitmap, &ctx->mc_queue,
@@ -459,7 +460,9 @@ int tim_load_graph(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* out_rowptr
     if (!out_rowptr || (m > 0 && (!out_dst || !edge_w)) || n < 2 || m < 0)
         return tim_fail(ctx, TIM_ERR_ARG, "invalid graph arguments");
     DeviceGuard g(ctx->device);
-    DevBuf r, d, w;
+    // the device copies stay allocated for the next load (a cudaFree would also wait for
+    // the whole device); tim_destroy frees them
+    DevBuf &r = ctx->ld_in_r, &d = ctx->ld_in_d, &w = ctx->ld_in_w;
     int rc = TIM_OK;
     do {
         if ((rc = tim_ensure(ctx, r, (size_t)(n + 1) * sizeof(int64_t)))) break;
@@ -482,10 +485,8 @@ int tim_load_graph(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* out_rowptr
         rc = tim_load_graph_device(ctx, n, m, (const int64_t*)r.p, (const int32_t*)d.p,
                                    (const float*)w.p, model);
     } while (0);
+    // the host arrays may be reused as soon as the call returns
     cudaStreamSynchronize(ctx->stream);
-    tim_free(r);
-    tim_free(d);
-    tim_free(w);
     return rc;
 }
 

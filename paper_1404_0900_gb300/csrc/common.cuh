@@ -131,6 +131,7 @@ struct tim_ctx {
     // graph-load temporaries (graph.cu), kept between loads
     DevBuf ld_keys, ld_vals, ld_lt_t, ld_lt_e, ld_nonuni, ld_srcof;
     DevBuf ld_posof;  // triggering model: in-CSR position of every out-CSR edge
+    DevBuf ld_in_r, ld_in_d, ld_in_w;  // device copies of tim_load_graph's host arrays
 
     // forward cascades (spread.cu): G as out-records {in-CSR position, destination},
     // built from G^T on first use; per-block visited bitmaps (kept all-zero between
