@@ -90,6 +90,8 @@ struct tim_ctx {
     DevBuf seed_mark;  // uint32 bitmap[n/32 + 1]
     DevBuf seeds_dev;  // int32[n]
     DevBuf greedy_bar; // grid barrier of the cooperative greedy launch
+    DevBuf greedy_chunks;  // cooperative greedy: member chunks of the round's large sets
+    DevBuf greedy_nchunk;  // and their count per round
 
     // sets handed from tier 1 to tier 2 and from tier 2 to tier 3 of the sampler
     DevBuf ovf_list;    // uint32 set index

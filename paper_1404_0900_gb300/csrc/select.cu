@@ -5,10 +5,13 @@
 // the store, an exclusive scan into node offsets, and a scatter of set ids into
 // per-node lists (node -> sets).
 // Greedy round r: an argmax over the counts with a warp-shuffle reduction of the key
-// (count << 32 | ~node) so ties go to the smallest id and chosen nodes are skipped;
-// then every not-yet-covered set in the chosen node's list is marked covered and each
-// of its members loses one from its count. The chosen node is read on the device, so
-// the k rounds run without host round trips.
+// (count << 32 | ~node) so ties go to the smallest id and chosen nodes are skipped
+// (counts read four at a time, several loads in flight per thread: the scan runs at
+// DRAM speed when the counts outgrow L2); then every not-yet-covered set in the chosen
+// node's list is marked covered and each of its members loses one from its count (in
+// the cooperative launch, sets of more than COVER_CHUNK members are cut into chunks
+// that all warps share). The chosen node is read on the device, so the k rounds run
+// without host round trips.
 #include <algorithm>
 #include <vector>
 
@@ -67,16 +70,51 @@ __device__ __forceinline__ unsigned long long greedy_key(int cnt, uint32_t v) {
     return ((unsigned long long)(uint32_t)max(cnt, 0) << 32) | (unsigned long long)(~v);
 }
 
+// Best key of nodes 4q .. 4q+3 (0 for chosen nodes): counts as one 16-byte load, the
+// chosen flags as one 32-bit word.
+__device__ __forceinline__ unsigned long long quad_key(int4 c, uint32_t ch, uint64_t q) {
+    const uint32_t v = (uint32_t)(q << 2);
+    unsigned long long b = (ch & 0xFFu) ? 0ull : greedy_key(c.x, v);
+    b = max(b, (ch & 0xFF00u) ? 0ull : greedy_key(c.y, v + 1));
+    b = max(b, (ch & 0xFF0000u) ? 0ull : greedy_key(c.z, v + 2));
+    b = max(b, (ch & 0xFF000000u) ? 0ull : greedy_key(c.w, v + 3));
+    return b;
+}
+
+// Best key over the thread's share of the nodes (thread t of `stride` takes quads t,
+// t + stride, ...; four quads in flight; the last n mod 4 nodes one by one). Counts
+// and flags are read from L2 (__ldcg): other blocks change them between rounds. Both
+// arrays start 16-byte aligned (cudaMalloc).
+__device__ __forceinline__ unsigned long long slice_argmax(const int* counts,
+                                                           const uint8_t* chosen, uint64_t n,
+                                                           uint64_t t, uint64_t stride) {
+    const int4* c4 = reinterpret_cast<const int4*>(counts);
+    const uint32_t* h4 = reinterpret_cast<const uint32_t*>(chosen);
+    const uint64_t nq = n >> 2;
+    unsigned long long b = 0;
+    uint64_t q = t;
+    for (; q + 3 * stride < nq; q += 4 * stride) {
+        int4 c[4];
+        uint32_t h[4];
+#pragma unroll
+        for (int i = 0; i < 4; i++) {
+            c[i] = __ldcg(c4 + q + i * stride);
+            h[i] = __ldcg(h4 + q + i * stride);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; i++) b = max(b, quad_key(c[i], h[i], q + i * stride));
+    }
+    for (; q < nq; q += stride) b = max(b, quad_key(__ldcg(c4 + q), __ldcg(h4 + q), q));
+    for (uint64_t v = (nq << 2) + t; v < n; v += stride)
+        if (!__ldcg(chosen + v)) b = max(b, greedy_key(__ldcg(counts + v), (uint32_t)v));
+    return b;
+}
+
 __global__ void argmax_kernel(const int* __restrict__ counts, const uint8_t* __restrict__ chosen,
                               uint64_t n, unsigned long long* __restrict__ best) {
-    unsigned long long b = 0;
-    for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-         v += (uint64_t)gridDim.x * blockDim.x) {
-        if (!chosen[v]) {
-            unsigned long long key = greedy_key(counts[v], (uint32_t)v);
-            b = key > b ? key : b;
-        }
-    }
+    unsigned long long b = slice_argmax(counts, chosen, n,
+                                        blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
+                                        (uint64_t)gridDim.x * blockDim.x);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
@@ -134,9 +172,17 @@ __global__ void cover_kernel(const unsigned long long* __restrict__ best,
     if (lane == 0 && fresh) atomicAdd(ncov, fresh);
 }
 
+// Members per chunk of a large set in the cooperative greedy: a newly covered set with
+// more members is split into chunks that all warps share after the cover step (one warp
+// walking a set of 10^4 - 10^6 members would hold up the round).
+constexpr uint32_t COVER_CHUNK = 4096;
+
 // All k greedy rounds in one cooperative launch: per round an argmax over the counts
 // (every block reduces a slice, atomicMax into best[r]), a grid barrier, the cover step
-// of the chosen node (warps over its set list), and a second barrier.
+// of the chosen node (warps over its set list; a set of more than COVER_CHUNK members is
+// only marked, and its member chunks listed), a second barrier, and when chunks were
+// listed, the chunks over all warps and a third barrier. chunks holds at most
+// chunk_cap entries (set id | chunk << 32); nchunk[r] counts round r's.
 __global__ void __launch_bounds__(256)
 greedy_rounds_kernel(int* __restrict__ counts, uint8_t* __restrict__ chosen, uint64_t n,
                      const uint64_t* __restrict__ node_off, const uint32_t* __restrict__ node_sets,
@@ -144,21 +190,17 @@ greedy_rounds_kernel(int* __restrict__ counts, uint8_t* __restrict__ chosen, uin
                      const uint32_t* __restrict__ pool, uint8_t* __restrict__ covered, int k,
                      unsigned long long* __restrict__ best, int32_t* __restrict__ seeds,
                      unsigned long long* __restrict__ ncov, GridBarrier* bar, int* err,
-                     unsigned limit) {
+                     unsigned limit, unsigned long long* __restrict__ chunks,
+                     unsigned long long* __restrict__ nchunk, unsigned long long chunk_cap) {
     __shared__ unsigned long long wb[8];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const uint64_t warp = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     unsigned long long fresh = 0;
     for (int r = 0; r < k; r++) {
-        unsigned long long b = 0;
-        for (uint64_t v = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; v < n;
-             v += (uint64_t)gridDim.x * blockDim.x) {
-            if (!((volatile uint8_t*)chosen)[v]) {
-                const unsigned long long key = greedy_key(((volatile int*)counts)[v], (uint32_t)v);
-                b = key > b ? key : b;
-            }
-        }
+        unsigned long long b = slice_argmax(counts, chosen, n,
+                                            blockIdx.x * (uint64_t)blockDim.x + threadIdx.x,
+                                            (uint64_t)gridDim.x * blockDim.x);
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);
@@ -194,10 +236,43 @@ greedy_rounds_kernel(int* __restrict__ counts, uint8_t* __restrict__ chosen, uin
                 }
                 const uint64_t st = set_start[s];
                 const uint32_t len = set_len[s];
-                for (uint32_t t = lane; t < len; t += 32) atomicSub(&counts[pool[st + t]], 1);
+                if (len <= COVER_CHUNK) {
+                    for (uint32_t t = lane; t < len; t += 32) atomicSub(&counts[pool[st + t]], 1);
+                } else {
+                    const uint32_t nc = (len + COVER_CHUNK - 1) / COVER_CHUNK;
+                    unsigned long long base = 0;
+                    if (lane == 0) base = atomicAdd(nchunk + r, (unsigned long long)nc);
+                    base = __shfl_sync(0xffffffffu, base, 0);
+                    for (uint32_t c = lane; c < nc; c += 32) {
+                        if (base + c < chunk_cap)
+                            chunks[base + c] = (unsigned long long)s | ((unsigned long long)c << 32);
+                        else
+                            atomicOr(err, TIM_DEV_ERR_BOUNDS);
+                    }
+                }
             }
         }
         if (!grid_barrier(bar, err, limit)) return;
+        // the large sets' member chunks, over all warps, eight loads in flight per lane
+        const unsigned long long nc = min(((volatile unsigned long long*)nchunk)[r], chunk_cap);
+        if (nc) {
+            for (uint64_t w = warp; w < nc; w += nwarps) {
+                const unsigned long long e = chunks[w];
+                const uint32_t s = (uint32_t)e, c = (uint32_t)(e >> 32);
+                const uint64_t st = set_start[s] + (uint64_t)c * COVER_CHUNK;
+                const uint32_t len = min(COVER_CHUNK, set_len[s] - c * COVER_CHUNK);
+                for (uint32_t t = lane; t < len; t += 256) {
+                    uint32_t u[8];
+#pragma unroll
+                    for (int q = 0; q < 8; q++)
+                        u[q] = t + 32u * q < len ? __ldg(pool + st + t + 32u * q) : 0u;
+#pragma unroll
+                    for (int q = 0; q < 8; q++)
+                        if (t + 32u * q < len) atomicSub(&counts[u[q]], 1);
+                }
+            }
+            if (!grid_barrier(bar, err, limit)) return;
+        }
     }
     if (lane == 0 && fresh) atomicAdd(ncov, fresh);
 }
@@ -252,6 +327,14 @@ int tim_greedy(tim_ctx* ctx, int k, int32_t* host_seeds, uint64_t* covered) {
         nb > 0) {
         TIM_TRY(tim_ensure(ctx, ctx->greedy_bar, sizeof(GridBarrier)));
         CUDA_TRY(ctx, cudaMemsetAsync(ctx->greedy_bar.p, 0, sizeof(GridBarrier), ctx->stream));
+        // every covered set is listed at most once, in ceil(len / COVER_CHUNK) chunks
+        unsigned long long chunk_cap = ctx->n_sets + ctx->members / COVER_CHUNK + 1;
+        TIM_TRY(tim_ensure(ctx, ctx->greedy_chunks, chunk_cap * sizeof(unsigned long long)));
+        TIM_TRY(tim_ensure(ctx, ctx->greedy_nchunk, (size_t)k * sizeof(unsigned long long)));
+        CUDA_TRY(ctx, cudaMemsetAsync(ctx->greedy_nchunk.p, 0, (size_t)k * sizeof(unsigned long long),
+                                      ctx->stream));
+        auto* d_chunks = (unsigned long long*)ctx->greedy_chunks.p;
+        auto* d_nchunk = (unsigned long long*)ctx->greedy_nchunk.p;
         const unsigned grid = (unsigned)(ctx->num_sms * std::min(nb, 4));
         int* d_counts = (int*)ctx->counts.p;
         uint8_t* d_chosen = (uint8_t*)ctx->chosen.p;
@@ -269,7 +352,8 @@ int tim_greedy(tim_ctx* ctx, int k, int32_t* host_seeds, uint64_t* covered) {
         int* d_err = &ds->err;
         unsigned limit = ctx->wait_limit;
         void* args[] = {&d_counts, &d_chosen, &nn, &d_off, &d_ns, &d_ss, &d_sl, &d_pool,
-                        &d_cov, &kk, &best, &d_seeds, &d_ncov, &d_bar, &d_err, &limit};
+                        &d_cov, &kk, &best, &d_seeds, &d_ncov, &d_bar, &d_err, &limit,
+                        &d_chunks, &d_nchunk, &chunk_cap};
         CUDA_TRY(ctx, cudaLaunchCooperativeKernel((const void*)greedy_rounds_kernel, dim3(grid),
                                                   dim3(256), args, 0, ctx->stream));
         LAUNCH_CHECK(ctx, "greedy_rounds_kernel");
@@ -279,6 +363,8 @@ int tim_greedy(tim_ctx* ctx, int k, int32_t* host_seeds, uint64_t* covered) {
         TIM_TRY(tim_read_scalars(ctx));
         if (ctx->h_scal->err & TIM_DEV_ERR_TIMEOUT)
             return tim_fail(ctx, TIM_ERR_TIMEOUT, "greedy grid barrier timed out");
+        if (ctx->h_scal->err)
+            return tim_fail(ctx, TIM_ERR_CUDA, "device error flags set by the greedy");
         if (covered) *covered = ctx->h_scal->covered;
         return TIM_OK;
     }
@@ -430,14 +516,9 @@ __global__ void margmax_kernel(const GreedyDesc* __restrict__ gd, const unsigned
     unsigned lb, nb;
     const GreedyDesc& d = gd[block_query(bstart, nq, &lb, &nb)];
     if (r >= d.k) return;
-    unsigned long long b = 0;
-    for (uint64_t v = lb * (uint64_t)blockDim.x + threadIdx.x; v < d.n;
-         v += (uint64_t)nb * blockDim.x) {
-        if (!d.chosen[v]) {
-            const unsigned long long key = greedy_key(d.counts[v], (uint32_t)v);
-            b = key > b ? key : b;
-        }
-    }
+    unsigned long long b = slice_argmax(d.counts, d.chosen, d.n,
+                                        lb * (uint64_t)blockDim.x + threadIdx.x,
+                                        (uint64_t)nb * blockDim.x);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long y = __shfl_xor_sync(0xffffffffu, b, o);

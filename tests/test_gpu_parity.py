@@ -194,6 +194,35 @@ def test_greedy_ties_and_k_equals_n(eng, k):
     assert np.array_equal(gs, seeds) and gcov == cov
 
 
+@pytest.mark.parametrize("p", [1.0, 0.3])
+def test_greedy_with_sets_of_many_member_chunks(eng, p):
+    # p = 1: every set is the root's whole reverse-reachable part of an R-MAT 14 graph,
+    # thousands of members, so the cooperative greedy splits the sets its first seed
+    # covers into chunks of members that all warps share; p = 0.3 mixes small and large
+    g = inputs.rmat(14, seed=3)
+    og = _load(eng, g, inputs.constant(g, p), O.IC)
+    tim.tim_sample_rr(eng.ctx, 3000, 7, O.make_sid(3, 0, 5))
+    roff, rmem, _ = O.sample(og, 7, O.make_sid(3, 0, 5), 3000)
+    assert np.diff(roff).max() > 4096
+    for k in (1, 10):
+        seeds, cov, _ = O.greedy(g.n, roff, rmem, k)
+        gs, frac, gcov = tim.tim_node_select(eng.ctx, k)
+        assert np.array_equal(gs, seeds) and gcov == cov, (p, k)
+    # after the last round the counts are the uncovered sets each node is in
+    tim.tim_select_begin(eng.ctx)
+    left = tim.tim_select_counts(eng.ctx, g.n).astype(np.int64)
+    for v in seeds:
+        tim.tim_select_take(eng.ctx, int(v))
+    after = tim.tim_select_counts(eng.ctx, g.n).astype(np.int64)
+    covered = np.zeros(3000, bool)
+    for j in range(3000):
+        covered[j] = np.isin(rmem[roff[j]:roff[j + 1]], seeds).any()
+    want = np.zeros(g.n, np.int64)
+    for j in np.nonzero(~covered)[0]:
+        want[rmem[roff[j]:roff[j + 1]]] += 1
+    assert np.array_equal(after, want) and left.sum() == rmem.shape[0]
+
+
 def _theta_equal(a, b, lam, kpt):
     if a == b:
         return True
