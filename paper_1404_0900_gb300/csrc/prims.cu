@@ -108,9 +108,11 @@ __global__ void scan_apply_kernel(const TIn* __restrict__ in, uint64_t count,
 
 // ---------------------------------------------------------------- radix sort
 
+// 8 warps x 6 rounds of 32 keys: tiles of 1536 keep the kernel at 64 registers, four
+// blocks per SM (4096-key tiles needed 127, two blocks); timed on the largest graph
 constexpr int RS_WARPS = 8;
-constexpr int RS_ROUNDS = 16;
-constexpr int RS_TILE = RS_WARPS * RS_ROUNDS * 32;  // 4096 keys per block
+constexpr int RS_ROUNDS = 6;
+constexpr int RS_TILE = RS_WARPS * RS_ROUNDS * 32;  // 1536 keys per block
 constexpr int RS_MAXBINS = 256;
 // dynamic shared memory of the scatter: the tile's keys and two value arrays in digit
 // order, per-warp digit counts, the tile's digit starts
@@ -133,7 +135,7 @@ __global__ void radix_hist_kernel(const uint32_t* __restrict__ keys, uint64_t co
         hist[(uint64_t)d * ntiles + blockIdx.x] = h[d];
 }
 
-// Stable scatter of one tile of (key, a, b): warp w owns elements [w*512, (w+1)*512) of
+// Stable scatter of one tile of (key, a, b): warp w owns elements [w*192, (w+1)*192) of
 // the tile, taken 32 at a time in order, ranked among equal digits by __match_any_sync
 // (so equal digits keep the input order). The tile is first rearranged in shared memory
 // into digit order, then written out so that consecutive threads write consecutive
@@ -145,6 +147,7 @@ radix_scatter3_kernel(const uint32_t* __restrict__ k_in, const uint32_t* __restr
                       uint64_t count, int shift, uint32_t mask, uint64_t ntiles,
                       const uint64_t* __restrict__ offsets, int* __restrict__ err) {
     extern __shared__ uint32_t rs_smem[];
+    __shared__ unsigned long long goff[RS_MAXBINS];  // the tile's output start per digit
     uint32_t* sk = rs_smem;
     uint32_t* sa = sk + RS_TILE;
     uint32_t* sb = sa + RS_TILE;
@@ -152,6 +155,9 @@ radix_scatter3_kernel(const uint32_t* __restrict__ k_in, const uint32_t* __restr
     uint32_t* dstart = run + RS_WARPS * RS_MAXBINS;  // [RS_MAXBINS]
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const uint32_t nbins = mask + 1;
+    // loaded now, read after the ranking: the write-out needs no global load per element
+    for (uint32_t d = threadIdx.x; d < nbins; d += blockDim.x)
+        goff[d] = offsets[(uint64_t)d * ntiles + blockIdx.x];
     for (int i = threadIdx.x; i < RS_WARPS * RS_MAXBINS; i += blockDim.x) run[i] = 0;
     __syncthreads();
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -215,7 +221,7 @@ radix_scatter3_kernel(const uint32_t* __restrict__ k_in, const uint32_t* __restr
     for (uint32_t i = threadIdx.x; i < n_tile; i += blockDim.x) {
         const uint32_t k = sk[i];
         const uint32_t d = (k >> shift) & mask;
-        const uint64_t pos = offsets[(uint64_t)d * ntiles + blockIdx.x] + (i - dstart[d]);
+        const uint64_t pos = goff[d] + (i - dstart[d]);
         if (i < dstart[d] || pos >= count) {  // cannot happen for a consistent tile
             atomicOr(err, TIM_DEV_ERR_BOUNDS);
             continue;
