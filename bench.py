@@ -848,6 +848,8 @@ def run_batch_compare(args, reps: int = 2):
             tim.tim_set_width_budget(e.ctx, tuning["width_budget"])
             tim.tim_set_team_size(e.ctx, tuning["team_size"])
             tim.tim_set_chunk(e.ctx, tuning["chunk"])
+            tim.tim_set_team_factor(e.ctx, tuning["team_factor"])
+            tim.tim_set_pass1_capacity(e.ctx, tuning["pass1_capacity"])
 
         def plain():
             outs = []

@@ -262,6 +262,21 @@ int tim_set_team_size(tim_ctx* ctx, int warps) {
     return TIM_OK;
 }
 
+int tim_set_team_factor(tim_ctx* ctx, int factor) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (factor < 1 || factor > 64) return tim_fail(ctx, TIM_ERR_ARG, "team factor must be in [1, 64]");
+    ctx->team_factor = factor;
+    return TIM_OK;
+}
+
+int tim_set_pass1_capacity(tim_ctx* ctx, int members) {
+    if (!ctx) return TIM_ERR_ARG;
+    if (members != 128 && members != 256 && members != 512)
+        return tim_fail(ctx, TIM_ERR_ARG, "pass-1 capacity must be 128, 256 or 512");
+    ctx->cap1 = members;
+    return TIM_OK;
+}
+
 int tim_autotune(tim_ctx* ctx, uint64_t sample_sets, uint64_t seed, tim_tuning* out) {
     if (!ctx) return TIM_ERR_ARG;
     if (!ctx->have_graph) return tim_fail(ctx, TIM_ERR_STATE, "no graph loaded");
@@ -269,14 +284,15 @@ int tim_autotune(tim_ctx* ctx, uint64_t sample_sets, uint64_t seed, tim_tuning* 
     DeviceGuard g(ctx->device);
     const uint64_t budgets_ic[] = {512, 1024, 2048, 4096, 16384};
     const uint64_t budgets_lt[] = {16384};
-    // pass-2 team size stays automatic: it is chosen per call from the number of sets
-    // handed over, which a fixed calibration size cannot stand in for
-    const int teams[] = {0};
+    // the pass-2 team size stays chosen per call from the number of sets handed over
+    // (a fixed calibration size cannot stand in for every call); what is tuned is the
+    // rule's factor, after the budget and the chunk, and then the pass-1 capacity
     const int chunks[] = {1, 2, 4};
+    const int factors[] = {1, 4, 8};
+    const int caps[] = {128, 512};
     const bool ic = ctx->model == TIM_IC;
     const uint64_t* budgets = ic ? budgets_ic : budgets_lt;
     const int nbud = ic ? 5 : 1;
-    const int nteam = 1;
     const tim_profile saved_prof = ctx->prof;
     SampleRequest req;
     req.seed = seed;
@@ -298,28 +314,56 @@ int tim_autotune(tim_ctx* ctx, uint64_t sample_sets, uint64_t seed, tim_tuning* 
     best.best_ms = 1e300;
     int trials = 0;
     double def_ms = 0.0;
+    ctx->team_size = 0;
+    ctx->team_factor = 2;
+    ctx->cap1 = 256;
+    auto trial = [&](bool* better) -> int {
+        double ms = 0.0, ms2 = 0.0;
+        TIM_TRY(run_once(&ms));   // warm: allocations settle
+        TIM_TRY(run_once(&ms2));
+        ms = std::min(ms, ms2);
+        trials++;
+        *better = ms < best.best_ms;
+        if (*better) {
+            best.best_ms = ms;
+            best.width_budget = ctx->width_budget;
+            best.team_size = 0;
+            best.chunk = ctx->chunk;
+            best.team_factor = ctx->team_factor;
+            best.pass1_capacity = ctx->cap1;
+        }
+        if (ctx->width_budget == 16384 && ctx->chunk == 2 && ctx->team_factor == 2 &&
+            ctx->cap1 == 256)
+            def_ms = ms;
+        return TIM_OK;
+    };
+    bool better = false;
+    // stage 1: pass-1 budget x sets per claim
     for (int b = 0; b < nbud; b++)
-        for (int t = 0; t < nteam; t++)
-            for (int c = 0; c < 3; c++) {
-                ctx->width_budget = budgets[b];
-                ctx->team_size = teams[t];
-                ctx->chunk = chunks[c];
-                double ms = 0.0, ms2 = 0.0;
-                TIM_TRY(run_once(&ms));   // warm: allocations settle
-                TIM_TRY(run_once(&ms2));
-                ms = std::min(ms, ms2);
-                trials++;
-                if (budgets[b] == 16384 && teams[t] == 0 && chunks[c] == 2) def_ms = ms;
-                if (ms < best.best_ms) {
-                    best.best_ms = ms;
-                    best.width_budget = budgets[b];
-                    best.team_size = teams[t];
-                    best.chunk = chunks[c];
-                }
-            }
+        for (int c = 0; c < 3; c++) {
+            ctx->width_budget = budgets[b];
+            ctx->chunk = chunks[c];
+            TIM_TRY(trial(&better));
+        }
+    if (ic) {
+        // stage 2: the team-size rule's factor, stage 3: the pass-1 capacity
+        ctx->width_budget = best.width_budget;
+        ctx->chunk = best.chunk;
+        for (int f : factors) {
+            ctx->team_factor = f;
+            TIM_TRY(trial(&better));
+        }
+        ctx->team_factor = best.team_factor;
+        for (int c : caps) {
+            ctx->cap1 = c;
+            TIM_TRY(trial(&better));
+        }
+    }
     ctx->width_budget = best.width_budget;
     ctx->team_size = best.team_size;
     ctx->chunk = best.chunk;
+    ctx->team_factor = best.team_factor;
+    ctx->cap1 = best.pass1_capacity;
     ctx->prof = saved_prof;
     ctx->have_kpt = false;
     best.trials = trials;

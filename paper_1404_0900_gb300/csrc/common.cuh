@@ -116,8 +116,12 @@ struct tim_ctx {
     // IC second pass: a team gives a set to the heavy-set pass once its examined
     // in-edges would exceed this many
     unsigned long long width_budget2 = ~0ull;
-    // IC tier 2: warps per RR set (1, 2, 4 or 8); 0 = chosen from the number of sets
+    // IC tier 2: warps per RR set (1, 2, 4 or 8); 0 = chosen from the number of sets:
+    // the smallest T with listed * team_factor >= resident warps / T (at most 8)
     int team_size = 0;
+    int team_factor = 2;
+    // IC tier 1: queue capacity of one warp's set (128, 256 or 512 members)
+    int cap1 = 256;
     // sets claimed per work-counter increment in tiers 1 and 2
     int chunk = 2;
     // set-id tag of this context's runs: ids are (phase << 56) | (round << 48) |

@@ -50,6 +50,9 @@ struct Cap {
     static constexpr int WORDS = (1 << LG) + QQ + QQ / 2 + 4;
 };
 using Tier1 = Cap<256, 9>;
+// the other first-pass capacities the autotuner may choose for IC
+using Tier1S = Cap<128, 8>;
+using Tier1L = Cap<512, 10>;
 using Tier2 = Cap<8192, 14>;
 
 struct SampleArgs {
@@ -1021,7 +1024,6 @@ __global__ void __launch_bounds__(BIG_THREADS) rr_trig_big_kernel(SampleArgs a) 
         if (idx >= nlist) break;
         const uint64_t j = a.list2[idx];
         const uint64_t sid = a.sid0 + j;
-        const uint32_t s0 = (uint32_t)sid, s1 = (uint32_t)(sid >> 32);
         const uint32_t root = rr_root(sid, a.n, a.K);
         if (tid == 0) {
             atomicOr(&bitmap[root >> 5], 1u << (root & 31));
@@ -1165,7 +1167,12 @@ int occupancy(size_t smem) {
 
 int launch_tier1(tim_ctx* ctx, const SampleArgs& a, unsigned grid, size_t smem) {
     if (ctx->model == TIM_IC) {
-        rr_team_kernel<TIM_IC, Tier1, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
+        if (ctx->cap1 == 128)
+            rr_team_kernel<TIM_IC, Tier1S, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
+        else if (ctx->cap1 == 512)
+            rr_team_kernel<TIM_IC, Tier1L, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
+        else
+            rr_team_kernel<TIM_IC, Tier1, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
         LAUNCH_CHECK(ctx, "rr_team_kernel (tier 1)");
     } else if (ctx->model == TIM_TRIG) {
         rr_team_kernel<TIM_TRIG, Tier1, 1, 1><<<grid, WARPS * 32, smem, ctx->stream>>>(a);
@@ -1623,7 +1630,12 @@ rr_lt_lane_multi_kernel(MultiArgs ma, const unsigned long long* lt_prefix,
 int launch_multi(tim_ctx* owner, const MultiArgs& ma, int tier, int T, unsigned grid,
                  size_t smem) {
     if (tier == 1) {
-        rr_multi_kernel<Tier1, 1, 1><<<grid, WARPS * 32, smem, owner->stream>>>(ma);
+        if (owner->cap1 == 128)
+            rr_multi_kernel<Tier1S, 1, 1><<<grid, WARPS * 32, smem, owner->stream>>>(ma);
+        else if (owner->cap1 == 512)
+            rr_multi_kernel<Tier1L, 1, 1><<<grid, WARPS * 32, smem, owner->stream>>>(ma);
+        else
+            rr_multi_kernel<Tier1, 1, 1><<<grid, WARPS * 32, smem, owner->stream>>>(ma);
     } else if (T == 1) {
         rr_multi_kernel<Tier2, 2, 1><<<grid, WARPS * 32, 0, owner->stream>>>(ma);
     } else if (T == 2) {
@@ -1677,8 +1689,13 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
     TIM_TRY(tim_ensure(ctx, ctx->ovf_list2, (size_t)cap_sets * sizeof(uint32_t)));
 
     // tier 2 arena: one slot per resident warp, hash regions kept EMPTY between sets
-    const size_t smem1 = (size_t)WARPS * Tier1::WORDS * sizeof(uint32_t);
-    const int nb1 = ctx->model == TIM_IC     ? occupancy<TIM_IC, Tier1, 1, 1>(smem1)
+    const int cap1 = ctx->model == TIM_IC ? ctx->cap1 : 256;
+    const size_t smem1 = (size_t)WARPS * sizeof(uint32_t) *
+                         (cap1 == 128 ? Tier1S::WORDS : cap1 == 512 ? Tier1L::WORDS : Tier1::WORDS);
+    const int nb1 = ctx->model == TIM_IC
+                        ? (cap1 == 128   ? occupancy<TIM_IC, Tier1S, 1, 1>(smem1)
+                           : cap1 == 512 ? occupancy<TIM_IC, Tier1L, 1, 1>(smem1)
+                                         : occupancy<TIM_IC, Tier1, 1, 1>(smem1))
                     : ctx->model == TIM_TRIG ? occupancy<TIM_TRIG, Tier1, 1, 1>(smem1)
                                              : occupancy<TIM_LT, Tier1, 1, 1>(smem1);
     const int nb2 = ctx->model == TIM_IC     ? occupancy<TIM_IC, Tier2, 2, 1>(0)
@@ -1763,7 +1780,7 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
                 T = ctx->team_size;
                 if (T <= 0) {
                     T = 1;
-                    while (T < 8 && listed * 2 < slots1 / T) T *= 2;
+                    while (T < 8 && listed * (uint64_t)ctx->team_factor < slots1 / T) T *= 2;
                 }
                 ctx->last_team = T;
             }
@@ -1990,8 +2007,12 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
     TIM_TRY(tim_ensure(owner, owner->ovf_list, (size_t)(total + 1) * sizeof(uint2)));
     TIM_TRY(tim_ensure(owner, owner->ovf_list2, (size_t)(total + 1) * sizeof(uint2)));
     // arena and occupancy as in the single-query path
-    const size_t smem1 = (size_t)WARPS * Tier1::WORDS * sizeof(uint32_t);
-    const int nb1 = multi_occupancy<Tier1, 1, 1>(smem1);
+    const int cap1 = owner->cap1;
+    const size_t smem1 = (size_t)WARPS * sizeof(uint32_t) *
+                         (cap1 == 128 ? Tier1S::WORDS : cap1 == 512 ? Tier1L::WORDS : Tier1::WORDS);
+    const int nb1 = cap1 == 128   ? multi_occupancy<Tier1S, 1, 1>(smem1)
+                    : cap1 == 512 ? multi_occupancy<Tier1L, 1, 1>(smem1)
+                                  : multi_occupancy<Tier1, 1, 1>(smem1);
     const int nb2 = multi_occupancy<Tier2, 2, 1>(0);
     const unsigned grid1 = (unsigned)(owner->num_sms * nb1);
     const unsigned grid2 = (unsigned)(owner->num_sms * nb2);
@@ -2072,7 +2093,8 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
             if (T <= 0) {
                 T = 1;
                 const uint64_t slots1 = (uint64_t)grid2 * WARPS;
-                while (T < 8 && (uint64_t)h_cnt[0] * 2 < slots1 / T) T *= 2;
+                while (T < 8 && (uint64_t)h_cnt[0] * (uint64_t)owner->team_factor < slots1 / T)
+                    T *= 2;
             }
             TIM_TRY(launch_multi(owner, ma, 2, T, grid2, 0));
             CUDA_TRY(owner, cudaMemcpyAsync(h_cnt, d_cnt, sizeof h_cnt, cudaMemcpyDeviceToHost,

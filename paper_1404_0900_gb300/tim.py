@@ -90,7 +90,8 @@ class tim_batch_stats(C.Structure):
 
 class tim_tuning(C.Structure):
     _fields_ = [("width_budget", C.c_uint64), ("team_size", C.c_int), ("chunk", C.c_int),
-                ("trials", C.c_int), ("best_ms", C.c_double), ("default_ms", C.c_double)]
+                ("trials", C.c_int), ("best_ms", C.c_double), ("default_ms", C.c_double),
+                ("team_factor", C.c_int), ("pass1_capacity", C.c_int)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -126,6 +127,8 @@ _SIGS = {
     "tim_get_profile": (C.c_int, [_P, _P, C.c_int]),
     "tim_set_width_budget": (C.c_int, [_P, C.c_uint64]),
     "tim_set_team_size": (C.c_int, [_P, C.c_int]),
+    "tim_set_team_factor": (C.c_int, [_P, C.c_int]),
+    "tim_set_pass1_capacity": (C.c_int, [_P, C.c_int]),
     "tim_set_wait_limit": (C.c_int, [_P, C.c_uint32]),
     "tim_set_pass2_budget": (C.c_int, [_P, C.c_uint64]),
     "tim_set_heavy_pass": (C.c_int, [_P, C.c_int]),
@@ -478,6 +481,14 @@ def tim_autotune(ctx, sample_sets: int, seed: int = 1) -> dict:
 
 def tim_set_team_size(ctx, warps: int):
     _check(ctx, lib().tim_set_team_size(ctx, warps))
+
+
+def tim_set_team_factor(ctx, factor: int):
+    _check(ctx, lib().tim_set_team_factor(ctx, factor))
+
+
+def tim_set_pass1_capacity(ctx, members: int):
+    _check(ctx, lib().tim_set_pass1_capacity(ctx, members))
 
 
 def tim_set_pass2_budget(ctx, budget: int):

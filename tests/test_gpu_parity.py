@@ -89,15 +89,22 @@ def test_rr_sets_bit_exact(eng, name, model):
     _compare_store(eng, og, 12345678901, (5 << 40) + 17, 777)
 
 
-@pytest.mark.parametrize("budget,team", [(0, 0), (64, 1), (1 << 40, 0), (0, 2), (0, 4),
-                                         (0, 8), (300, 8)])
-def test_ic_rr_sets_bit_exact_for_any_split(eng, budget, team):
-    # which pass expands a set, and how many warps share it, must not matter
+@pytest.mark.parametrize("budget,team,cap,factor", [(0, 0, 256, 2), (64, 1, 256, 2),
+                                                    (1 << 40, 0, 256, 2), (0, 2, 256, 2),
+                                                    (0, 4, 256, 2), (0, 8, 256, 2),
+                                                    (300, 8, 256, 2), (1024, 0, 128, 1),
+                                                    (1024, 0, 512, 8), (1 << 40, 0, 512, 64),
+                                                    (2048, 0, 128, 4)])
+def test_ic_rr_sets_bit_exact_for_any_split(eng, budget, team, cap, factor):
+    # which pass expands a set, its queue capacity in pass 1 and how many warps share it
+    # must not matter
     g = inputs.rmat(13, seed=3)
     w = inputs.weighted_cascade(g)
     og = _load(eng, g, w, O.IC)
     tim.tim_set_width_budget(eng.ctx, budget)
     tim.tim_set_team_size(eng.ctx, team)
+    tim.tim_set_pass1_capacity(eng.ctx, cap)
+    tim.tim_set_team_factor(eng.ctx, factor)
     try:
         _compare_store(eng, og, 5, O.make_sid(3, 0, 0), 6000)
         k = O.kappa_sum(og, 10, 5, O.make_sid(1, 3, 0), 4000)
@@ -108,6 +115,8 @@ def test_ic_rr_sets_bit_exact_for_any_split(eng, budget, team):
     finally:
         tim.tim_set_width_budget(eng.ctx, 16384)
         tim.tim_set_team_size(eng.ctx, 0)
+        tim.tim_set_pass1_capacity(eng.ctx, 256)
+        tim.tim_set_team_factor(eng.ctx, 2)
 
 
 def test_rr_sets_ragged_and_empty(eng):
@@ -328,9 +337,13 @@ def test_autotune_keeps_results(eng):
     assert np.array_equal(before[0], after[0]) and before[2]["theta"] == after[2]["theta"]
     ref = O.tim_plus(og, 5, 0.5, 1.0, 9)
     assert np.array_equal(after[0], ref.seeds)
+    assert t["team_factor"] in (1, 2, 4, 8) and t["pass1_capacity"] in (128, 256, 512)
+    assert t["trials"] == 20
     tim.tim_set_width_budget(eng.ctx, 16384)
     tim.tim_set_team_size(eng.ctx, 0)
     tim.tim_set_chunk(eng.ctx, 2)
+    tim.tim_set_team_factor(eng.ctx, 2)
+    tim.tim_set_pass1_capacity(eng.ctx, 256)
 
 
 def _hub_graph(n, m_background, hub_degrees, seed):
