@@ -280,8 +280,9 @@ __device__ __forceinline__ void wstage_append4(uint32_t bits, const T* items, Wa
 // and marks the item starts in a 256-bit mask, so that every group finds its item and
 // the item's first group by popcounts; then, four chunks at a time, every lane loads
 // its group's item record, its 4 thresholds and draws its 4 coins, and the live
-// in-edges are queued as (position, set slot). The queue is resolved 64 at a time:
-// sources, then visited bits, then the new members' in-lists, each loaded together.
+// in-edges are queued as (position, set slot). The queue is resolved in two sweeps:
+// sources and visited-bit atomics, eight per lane in flight, then the new members'
+// in-lists, four per lane in flight.
 // Appends go through the warp's stages (members, frontier).
 __device__ __forceinline__ void expand_level(const BulkArgs& a, uint64_t lo, uint64_t nl,
                                              uint2* mbuf, uint4* fbuf, uint2* lb,
@@ -297,28 +298,50 @@ __device__ __forceinline__ void expand_level(const BulkArgs& a, uint64_t lo, uin
     uint32_t live_acc = 0, exam_acc = 0, nbuf = 0;
     auto drain = [&]() {
         __syncwarp();
-        for (uint32_t i = 0; i < nbuf; i += 64) {
-            const bool h0 = i + lane < nbuf, h1 = i + 32 + lane < nbuf;
-            const uint2 e0 = h0 ? lb[i + lane] : make_uint2(0u, 0u);
-            const uint2 e1 = h1 ? lb[i + 32 + lane] : make_uint2(0u, 0u);
-            uint32_t u[4] = {0u, 0u, 0u, 0u}, sv[4] = {e0.y, e1.y, 0u, 0u};
-            if (h0) u[0] = __ldg(a.src + e0.x);
-            if (h1) u[1] = __ldg(a.src + e1.x);
-            uint32_t fr = 0;
+        // sources and visited bits of every queued live in-edge, eight per lane in
+        // flight; each entry becomes (source, slot | new << 31) (slots are below 2^16)
+        for (uint32_t i0 = 0; i0 < nbuf; i0 += 256) {
+            uint32_t u[8], old[8];
 #pragma unroll
-            for (int q = 0; q < 2; q++)
-                if (q == 0 ? h0 : h1) {
-                    const uint32_t b = 1u << (u[q] & 31);
-                    const uint32_t old =
-                        atomicOr(&a.bitmap[(uint64_t)sv[q] * a.words + (u[q] >> 5)], b);
-                    if (!(old & b)) fr |= 1u << q;
+            for (int q = 0; q < 8; q++) {
+                const uint32_t idx = i0 + 32u * q + lane;
+                u[q] = idx < nbuf ? __ldg(a.src + lb[idx].x) : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t idx = i0 + 32u * q + lane;
+                old[q] = idx < nbuf ? atomicOr(&a.bitmap[(uint64_t)lb[idx].y * a.words + (u[q] >> 5)],
+                                               1u << (u[q] & 31))
+                                    : 0u;
+            }
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint32_t idx = i0 + 32u * q + lane;
+                if (idx < nbuf) {
+                    const bool fresh = !(old[q] & (1u << (u[q] & 31)));
+                    lb[idx] = make_uint2(u[q], lb[idx].y | (fresh ? 0x80000000u : 0u));
                 }
-            uint64_t d[2] = {0, 0};
+            }
+        }
+        __syncwarp();
+        // the new members: their in-lists and node words, four per lane in flight, then
+        // the member and frontier appends
+        for (uint32_t i = 0; i < nbuf; i += 128) {
+            uint32_t u[4], sv[4], fr = 0;
+#pragma unroll
+            for (int q = 0; q < 4; q++) {
+                const uint32_t idx = i + 32u * q + lane;
+                const uint2 e = idx < nbuf ? lb[idx] : make_uint2(0u, 0u);
+                u[q] = e.x;
+                sv[q] = e.y & 0x7FFFFFFFu;
+                if (e.y >> 31) fr |= 1u << q;
+            }
+            uint64_t d[4] = {0, 0, 0, 0};
             uint32_t push = 0;
             uint4 fi[4];
             uint2 mi[4];
 #pragma unroll
-            for (int q = 0; q < 2; q++) {
+            for (int q = 0; q < 4; q++) {
                 mi[q] = make_uint2(sv[q], u[q]);
                 if ((fr >> q) & 1u) {
                     const uint64_t ub = __ldg(a.rowptr + u[q]), ue = __ldg(a.rowptr + u[q] + 1);
@@ -331,12 +354,12 @@ __device__ __forceinline__ void expand_level(const BulkArgs& a, uint64_t lo, uin
                     if (cover && marked(a.seed_mark, u[q])) a.slot_flag[sv[q]] = 1u;
                 }
             }
-            slot_add(fr & 1u, sv[0], d[0], 1u, a, lane);
-            slot_add((fr >> 1) & 1u, sv[1], d[1], 1u, a, lane);
+#pragma unroll
+            for (int q = 0; q < 4; q++) slot_add((fr >> q) & 1u, sv[q], d[q], 1u, a, lane);
             wstage_append4(fr, mi, wm, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2, lane);
             if (cover) {
 #pragma unroll
-                for (int q = 0; q < 2; q++)
+                for (int q = 0; q < 4; q++)
                     if (((push >> q) & 1u) && a.slot_flag[sv[q]]) push &= ~(1u << q);
             }
             wstage_append4(push, fi, wf, &a.bs->f_count, a.F, a.fcap, &a.bs->err, 1, lane);
