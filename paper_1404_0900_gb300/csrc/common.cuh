@@ -229,6 +229,11 @@ int tim_scan_u64(tim_ctx* ctx, const unsigned long long* in, uint64_t* out, uint
 // in place (alternate buffers are taken from scratch).
 int tim_radix_sort_triples(tim_ctx* ctx, uint32_t* keys, uint32_t* va, uint32_t* vb,
                            uint64_t count, int bits);
+// The same, the first pass reading (k0, a0, b0) (which may be the destination arrays);
+// the sorted triples end in (keys, va, vb).
+int tim_radix_sort_triples_from(tim_ctx* ctx, const uint32_t* k0, const uint32_t* a0,
+                                const uint32_t* b0, uint32_t* keys, uint32_t* va, uint32_t* vb,
+                                uint64_t count, int bits);
 
 // graph.cu
 int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,

@@ -25,25 +25,22 @@ __global__ void check_rowptr_kernel(const int64_t* __restrict__ rowptr, int64_t 
     }
 }
 
-// Sort input per out-CSR edge e: key = destination, a = source, b = the weight's bits
-// (the triggering model, which has no per-edge weight: the edge id e).
-// Destinations are checked here; one warp per source node u writes the source of its
-// out-edges (the offsets are checked by check_rowptr_kernel only at the end of the load,
+// Sort input per out-CSR edge e: key = destination and b = the weight's bits are read by
+// the sort's first pass straight from the caller's arrays; this kernel checks the
+// destinations and writes a = the source (one warp per source node u over its
+// out-edges; the offsets are checked by check_rowptr_kernel only at the end of the load,
 // so they are clamped to [0, m) here: an invalid graph is rejected and its sources are
-// never used).
+// never used), and for the triggering model, which has no per-edge weight, b = the edge
+// id e.
 __global__ void edges_kernel(const int64_t* __restrict__ rowptr, const int32_t* __restrict__ dst,
                              const float* __restrict__ w, int64_t n, int64_t m,  // w null: ids
-                             uint32_t* __restrict__ keys, uint32_t* __restrict__ srcs,
-                             uint32_t* __restrict__ wbits, int* __restrict__ err) {
+                             uint32_t* __restrict__ srcs, uint32_t* __restrict__ wbits,
+                             int* __restrict__ err) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < m;
          e += (int64_t)gridDim.x * blockDim.x) {
-        int32_t v = dst[e];
-        if (v < 0 || v >= n) {
-            atomicOr(err, TIM_DEV_ERR_GRAPH);
-            v = 0;
-        }
-        keys[e] = (uint32_t)v;
-        wbits[e] = w ? __float_as_uint(w[e]) : (uint32_t)e;
+        const int32_t v = dst[e];
+        if (v < 0 || v >= n) atomicOr(err, TIM_DEV_ERR_GRAPH);
+        if (!w) wbits[e] = (uint32_t)e;
     }
     const int lane = threadIdx.x & 31;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -54,67 +51,76 @@ __global__ void edges_kernel(const int64_t* __restrict__ rowptr, const int32_t* 
     }
 }
 
-// In-CSR offsets from the sorted destinations: position j starts the in-lists of the
-// nodes after its predecessor's destination up to its own; the nodes after the last
-// destination start at m.
-__global__ void rowptr_from_keys_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t m,
-                                        uint64_t* __restrict__ rowptr) {
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = keys[j];
-        const int64_t prev = j > 0 ? (int64_t)keys[j - 1] : -1;
-        for (int64_t v = prev + 1; v <= k; v++) rowptr[v] = (uint64_t)j;
-        if (j == m - 1)
-            for (int64_t v = k + 1; v <= n; v++) rowptr[v] = (uint64_t)m;
-    }
+// floor(p 2^32) of an edge weight (bits) as a 64-bit integer; invalid weights (outside
+// [0, 1]) count as 0 and set *bad. In single precision: multiplying by 2^32 only moves
+// the exponent, so p 2^32 is exact, and conversion toward zero is the floor.
+__device__ __forceinline__ unsigned long long weight_scaled(uint32_t wb, bool* bad) {
+    float p = __uint_as_float(wb);
+    *bad = !(p >= 0.0f && p <= 1.0f);
+    if (*bad) p = 0.0f;
+    return __float2ull_rz(p * 4294967296.0f);
 }
 
-// Per in-edge (sorted position): its source, the self-loop and weight checks, and the
-// model's threshold from the weight carried through the sort.
-__global__ void fill_in_edges_kernel(const uint32_t* __restrict__ sorted_dst,
-                                     const uint32_t* __restrict__ sorted_src,
-                                     const uint32_t* __restrict__ sorted_wbits, int64_t n,
-                                     int64_t m, int model, uint32_t* __restrict__ src,
-                                     uint32_t* __restrict__ thr,
-                                     unsigned long long* __restrict__ lt_t,
-                                     uint32_t* __restrict__ posof, int* __restrict__ err) {
+// IC threshold: floor(p 2^32), p >= 1 (2^32) as 2^32 - 1 (always live)
+__device__ __forceinline__ uint32_t ic_threshold(uint32_t wb) {
+    bool bad;
+    const unsigned long long scaled = weight_scaled(wb, &bad);
+    return scaled > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)scaled;
+}
+
+// Everything the sorted (destination, source, weight) triples give, one pass per in-edge
+// (sorted position) that also reads its predecessor: the source (range and self-loop
+// checks), the in-CSR offsets at destination boundaries, the duplicate check (sources
+// strictly ascending inside an in-list), the model's threshold (weight checks), and for
+// IC whether a node's in-edges carry different thresholds.
+__global__ void in_edges_kernel(const uint32_t* __restrict__ sorted_dst,
+                                const uint32_t* __restrict__ sorted_src,
+                                const uint32_t* __restrict__ sorted_wbits, int64_t n, int64_t m,
+                                int model, uint64_t* __restrict__ rowptr,
+                                uint32_t* __restrict__ src, uint32_t* __restrict__ thr,
+                                unsigned long long* __restrict__ lt_t,
+                                uint32_t* __restrict__ posof, uint8_t* __restrict__ nonuni,
+                                int* __restrict__ err) {
+    // keys outside [0, n) come from an invalid graph (already flagged): clamped, so that
+    // nothing is written out of bounds
+    const uint32_t vmax = (uint32_t)(n - 1);
     for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < m;
          pos += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t v = sorted_dst[pos];
+        const uint32_t v = min(sorted_dst[pos], vmax);
         uint32_t u = sorted_src[pos];
+        const uint32_t wb = sorted_wbits[pos];
         if (u >= (uint64_t)n) {  // offsets that miss this edge (an invalid graph)
             atomicOr(err, TIM_DEV_ERR_GRAPH);
             u = 0;
         }
         if (u == v) atomicOr(err, TIM_DEV_ERR_GRAPH);
         src[pos] = u;
-        if (model == TIM_TRIG) {  // no weight; record where out-edge e landed
+        // the in-CSR offsets: rowptr[w] = pos for every w in (previous key, v]
+        const int64_t prev = pos > 0 ? (int64_t)min(sorted_dst[pos - 1], vmax) : -1;
+        for (int64_t w = prev + 1; w <= (int64_t)v; w++) rowptr[w] = (uint64_t)pos;
+        if (pos == m - 1)
+            for (int64_t w = (int64_t)v + 1; w <= n; w++) rowptr[w] = (uint64_t)m;
+        const bool same = prev == (int64_t)v;  // the predecessor is in the same in-list
+        if (same) {
+            uint32_t pu = sorted_src[pos - 1];
+            if (pu >= (uint64_t)n) pu = 0;
+            if (u <= pu) atomicOr(err, TIM_DEV_ERR_GRAPH);
+        }
+        if (model == TIM_TRIG) {  // no weight; record where out-edge wb landed
             thr[pos] = 0u;
-            posof[sorted_wbits[pos]] = (uint32_t)pos;
+            posof[wb] = (uint32_t)pos;
             continue;
         }
-        float p = __uint_as_float(sorted_wbits[pos]);
-        if (!(p >= 0.0f && p <= 1.0f)) {
-            atomicOr(err, TIM_DEV_ERR_WEIGHT);
-            p = 0.0f;
-        }
-        double scaled = (double)p * 4294967296.0;  // exact: float -> double, times 2^32
+        bool bad;
+        const unsigned long long scaled = weight_scaled(wb, &bad);
+        if (bad) atomicOr(err, TIM_DEV_ERR_WEIGHT);
         if (model == TIM_IC) {
-            thr[pos] = p >= 1.0f ? 0xFFFFFFFFu : (uint32_t)scaled;  // truncation = floor
+            const uint32_t t = scaled > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)scaled;
+            thr[pos] = t;
+            if (same && ic_threshold(sorted_wbits[pos - 1]) != t) nonuni[v] = 1;
         } else {
-            lt_t[pos] = (unsigned long long)scaled;
+            lt_t[pos] = scaled;
         }
-    }
-}
-
-// Duplicate edges: equal neighbouring sources inside one in-list.
-__global__ void check_dups_kernel(const uint32_t* __restrict__ sorted_dst,
-                                  const uint32_t* __restrict__ src, int64_t m,
-                                  int* __restrict__ err) {
-    for (int64_t pos = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < m;
-         pos += (int64_t)gridDim.x * blockDim.x) {
-        if (sorted_dst[pos] == sorted_dst[pos - 1] && src[pos] <= src[pos - 1])
-            atomicOr(err, TIM_DEV_ERR_GRAPH);
     }
 }
 
@@ -136,19 +142,6 @@ __global__ void lt_thr_kernel(const uint64_t* __restrict__ rowptr, const uint32_
         thr[j] = c > 0xFFFFFFFFull ? 0xFFFFFFFFu : (uint32_t)c;
         if ((uint64_t)j + 1 == end && c > bound) atomicOr(err, TIM_DEV_ERR_WEIGHT);
         if ((uint64_t)j > beg && lt_t[j] != lt_t[j - 1]) nonuni[v] = 1;
-    }
-}
-
-// IC: mark nodes whose in-edges do not all carry the same threshold. One thread per
-// in-edge.
-__global__ void ic_nonuniform_kernel(const uint64_t* __restrict__ rowptr,
-                                     const uint32_t* __restrict__ dst_sorted, int64_t m,
-                                     const uint32_t* __restrict__ thr,
-                                     uint8_t* __restrict__ nonuni) {
-    for (int64_t j = 1 + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < m;
-         j += (int64_t)gridDim.x * blockDim.x) {
-        const uint32_t v = dst_sorted[j];
-        if ((uint64_t)j > rowptr[v] && thr[j] != thr[j - 1]) nonuni[v] = 1;
     }
 }
 
@@ -329,8 +322,10 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
     TIM_TRY(tim_ensure(ctx, ctx->rowptr, (size_t)(n + 1) * sizeof(uint64_t)));
     TIM_TRY(tim_ensure(ctx, ctx->src, (size_t)(m + 4) * sizeof(uint32_t)));
     TIM_TRY(tim_ensure(ctx, ctx->thr, (size_t)(m + 4) * sizeof(uint32_t)));
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->src.p, 0, (size_t)(m + 4) * sizeof(uint32_t), ctx->stream));
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->thr.p, 0, (size_t)(m + 4) * sizeof(uint32_t), ctx->stream));
+    // every in-edge is written below; only the padding after the last one (read by
+    // 16-byte group loads) needs zeros
+    CUDA_TRY(ctx, cudaMemsetAsync((uint32_t*)ctx->src.p + m, 0, 4 * sizeof(uint32_t), ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync((uint32_t*)ctx->thr.p + m, 0, 4 * sizeof(uint32_t), ctx->stream));
 
     // temporaries of the build, kept by the context so that reloading allocates nothing
     DevBuf& keys = ctx->ld_keys;
@@ -350,28 +345,30 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
         check_rowptr_kernel<<<G, T, 0, ctx->stream>>>(d_rowptr, n, m, &ds->err);
         ctx->launches++;
         if (m > 0) {
-            edges_kernel<<<G, T, 0, ctx->stream>>>(d_rowptr, d_dst, d_w, n, m, (uint32_t*)keys.p,
-                                                   (uint32_t*)srcs.p, (uint32_t*)wbits.p,
-                                                   &ds->err);
+            edges_kernel<<<G, T, 0, ctx->stream>>>(d_rowptr, d_dst, d_w, n, m, (uint32_t*)srcs.p,
+                                                   (uint32_t*)wbits.p, &ds->err);
             ctx->launches++;
             int bits = 0;
             while (bits < 32 && ((int64_t)1 << bits) < n) bits++;
-            if ((rc = tim_radix_sort_triples(ctx, (uint32_t*)keys.p, (uint32_t*)srcs.p,
-                                             (uint32_t*)wbits.p, (uint64_t)m, bits)))
+            // destinations and weight bits straight from the caller's arrays (an invalid
+            // destination has been flagged and only has to stay in bounds below)
+            if ((rc = tim_radix_sort_triples_from(
+                     ctx, (const uint32_t*)d_dst, (const uint32_t*)srcs.p,
+                     d_w ? (const uint32_t*)d_w : (const uint32_t*)wbits.p, (uint32_t*)keys.p,
+                     (uint32_t*)srcs.p, (uint32_t*)wbits.p, (uint64_t)m, bits)))
                 break;
-            rowptr_from_keys_kernel<<<G, T, 0, ctx->stream>>>((const uint32_t*)keys.p, n, m,
-                                                              (uint64_t*)ctx->rowptr.p);
-            ctx->launches++;
             if (model == TIM_TRIG &&
                 (rc = tim_ensure(ctx, ctx->ld_posof, (size_t)(m + 1) * sizeof(uint32_t))))
                 break;
-            fill_in_edges_kernel<<<G, T, 0, ctx->stream>>>(
+            if ((rc = tim_ensure(ctx, nonuni, (size_t)(n + 1)))) break;
+            if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(nonuni.p, 0, (size_t)(n + 1), ctx->stream),
+                                     "memset")))
+                break;
+            in_edges_kernel<<<G, T, 0, ctx->stream>>>(
                 (const uint32_t*)keys.p, (const uint32_t*)srcs.p, (const uint32_t*)wbits.p, n, m,
-                model, (uint32_t*)ctx->src.p, (uint32_t*)ctx->thr.p, (unsigned long long*)lt_t.p,
-                (uint32_t*)ctx->ld_posof.p, &ds->err);
-            ctx->launches++;
-            check_dups_kernel<<<G, T, 0, ctx->stream>>>((const uint32_t*)keys.p,
-                                                        (const uint32_t*)ctx->src.p, m, &ds->err);
+                model, (uint64_t*)ctx->rowptr.p, (uint32_t*)ctx->src.p, (uint32_t*)ctx->thr.p,
+                (unsigned long long*)lt_t.p, (uint32_t*)ctx->ld_posof.p, (uint8_t*)nonuni.p,
+                &ds->err);
             ctx->launches++;
         } else if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(ctx->rowptr.p, 0,
                                                              (size_t)(n + 1) * sizeof(uint64_t),
@@ -379,10 +376,13 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
                                         "memset"))) {
             break;
         }
-        if ((rc = tim_ensure(ctx, nonuni, (size_t)(n + 1)))) break;
-        if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(nonuni.p, 0, (size_t)(n + 1), ctx->stream),
-                                 "memset")))
-            break;
+        if (m == 0) {  // no in-edges: every node's list is uniform (empty)
+            if ((rc = tim_ensure(ctx, nonuni, (size_t)(n + 1)))) break;
+            if ((rc = tim_cuda_check(ctx, cudaMemsetAsync(nonuni.p, 0, (size_t)(n + 1),
+                                                          ctx->stream),
+                                     "memset")))
+                break;
+        }
         if (m > 0 && model == TIM_LT) {
             if ((rc = tim_ensure(ctx, lt_e, (size_t)(m + 1) * sizeof(uint64_t)))) break;
             if ((rc = tim_scan_u64(ctx, (const unsigned long long*)lt_t.p, (uint64_t*)lt_e.p,
@@ -392,11 +392,6 @@ int tim_graph_build(tim_ctx* ctx, int64_t n, int64_t m, const int64_t* d_rowptr,
                 (const uint64_t*)ctx->rowptr.p, (const uint32_t*)keys.p, m,
                 (const unsigned long long*)lt_t.p, (const uint64_t*)lt_e.p, (uint32_t*)ctx->thr.p,
                 (uint8_t*)nonuni.p, &ds->err);
-            ctx->launches++;
-        } else if (m > 0 && model == TIM_IC) {
-            ic_nonuniform_kernel<<<G, T, 0, ctx->stream>>>(
-                (const uint64_t*)ctx->rowptr.p, (const uint32_t*)keys.p, m,
-                (const uint32_t*)ctx->thr.p, (uint8_t*)nonuni.p);
             ctx->launches++;
         }
         if ((rc = tim_ensure(ctx, ctx->node_thr, (size_t)(n + 1) * 8))) break;

@@ -261,9 +261,22 @@ int tim_scan_u64(tim_ctx* ctx, const unsigned long long* in, uint64_t* out, uint
     return scan_to_u64<unsigned long long>(ctx, in, out, count);
 }
 
-int tim_radix_sort_triples(tim_ctx* ctx, uint32_t* keys, uint32_t* va, uint32_t* vb,
-                           uint64_t count, int bits) {
-    if (count <= 1 || bits <= 0) return TIM_OK;
+int tim_radix_sort_triples_from(tim_ctx* ctx, const uint32_t* k0, const uint32_t* a0,
+                                const uint32_t* b0, uint32_t* keys, uint32_t* va, uint32_t* vb,
+                                uint64_t count, int bits) {
+    auto copy_to = [&](const uint32_t* k, const uint32_t* a, const uint32_t* b) -> int {
+        if (k != keys)
+            CUDA_TRY(ctx, cudaMemcpyAsync(keys, k, count * sizeof(uint32_t),
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
+        if (a != va)
+            CUDA_TRY(ctx, cudaMemcpyAsync(va, a, count * sizeof(uint32_t),
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
+        if (b != vb)
+            CUDA_TRY(ctx, cudaMemcpyAsync(vb, b, count * sizeof(uint32_t),
+                                          cudaMemcpyDeviceToDevice, ctx->stream));
+        return TIM_OK;
+    };
+    if (count <= 1 || bits <= 0) return count ? copy_to(k0, a0, b0) : TIM_OK;
     // passes of at most 8 bits, the digit width spread evenly over them (26 bits: four
     // passes of 7 bits; fewer bins make longer runs per tile)
     const int passes = (bits + 7) / 8;
@@ -280,30 +293,31 @@ int tim_radix_sort_triples(tim_ctx* ctx, uint32_t* keys, uint32_t* va, uint32_t*
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RS_SMEM));
     uint32_t* hist = (uint32_t*)ctx->scratch_c.p;
     uint64_t* offs = (uint64_t*)ctx->scratch_d.p;
-    uint32_t *kin = keys, *ain = va, *bin = vb;
-    uint32_t *kout = (uint32_t*)ctx->scratch_a.p, *aout = (uint32_t*)ctx->scratch_b.p,
-             *bout = (uint32_t*)ctx->scratch_f.p;
+    // pass p writes the scratch arrays when p is even and the destination when p is odd,
+    // so that the first pass may read the caller's arrays (which may be the destination's)
+    uint32_t* const S[3] = {(uint32_t*)ctx->scratch_a.p, (uint32_t*)ctx->scratch_b.p,
+                            (uint32_t*)ctx->scratch_f.p};
+    uint32_t* const D[3] = {keys, va, vb};
+    const uint32_t *kin = k0, *ain = a0, *bin = b0;
     for (int p = 0; p < passes; p++) {
         const int shift = width * p;
+        uint32_t* const* out = (p % 2 == 0) ? S : D;
         radix_hist_kernel<<<(unsigned)ntiles, 256, 0, ctx->stream>>>(kin, count, shift, mask,
                                                                      ntiles, hist);
         LAUNCH_CHECK(ctx, "radix_hist_kernel");
         TIM_TRY(tim_scan_u32_to_u64(ctx, hist, offs, nh));
         radix_scatter3_kernel<<<(unsigned)ntiles, RS_WARPS * 32, RS_SMEM, ctx->stream>>>(
-            kin, ain, bin, kout, aout, bout, count, shift, mask, ntiles, offs,
+            kin, ain, bin, out[0], out[1], out[2], count, shift, mask, ntiles, offs,
             &tim_dscal(ctx)->err);
         LAUNCH_CHECK(ctx, "radix_scatter3_kernel");
-        std::swap(kin, kout);
-        std::swap(ain, aout);
-        std::swap(bin, bout);
+        kin = out[0];
+        ain = out[1];
+        bin = out[2];
     }
-    if (kin != keys) {
-        CUDA_TRY(ctx, cudaMemcpyAsync(keys, kin, count * sizeof(uint32_t),
-                                      cudaMemcpyDeviceToDevice, ctx->stream));
-        CUDA_TRY(ctx, cudaMemcpyAsync(va, ain, count * sizeof(uint32_t),
-                                      cudaMemcpyDeviceToDevice, ctx->stream));
-        CUDA_TRY(ctx, cudaMemcpyAsync(vb, bin, count * sizeof(uint32_t),
-                                      cudaMemcpyDeviceToDevice, ctx->stream));
-    }
-    return TIM_OK;
+    return copy_to(kin, ain, bin);
+}
+
+int tim_radix_sort_triples(tim_ctx* ctx, uint32_t* keys, uint32_t* va, uint32_t* vb,
+                           uint64_t count, int bits) {
+    return tim_radix_sort_triples_from(ctx, keys, va, vb, keys, va, vb, count, bits);
 }
