@@ -517,6 +517,20 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
     return T == 1 ? __shfl_sync(0xffffffffu, vctl[1], 0) : vctl[1];
 }
 
+// kappa (Eq. 6) of the sets whose widths lanes 0 .. cnt-1 hold, one set per lane: the
+// FP64 operations of 32 sets share one warp instruction each (GB300's FP64 rate is a
+// small fraction of its FP32 rate, and one set per warp instruction cost several ms per
+// run of Algorithm 2 on the largest graphs). Each lane adds into its own 128-bit sum.
+__device__ __forceinline__ void kappa_lanes(unsigned long long w, unsigned cnt, int lane,
+                                            unsigned long long m, int k, unsigned long long& lo,
+                                            unsigned long long& hi) {
+    if ((unsigned)lane < cnt) {
+        const unsigned long long kf = kappa_fixed(kappa_fp64(w, m, k));
+        lo += kf;
+        if (lo < kf) hi++;
+    }
+}
+
 // TIER 1: teams of one warp, storage in shared memory, every set index of [0, count),
 // in-edge budget (IC); listed sets go to list1. TIER 2: teams of T warps, storage in
 // the global arena, the sets of list1, no budget; listed sets go to list2.
@@ -553,6 +567,10 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
     unsigned long long k_lo = 0, k_hi = 0, wsum = 0, cov = 0, live = 0, memb = 0, exam = 0;
     const bool emit = a.flags & SAMPLE_EMIT, kap = a.flags & SAMPLE_KAPPA;
     const bool leader = wt == 0 && lane == 0;
+    // widths of completed sets waiting for their kappa (warp 0 of the team; lane i holds
+    // the i-th, kcnt is the same on every lane)
+    unsigned long long kw = 0;
+    unsigned kcnt = 0;
     for (;;) {
         unsigned long long i0 = 0;
         if (leader) i0 = atomicAdd(counter, (unsigned long long)a.chunk);
@@ -592,10 +610,12 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
                 wsum += width;
                 memb += tail;
                 if (st & ST_COVERED) cov++;
-                if (kap) {
-                    unsigned long long kf = kappa_fixed(kappa_fp64(width, a.m, a.k));
-                    k_lo += kf;
-                    if (k_lo < kf) k_hi++;
+            }
+            if (kap && wt == 0) {  // width is the same on every lane
+                if ((unsigned)lane == kcnt) kw = width;
+                if (++kcnt == 32) {
+                    kappa_lanes(kw, kcnt, lane, a.m, a.k, k_lo, k_hi);
+                    kcnt = 0;
                 }
             }
             if (emit) {
@@ -629,8 +649,11 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
     live = warp_sum_u64(live);
     if (lane == 0 && live) atomicAdd(&a.ds->live[TIER - 1], live);
     if (lane == 0 && exam) atomicAdd(&a.ds->exam[TIER - 1], exam);
+    if (kap && wt == 0) {
+        kappa_lanes(kw, kcnt, lane, a.m, a.k, k_lo, k_hi);
+        if (k_lo || k_hi) atomic_add_u128(&a.ds->ksum_lo, &a.ds->ksum_hi, k_lo, k_hi);
+    }
     if (leader) {
-        if (kap) atomic_add_u128(&a.ds->ksum_lo, &a.ds->ksum_hi, k_lo, k_hi);
         if (wsum) {
             atomicAdd(&a.ds->wsum, wsum);
             atomicAdd(&a.ds->width[TIER - 1], wsum);
