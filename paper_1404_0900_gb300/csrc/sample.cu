@@ -1342,6 +1342,18 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
     const bool leader = wt == 0 && lane == 0;
     QAcc acc{0, 0, 0, 0, 0, 0, 0};
     int cur_q = -1;
+    // kappa of the current query's completed sets, 32 at a time, one per lane (warp 0 of
+    // the team): pending widths, the query's m and k, and each lane's 128-bit sum
+    unsigned long long kw = 0, km = 0, klo = 0, khi = 0;
+    unsigned kcnt = 0;
+    int kk = 0;
+    auto kflush = [&](int qi) {
+        kappa_lanes(kw, kcnt, lane, km, kk, klo, khi);
+        kcnt = 0;
+        if (qi >= 0 && (klo || khi))
+            atomic_add_u128(&ma.q[qi].ds->ksum_lo, &ma.q[qi].ds->ksum_hi, klo, khi);
+        klo = khi = 0;
+    };
     for (;;) {
         unsigned long long i0 = 0;
         if (leader) i0 = atomicAdd(counter, (unsigned long long)ma.chunk);
@@ -1375,6 +1387,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
                 j = e.y;
             }
             if (qi != cur_q) {
+                if (wt == 0) kflush(cur_q);
                 flush_acc<TIER>(ma.q, cur_q, acc, lane);
                 cur_q = qi;
             }
@@ -1414,10 +1427,14 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
                 acc.wsum += width;
                 acc.memb += tail;
                 if (st & ST_COVERED) acc.cov++;
-                if (d.flags & SAMPLE_KAPPA) {
-                    const unsigned long long kf = kappa_fixed(kappa_fp64(width, d.m, d.k));
-                    acc.k_lo += kf;
-                    if (acc.k_lo < kf) acc.k_hi++;
+            }
+            if ((d.flags & SAMPLE_KAPPA) && wt == 0) {  // width is the same on every lane
+                if ((unsigned)lane == kcnt) kw = width;
+                km = d.m;
+                kk = d.k;
+                if (++kcnt == 32) {
+                    kappa_lanes(kw, kcnt, lane, km, kk, klo, khi);
+                    kcnt = 0;
                 }
             }
             if (d.flags & SAMPLE_EMIT) {
@@ -1448,6 +1465,7 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
             team_sync<T>(team);
         }
     }
+    if (wt == 0) kflush(cur_q);
     flush_acc<TIER>(ma.q, cur_q, acc, lane);
 }
 
