@@ -96,6 +96,7 @@ struct tim_ctx {
     // sets handed from tier 1 to tier 2 and from tier 2 to tier 3 of the sampler
     DevBuf ovf_list;    // uint32 set index
     DevBuf ovf_list2;   // uint32 set index
+    DevBuf hand;        // IC: pass-1 state of the sets handed to pass 2
     DevBuf arena;       // tier-2 per-warp hash + queue
     bool arena_clean = false;
     DevBuf lt_col;      // tier-1 LT: member columns, one per thread

@@ -13,6 +13,9 @@
 //   coin words) and loads 4 thresholds with one 16-byte load. A set whose members
 //   outgrow the queue, or (IC) whose examined in-edges would pass a budget, is listed
 //   for tier 2. This keeps the kernel's tail short: light sets are most sets.
+// An IC set that tier 1 gives up on is handed over with its state (the queue so far,
+//   the frontier batch to redo, the width before it), and tier 2 goes on from there
+//   instead of starting again from the root (the coins are keyed, so the set is the same).
 // Tier 2: the same code with a 32x larger queue and hash in global memory (one arena
 //   slot per team; the queue tail and status stay in shared memory, since every new
 //   member takes a tail atomic) and no edge budget, run by teams of T warps per set: T = 1 when the
@@ -84,6 +87,10 @@ struct SampleArgs {
     unsigned long long width_budget2; // tier 2 IC: in-edges one team may examine per set
     int chunk;                        // sets claimed per work-counter increment
     uint32_t* lt_col;                 // tier 1 LT: per-thread member columns
+    // IC: the state pass 1 hands to pass 2 for the set at list1 position i < hcap, hw
+    // words at hand + i hw: queue length, resume position, width so far (2 words), queue
+    uint32_t* hand;
+    uint32_t hcap, hw;
     // triggering model: options of each node, their cumulative thresholds, their in-edges
     const uint64_t* node_opt;
     const uint32_t* opt_cum;
@@ -220,8 +227,17 @@ __device__ __forceinline__ int follow_live(const A& a, uint32_t g, uint32_t mask
 // whole team (no ownership search, two groups in flight per lane).
 constexpr uint32_t BIG_GROUPS = 32;
 
+// Where an IC expansion stopped: the queue position of the frontier batch to process
+// next and the width of the members before it.
+struct Resume {
+    int head;
+    unsigned long long width;
+};
+
 // Expand one RR set with a team of T warps (wt = warp index in the team, team = team
-// index in the block). Returns the status bits; *width_out = w(R) (Eq. 1); *live_out
+// index in the block). IC only: with `in` the queue, hash and ctl already hold a set
+// that an earlier pass stopped (queue[0 .. ctl[0])), and the expansion goes on from
+// in->head with width in->width; with `out`, an expansion that stops records where. Returns the status bits; *width_out = w(R) (Eq. 1); *live_out
 // counts live in-edges followed (per lane).
 template <int MODEL, class C, int T, class A>
 __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t sid, uint32_t* hash,
@@ -229,12 +245,13 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                                        unsigned long long budget, int wt, int team,
                                        unsigned long long* width_out,
                                        unsigned long long* live_out,
-                                       unsigned long long* exam_out) {
+                                       unsigned long long* exam_out,
+                                       const Resume* in = nullptr, Resume* out = nullptr) {
     const int lane = threadIdx.x & 31;
     volatile int* vctl = ctl;
     const bool cover = a.flags & SAMPLE_COVER;
     const uint32_t root = rr_root(sid, a.n, K);
-    if (wt == 0 && lane == 0) {
+    if (!in && wt == 0 && lane == 0) {
         uint32_t h = (root * 0x9E3779B1u) >> (32 - C::LOG2H);
         hash[h] = root;
         queue[0] = root;
@@ -243,11 +260,13 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
         ctl[1] = (cover && marked(a.seed_mark, root)) ? ST_COVERED : 0;
     }
     team_sync<T>(team);
-    unsigned long long width = 0, live = 0, work = 0, exam = 0;
+    unsigned long long width = in ? in->width : 0, live = 0, work = 0, exam = 0;
     if constexpr (MODEL == TIM_IC) {
         const uint32_t s0 = (uint32_t)sid, s1 = (uint32_t)(sid >> 32);
         const uint4* thr4 = reinterpret_cast<const uint4*>(a.thr);
-        int head = 0;
+        int head = in ? in->head : 0;
+        int bh = head;                // the batch being processed and the width before it
+        unsigned long long bw = width;
         for (int guard = 0; guard < C::Q + 1; guard++) {
             // a consistent snapshot of (tail, status) for the whole team
             int tail, stat;
@@ -260,6 +279,8 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
                 team_sync<T>(team);
             }
             if (stat || head >= tail) break;
+            bh = head;
+            bw = width;
             const int nb = min(32, tail - head);
             uint64_t beg = 0, end = 0;
             // a node's in-edges often share one threshold (weighted cascade: p = 1/indeg);
@@ -411,6 +432,10 @@ __device__ __forceinline__ int team_rr(const A& a, const PhiloxKeys& K, uint64_t
             }
             team_sync<T>(team);
             head += nb;
+        }
+        if (out) {  // meaningful when the set stopped: the batch to (re)process
+            out->head = bh;
+            out->width = bw;
         }
     } else if constexpr (MODEL == TIM_TRIG) {
         // a general triggering model (Section 4.2): every reached node picks one option
@@ -587,20 +612,69 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
         for (unsigned long long it = i0; it < i1; it++) {
             const uint64_t j = TIER == 1 ? it : a.list1[it];
             unsigned long long width;
-            const int st = team_rr<MODEL, C, T, SampleArgs>(a, a.K, a.sid0 + j, hash, queue, slot,
-                                                            ctl, budget, wt, team, &width, &live,
-                                                            &exam);
+            // IC: pass 2 goes on with a set where pass 1 stopped, from the state pass 1
+            // handed over (its queue, the batch to redo, the width before it)
+            constexpr bool HAND = MODEL == TIM_IC;
+            Resume rin{0, 0ull}, rout{0, 0ull};
+            bool resumed = false;
+            if (HAND && TIER == 2 && a.hand && it < a.hcap) {
+                const uint32_t* hs = a.hand + it * (uint64_t)a.hw;
+                const uint32_t t0 = hs[0];
+                if (t0 > 0 && t0 <= (uint32_t)C::Q) {
+                    if (leader) {
+                        ctl[0] = (int)t0;
+                        ctl[1] = 0;
+                    }
+                    team_sync<T>(team);
+                    for (uint32_t i = tl; i < t0; i += 32 * T) {
+                        const uint32_t u = hs[4 + i];
+                        queue[i] = u;
+                        // the members are distinct: each takes the first empty slot it finds
+                        uint32_t h = (u * 0x9E3779B1u) >> (32 - C::LOG2H);
+                        for (int probe = 0; probe < C::H; probe++) {
+                            if (atomicCAS(&hash[h], EMPTY, u) == EMPTY) break;
+                            h = (h + 1) & (C::H - 1);
+                        }
+                        slot[i] = (uint16_t)h;
+                        // a member in the seed set found in the batch that overflowed pass
+                        // 1's queue: the set is covered (as a fresh expansion would find)
+                        if ((a.flags & SAMPLE_COVER) && marked(a.seed_mark, u))
+                            atomicOr(&ctl[1], ST_COVERED);
+                    }
+                    rin.head = (int)min(hs[1], t0);
+                    rin.width = (unsigned long long)hs[2] | ((unsigned long long)hs[3] << 32);
+                    resumed = true;
+                }
+                team_sync<T>(team);
+            }
+            const int st = team_rr<MODEL, C, T, SampleArgs>(
+                a, a.K, a.sid0 + j, hash, queue, slot, ctl, budget, wt, team, &width, &live,
+                &exam, resumed ? &rin : nullptr, (HAND && TIER == 1 && a.hand) ? &rout : nullptr);
             const int tail = min(T == 1 ? __shfl_sync(0xffffffffu, ((volatile int*)ctl)[0], 0)
                                         : ((volatile int*)ctl)[0],
                                  C::Q);
             team_sync<T>(team);
             if (st & ST_OVERFLOW) {
+                unsigned idx = 0;
                 if (leader) {
-                    unsigned idx = atomicAdd(out_cnt, 1u);
+                    idx = atomicAdd(out_cnt, 1u);
                     if (idx < a.list_cap)
                         out_list[idx] = (uint32_t)j;
                     else
                         atomicOr(&a.ds->err, TIM_DEV_ERR_OVF_LIST);
+                }
+                if (HAND && TIER == 1 && T == 1 && a.hand) {  // hand the state to pass 2
+                    idx = __shfl_sync(0xffffffffu, idx, 0);
+                    if (idx < a.hcap) {
+                        uint32_t* hs = a.hand + idx * (uint64_t)a.hw;
+                        for (int i = lane; i < tail; i += 32) hs[4 + i] = queue[i];
+                        if (lane == 0) {
+                            hs[0] = (uint32_t)tail;
+                            hs[1] = (uint32_t)rout.head;
+                            hs[2] = (uint32_t)rout.width;
+                            hs[3] = (uint32_t)(rout.width >> 32);
+                        }
+                    }
                 }
                 for (int i = tl; i < C::H; i += 32 * T) hash[i] = EMPTY;
                 team_sync<T>(team);
@@ -1798,6 +1872,19 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
     a.width_budget = ctx->width_budget;
     a.width_budget2 = ctx->width_budget2;
     a.chunk = std::max(1, ctx->chunk);
+    // IC: room for the pass-1 state of up to count / 8 + 4096 handed-over sets (at most
+    // 1 GiB); sets listed beyond it start over in pass 2
+    a.hand = nullptr;
+    a.hcap = 0;
+    a.hw = 4u + (uint32_t)cap1;
+    if (ctx->model == TIM_IC && count > 0) {
+        const uint64_t maxslots = (1ull << 30) / ((uint64_t)a.hw * sizeof(uint32_t));
+        const uint64_t hcap = std::min<uint64_t>(std::min<uint64_t>(count / 8 + 4096, maxslots),
+                                                 list_cap);
+        TIM_TRY(tim_ensure(ctx, ctx->hand, (size_t)hcap * a.hw * sizeof(uint32_t)));
+        a.hand = (uint32_t*)ctx->hand.p;
+        a.hcap = (uint32_t)hcap;
+    }
     a.node_opt = (const uint64_t*)ctx->node_opt.p;
     a.opt_cum = (const uint32_t*)ctx->opt_cum.p;
     a.opt_off = (const uint64_t*)ctx->opt_off.p;
