@@ -187,7 +187,7 @@ int tim_destroy(tim_ctx* ctx) {
                       &ctx->counts,   &ctx->node_off,   &ctx->cursor,    &ctx->node_sets,
                       &ctx->covered,  &ctx->chosen,     &ctx->best,      &ctx->seed_mark,
                       &ctx->seeds_dev, &ctx->ovf_list,  &ctx->big_bitmap, &ctx->big_queue,
-                      &ctx->ovf_list2, &ctx->hand, &ctx->arena,    &ctx->lt_col,    &ctx->greedy_bar,
+                      &ctx->ovf_list2, &ctx->hand, &ctx->hand2, &ctx->arena,    &ctx->lt_col,    &ctx->greedy_bar,
                       &ctx->greedy_chunks, &ctx->greedy_nchunk,
                       &ctx->scratch_a, &ctx->scratch_b, &ctx->scratch_c, &ctx->scratch_d,
                       &ctx->scratch_e, &ctx->scratch_f, &ctx->scal,     &ctx->bulk_bitmap,

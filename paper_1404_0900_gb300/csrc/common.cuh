@@ -97,6 +97,7 @@ struct tim_ctx {
     DevBuf ovf_list;    // uint32 set index
     DevBuf ovf_list2;   // uint32 set index
     DevBuf hand;        // IC: pass-1 state of the sets handed to pass 2
+    DevBuf hand2;       // IC: pass-2 state of the sets handed to the heavy pass
     DevBuf arena;       // tier-2 per-warp hash + queue
     bool arena_clean = false;
     DevBuf lt_col;      // tier-1 LT: member columns, one per thread
@@ -265,10 +266,13 @@ struct SampleResult {
     uint64_t big_sets = 0;
 };
 int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res);
-// Third tier for the heavy IC sets list[0 .. count) (sample_bulk.cu).
+// Third tier for the heavy IC sets list[0 .. count) (sample_bulk.cu). With hand (may be
+// null), the set at list position i < hcap starts from the state pass 2 left at
+// hand + i hw: queue length, position of the batch to redo, then the queue.
 int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, uint32_t count,
                 uint32_t* pool, uint32_t* pool_sid, uint64_t pool_cap, DevScalars* ds,
-                uint64_t* live_out);
+                uint64_t* live_out, const uint32_t* hand = nullptr, uint32_t hcap = 0,
+                uint32_t hw = 0);
 
 // Several queries, each with its own context (graph, RR-set store), sampled by one
 // launch per tier; all share the Philox key of `seed` and use the owner's stream and

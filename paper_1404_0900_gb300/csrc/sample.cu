@@ -91,6 +91,10 @@ struct SampleArgs {
     // words at hand + i hw: queue length, resume position, width so far (2 words), queue
     uint32_t* hand;
     uint32_t hcap, hw;
+    // IC: the state pass 2 hands to the heavy pass for the set at list2 position i < h2cap,
+    // h2w words at hand2 + i h2w: queue length, resume position, 2 spare words, queue
+    uint32_t* hand2;
+    uint32_t h2cap, h2w;
     // triggering model: options of each node, their cumulative thresholds, their in-edges
     const uint64_t* node_opt;
     const uint32_t* opt_cum;
@@ -649,7 +653,8 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
             }
             const int st = team_rr<MODEL, C, T, SampleArgs>(
                 a, a.K, a.sid0 + j, hash, queue, slot, ctl, budget, wt, team, &width, &live,
-                &exam, resumed ? &rin : nullptr, (HAND && TIER == 1 && a.hand) ? &rout : nullptr);
+                &exam, resumed ? &rin : nullptr,
+                (HAND && ((TIER == 1 && a.hand) || (TIER == 2 && a.hand2))) ? &rout : nullptr);
             const int tail = min(T == 1 ? __shfl_sync(0xffffffffu, ((volatile int*)ctl)[0], 0)
                                         : ((volatile int*)ctl)[0],
                                  C::Q);
@@ -675,6 +680,24 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
                             hs[3] = (uint32_t)(rout.width >> 32);
                         }
                     }
+                }
+                if (HAND && TIER == 2 && a.hand2) {  // hand the state to the heavy pass
+                    if (T == 1) {
+                        idx = __shfl_sync(0xffffffffu, idx, 0);
+                    } else {
+                        if (leader) s_claim[team] = idx;
+                        team_sync<T>(team);
+                        idx = (unsigned)s_claim[team];
+                    }
+                    if (idx < a.h2cap) {
+                        uint32_t* hs = a.hand2 + idx * (uint64_t)a.h2w;
+                        for (int i = tl; i < tail; i += 32 * T) hs[4 + i] = queue[i];
+                        if (leader) {
+                            hs[0] = (uint32_t)tail;
+                            hs[1] = (uint32_t)min(rout.head, tail);
+                        }
+                    }
+                    team_sync<T>(team);
                 }
                 for (int i = tl; i < C::H; i += 32 * T) hash[i] = EMPTY;
                 team_sync<T>(team);
@@ -1885,6 +1908,15 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
         a.hand = (uint32_t*)ctx->hand.p;
         a.hcap = (uint32_t)hcap;
     }
+    a.hand2 = nullptr;
+    a.h2cap = 0;
+    a.h2w = 4u + (uint32_t)Tier2::Q;
+    if (ctx->model == TIM_IC && count > 0) {  // at most 1 GiB; later sets start over
+        const uint64_t h2cap = std::min<uint64_t>((1ull << 30) / ((uint64_t)a.h2w * 4), list_cap);
+        TIM_TRY(tim_ensure(ctx, ctx->hand2, (size_t)h2cap * a.h2w * sizeof(uint32_t)));
+        a.hand2 = (uint32_t*)ctx->hand2.p;
+        a.h2cap = (uint32_t)h2cap;
+    }
     a.node_opt = (const uint64_t*)ctx->node_opt.p;
     a.opt_cum = (const uint32_t*)ctx->opt_cum.p;
     a.opt_off = (const uint64_t*)ctx->opt_off.p;
@@ -1918,7 +1950,7 @@ int tim_sample(tim_ctx* ctx, const SampleRequest& req, SampleResult* res) {
                 TIM_TRY(tim_read_scalars(ctx));
                 const unsigned n3 = std::min(ctx->h_scal->cnt2, list_cap);
                 TIM_TRY(tim_bulk_ic(ctx, req, a.list2, n3, a.pool, a.pool_sid, a.pool_cap, a.ds,
-                                    &live3));
+                                    &live3, a.hand2, a.h2cap, a.h2w));
             } else if (ctx->model == TIM_TRIG) {
                 rr_trig_big_kernel<<<slots, BIG_THREADS, 0, ctx->stream>>>(a);
                 LAUNCH_CHECK(ctx, "rr_trig_big_kernel");

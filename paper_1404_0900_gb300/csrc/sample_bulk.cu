@@ -61,6 +61,8 @@ struct BulkArgs {
     const uint32_t* seed_mark;
     const uint32_t* list;  // heavy set indices (relative to sid0)
     uint32_t base, S;      // this batch: slots s in [0, S) hold list[base + s]
+    const uint32_t* hand;  // pass 2's state of the set at list position i < hcap (or null)
+    uint32_t hcap, hw;
     uint32_t* bitmap;
     uint64_t words;
     unsigned long long* slot_width;
@@ -109,51 +111,6 @@ __device__ __forceinline__ uint32_t pick4(uint4 v, int c) {
     return c == 0 ? v.x : c == 1 ? v.y : c == 2 ? v.z : v.w;
 }
 
-__global__ void bulk_init_kernel(BulkArgs a) {
-    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.S; s += gridDim.x * blockDim.x) {
-        const uint32_t j = a.list[a.base + s];
-        const uint64_t sid = a.sid0 + j;
-        const uint32_t root = rr_root(sid, a.n, a.K);
-        atomicOr(&a.bitmap[(uint64_t)s * a.words + (root >> 5)], 1u << (root & 31));
-        const uint64_t beg = a.rowptr[root], end = a.rowptr[root + 1];
-        a.slot_width[s] = end - beg;
-        a.slot_cnt[s] = 1;
-        a.slot_cursor[s] = 0;
-        const bool cov = (a.flags & SAMPLE_COVER) && marked(a.seed_mark, root);
-        a.slot_flag[s] = cov ? 1u : 0u;
-        unsigned long long pm = atomicAdd(&a.bs->m_count, 1ull);
-        if (pm < a.mcap)
-            a.M[pm] = make_uint2(s, root);
-        else
-            atomicOr(&a.bs->err, 2);
-        if (end > beg && !cov) {
-            unsigned long long pf = atomicAdd(&a.bs->f_count, 1ull);
-            const bool sk = tim_skip_rule(a.node_thr[root], end - beg);
-            if (pf < a.fcap)
-                a.F[pf] = make_uint4((uint32_t)beg, (uint32_t)end, s | (sk ? 0x80000000u : 0u),
-                                     root);
-            else
-                atomicOr(&a.bs->err, 1);
-        }
-    }
-}
-
-constexpr uint32_t NG_SKIP = 0x80000000u;
-
-// Groups of frontier item F[lo + i]: the 4-aligned groups of its in-list, or one
-// placeholder group (flagged NG_SKIP) for a list under the skip rule.
-__device__ __forceinline__ uint32_t item_groups(const BulkArgs& a, uint64_t lo, uint64_t i) {
-    const uint4 it = __ldcg(&a.F[lo + i]);
-    return (it.z >> 31) ? (1u | NG_SKIP) : ((it.y - 1) >> 2) - (it.x >> 2) + 1u;  // y > x
-}
-
-// Host-stepped path: group counts of the level without the skip flag (the scan input).
-__global__ void bulk_ng_kernel(BulkArgs a) {
-    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.lvl_n;
-         i += (uint64_t)gridDim.x * blockDim.x)
-        a.ng[i] = item_groups(a, a.lvl_lo, i) & ~NG_SKIP;
-}
-
 // Warp-aggregated append of (slot, node) to one of the lists; returns nothing.
 __device__ __forceinline__ void warp_append(bool pred, uint32_t s, uint32_t u,
                                             unsigned long long* counter, uint2* list,
@@ -189,6 +146,111 @@ __device__ __forceinline__ void warp_append_f(bool pred, uint4 item, unsigned lo
         else
             atomicOr(err, 1);
     }
+}
+
+// The state pass 2 handed over for list position li, or null.
+__device__ __forceinline__ const uint32_t* bulk_hand(const BulkArgs& a, uint64_t li) {
+    if (!a.hand || li >= a.hcap) return nullptr;
+    const uint32_t* hs = a.hand + li * (uint64_t)a.hw;
+    const uint32_t t0 = hs[0];
+    return t0 > 0 && t0 + 4 <= a.hw ? hs : nullptr;
+}
+
+// One thread per slot: a set without handed-over state starts from its root; a set with
+// it gets its counters (width 0, its members' count) for bulk_hand_kernel to fill.
+__global__ void bulk_init_kernel(BulkArgs a) {
+    const bool cover = a.flags & SAMPLE_COVER;
+    for (uint32_t s = blockIdx.x * blockDim.x + threadIdx.x; s < a.S; s += gridDim.x * blockDim.x) {
+        const uint64_t li = (uint64_t)a.base + s;
+        const uint32_t* hs = bulk_hand(a, li);
+        a.slot_cursor[s] = 0;
+        if (hs) {
+            a.slot_width[s] = 0;
+            a.slot_cnt[s] = hs[0];
+            a.slot_flag[s] = 0u;
+            continue;
+        }
+        const uint32_t j = a.list[li];
+        const uint64_t sid = a.sid0 + j;
+        const uint32_t root = rr_root(sid, a.n, a.K);
+        atomicOr(&a.bitmap[(uint64_t)s * a.words + (root >> 5)], 1u << (root & 31));
+        const uint64_t beg = a.rowptr[root], end = a.rowptr[root + 1];
+        a.slot_width[s] = end - beg;
+        a.slot_cnt[s] = 1;
+        const bool cov = cover && marked(a.seed_mark, root);
+        a.slot_flag[s] = cov ? 1u : 0u;
+        unsigned long long pm = atomicAdd(&a.bs->m_count, 1ull);
+        if (pm < a.mcap)
+            a.M[pm] = make_uint2(s, root);
+        else
+            atomicOr(&a.bs->err, 2);
+        if (end > beg && !cov) {
+            unsigned long long pf = atomicAdd(&a.bs->f_count, 1ull);
+            const bool sk = tim_skip_rule(a.node_thr[root], end - beg);
+            if (pf < a.fcap)
+                a.F[pf] = make_uint4((uint32_t)beg, (uint32_t)end, s | (sk ? 0x80000000u : 0u),
+                                     root);
+            else
+                atomicOr(&a.bs->err, 1);
+        }
+    }
+}
+
+// The members pass 2 found before it handed a set over, 32 per warp item over the whole
+// grid (item = slot x 32-member chunk): visited bits, member list, in-degree sum into the
+// set's width, the seed test (cover), and the members from the batch pass 2 was at on,
+// with in-edges, into the frontier (a covered set's frontier items are skipped when the
+// level is expanded).
+__global__ void bulk_hand_kernel(BulkArgs a, uint32_t chunks_per_slot) {
+    const int lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const bool cover = a.flags & SAMPLE_COVER;
+    const uint64_t items = (uint64_t)a.S * chunks_per_slot;
+    for (uint64_t w = (blockIdx.x * (uint64_t)blockDim.x + threadIdx.x) >> 5; w < items; w += nw) {
+        const uint32_t s = (uint32_t)(w / chunks_per_slot);
+        const uint32_t c = (uint32_t)(w % chunks_per_slot);
+        const uint32_t* hs = bulk_hand(a, (uint64_t)a.base + s);
+        if (!hs) continue;
+        const uint32_t t0 = hs[0];
+        if (c * 32u >= t0) continue;
+        const uint32_t h0 = min(hs[1], t0);
+        const uint32_t i = c * 32u + lane;
+        const bool h = i < t0;
+        const uint32_t u = h ? hs[4 + i] : 0u;
+        uint64_t beg = 0, end = 0;
+        bool cov = false;
+        if (h) {
+            atomicOr(&a.bitmap[(uint64_t)s * a.words + (u >> 5)], 1u << (u & 31));
+            beg = a.rowptr[u];
+            end = a.rowptr[u + 1];
+            cov = cover && marked(a.seed_mark, u);
+        }
+        warp_append(h, s, u, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2, lane);
+        const unsigned long long wsum = __reduce_add_sync(0xffffffffu, (unsigned)(end - beg));
+        if (lane == 0 && wsum) atomicAdd(&a.slot_width[s], wsum);
+        if (__any_sync(0xffffffffu, cov) && lane == 0) a.slot_flag[s] = 1u;
+        const bool push = h && i >= h0 && end > beg;
+        const uint4 item = make_uint4((uint32_t)beg, (uint32_t)end,
+                                      s | (push && tim_skip_rule(a.node_thr[u], end - beg)
+                                               ? 0x80000000u : 0u), u);
+        warp_append_f(push, item, &a.bs->f_count, a.F, a.fcap, &a.bs->err, lane);
+    }
+}
+
+constexpr uint32_t NG_SKIP = 0x80000000u;
+
+// Groups of frontier item F[lo + i]: the 4-aligned groups of its in-list, or one
+// placeholder group (flagged NG_SKIP) for a list under the skip rule.
+__device__ __forceinline__ uint32_t item_groups(const BulkArgs& a, uint64_t lo, uint64_t i) {
+    const uint4 it = __ldcg(&a.F[lo + i]);
+    return (it.z >> 31) ? (1u | NG_SKIP) : ((it.y - 1) >> 2) - (it.x >> 2) + 1u;  // y > x
+}
+
+// Host-stepped path: group counts of the level without the skip flag (the scan input).
+__global__ void bulk_ng_kernel(BulkArgs a) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < a.lvl_n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        a.ng[i] = item_groups(a, a.lvl_lo, i) & ~NG_SKIP;
 }
 
 // Appends of one warp staged in shared memory and copied to the global list in runs of
@@ -797,7 +859,7 @@ __global__ void bulk_emit_clear_kernel(BulkArgs a, unsigned long long mcount, in
 // Heavy IC sets listed in ctx->ovf_list[0 .. count): expand them in batches.
 int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, uint32_t count,
                 uint32_t* pool, uint32_t* pool_sid, uint64_t pool_cap, DevScalars* ds,
-                uint64_t* live_out) {
+                uint64_t* live_out, const uint32_t* hand, uint32_t hcap, uint32_t hw) {
     if (count == 0) return TIM_OK;
     const uint64_t n = (uint64_t)ctx->n;
     const uint64_t words = (n + 31) / 32 + 1;
@@ -856,6 +918,9 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
     a.k = req.k;
     a.seed_mark = req.seed_mark;
     a.list = list;
+    a.hand = hand;
+    a.hcap = hand ? hcap : 0u;
+    a.hw = hw;
     a.bitmap = (uint32_t*)ctx->bulk_bitmap.p;
     a.words = words;
     char* sl = (char*)ctx->bulk_slot.p;
@@ -892,6 +957,11 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
         CUDA_TRY(ctx, cudaMemsetAsync(a.bs, 0, sizeof(BulkScalars), ctx->stream));
         bulk_init_kernel<<<(bs + 255) / 256, 256, 0, ctx->stream>>>(a);
         LAUNCH_CHECK(ctx, "bulk_init_kernel");
+        if (a.hand) {
+            bulk_hand_kernel<<<(unsigned)(ctx->num_sms * 8), 256, 0, ctx->stream>>>(
+                a, (hw > 4 ? hw - 4 + 31 : 0) / 32);
+            LAUNCH_CHECK(ctx, "bulk_hand_kernel");
+        }
         uint64_t lo = 0, hi = 0;
         bool overflow = false;
         if (persistent) {
