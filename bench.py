@@ -41,7 +41,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # exists.
 DRAM_BYTES_PER_MEMBER = {
     # profiles/sampler_dram_c3.md
-    "c3": {1: 382.7, 2: 779.8, 3: 593.3},
+    "c3": {1: None, 2: None, 3: None},  # passes changed since the capture
     "c2": {1: None, 2: None, 3: None},
 }
 FALLBACK_HBM_GBS = 6800.0
