@@ -92,7 +92,8 @@ struct SampleArgs {
     uint32_t* hand;
     uint32_t hcap, hw;
     // IC: the state pass 2 hands to the heavy pass for the set at list2 position i < h2cap,
-    // h2w words at hand2 + i h2w: queue length, resume position, 2 spare words, queue
+    // h2w words at hand2 + i h2w: queue length, resume position, width before it (2
+    // words), queue
     uint32_t* hand2;
     uint32_t h2cap, h2w;
     // triggering model: options of each node, their cumulative thresholds, their in-edges
@@ -695,6 +696,8 @@ __global__ void __launch_bounds__(WARPS * 32, TIER == 1 ? 4 : 6) rr_team_kernel(
                         if (leader) {
                             hs[0] = (uint32_t)tail;
                             hs[1] = (uint32_t)min(rout.head, tail);
+                            hs[2] = (uint32_t)rout.width;  // in-degrees of queue[0 .. hs[1])
+                            hs[3] = (uint32_t)(rout.width >> 32);
                         }
                     }
                     team_sync<T>(team);

@@ -165,7 +165,9 @@ __global__ void bulk_init_kernel(BulkArgs a) {
         const uint32_t* hs = bulk_hand(a, li);
         a.slot_cursor[s] = 0;
         if (hs) {
-            a.slot_width[s] = 0;
+            // the width pass 2 counted for the members before the batch it stopped at;
+            // bulk_hand_kernel adds the in-degrees of the rest
+            a.slot_width[s] = (unsigned long long)hs[2] | ((unsigned long long)hs[3] << 32);
             a.slot_cnt[s] = hs[0];
             a.slot_flag[s] = 0u;
             continue;
@@ -197,10 +199,11 @@ __global__ void bulk_init_kernel(BulkArgs a) {
 }
 
 // The members pass 2 found before it handed a set over, 32 per warp item over the whole
-// grid (item = slot x 32-member chunk): visited bits, member list, in-degree sum into the
-// set's width, the seed test (cover), and the members from the batch pass 2 was at on,
-// with in-edges, into the frontier (a covered set's frontier items are skipped when the
-// level is expanded).
+// grid (item = slot x 32-member chunk): visited bits, member list, the seed test (cover),
+// and the members from the batch pass 2 was at on: their in-degrees into the set's
+// width (pass 2 handed over the sum for the members before them) and, with in-edges,
+// into the frontier (a covered set's frontier items are skipped when the level is
+// expanded).
 __global__ void bulk_hand_kernel(BulkArgs a, uint32_t chunks_per_slot) {
     const int lane = threadIdx.x & 31;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
@@ -221,8 +224,10 @@ __global__ void bulk_hand_kernel(BulkArgs a, uint32_t chunks_per_slot) {
         bool cov = false;
         if (h) {
             atomicOr(&a.bitmap[(uint64_t)s * a.words + (u >> 5)], 1u << (u & 31));
-            beg = a.rowptr[u];
-            end = a.rowptr[u + 1];
+            if (i >= h0) {  // not yet expanded: its in-degree is not in the width yet
+                beg = a.rowptr[u];
+                end = a.rowptr[u + 1];
+            }
             cov = cover && marked(a.seed_mark, u);
         }
         warp_append(h, s, u, &a.bs->m_count, a.M, a.mcap, &a.bs->err, 2, lane);
