@@ -1371,6 +1371,9 @@ struct MultiArgs {
     uint2* list2;
     uint32_t list_cap;
     uint32_t* arena;
+    // IC: pass-1 state handed to pass 2 for list1 position i < hcap (as in SampleArgs)
+    uint32_t* hand;
+    uint32_t hcap, hw;
 };
 
 // What team_rr reads of one query: its graph and flags, plus the launch's keys.
@@ -1499,10 +1502,41 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
                 model != TIM_IC ? ~0ull : TIER == 1 ? d.width_budget : d.width_budget2;
             unsigned long long width;
             int st;
+            // IC: pass 2 goes on from the state pass 1 handed over (see rr_team_kernel)
+            Resume rin{0, 0ull}, rout{0, 0ull};
+            bool resumed = false;
+            if (TIER == 2 && model == TIM_IC && ma.hand && it < ma.hcap) {
+                const uint32_t* hs = ma.hand + it * (uint64_t)ma.hw;
+                const uint32_t t0 = hs[0];
+                if (t0 > 0 && t0 <= (uint32_t)C::Q) {
+                    if (leader) {
+                        ctl[0] = (int)t0;
+                        ctl[1] = 0;
+                    }
+                    team_sync<T>(team);
+                    for (uint32_t i = tl; i < t0; i += 32 * T) {
+                        const uint32_t u = hs[4 + i];
+                        queue[i] = u;
+                        uint32_t h = (u * 0x9E3779B1u) >> (32 - C::LOG2H);
+                        for (int probe = 0; probe < C::H; probe++) {
+                            if (atomicCAS(&hash[h], EMPTY, u) == EMPTY) break;
+                            h = (h + 1) & (C::H - 1);
+                        }
+                        slot[i] = (uint16_t)h;
+                        if ((d.flags & SAMPLE_COVER) && marked(d.seed_mark, u))
+                            atomicOr(&ctl[1], ST_COVERED);
+                    }
+                    rin.head = (int)min(hs[1], t0);
+                    rin.width = (unsigned long long)hs[2] | ((unsigned long long)hs[3] << 32);
+                    resumed = true;
+                }
+                team_sync<T>(team);
+            }
             if (model == TIM_IC)
                 st = team_rr<TIM_IC, C, T, QArgs>(qa, ma.K, d.sid0 + j, hash, queue, slot, ctl,
                                                   budget, wt, team, &width, &acc.live,
-                                                  &acc.exam);
+                                                  &acc.exam, resumed ? &rin : nullptr,
+                                                  (TIER == 1 && ma.hand) ? &rout : nullptr);
             else
                 st = team_rr<TIM_LT, C, T, QArgs>(qa, ma.K, d.sid0 + j, hash, queue, slot, ctl,
                                                   budget, wt, team, &width, &acc.live,
@@ -1512,12 +1546,26 @@ __global__ void __launch_bounds__(WARPS * 32, 3) rr_multi_kernel(MultiArgs ma) {
                                  C::Q);
             team_sync<T>(team);
             if (st & ST_OVERFLOW) {
+                unsigned idx = 0;
                 if (leader) {
-                    const unsigned idx = atomicAdd(out_cnt, 1u);
+                    idx = atomicAdd(out_cnt, 1u);
                     if (idx < ma.list_cap)
                         out_list[idx] = make_uint2((uint32_t)qi, (uint32_t)j);
                     else
                         atomicOr(ma.err, TIM_DEV_ERR_OVF_LIST);
+                }
+                if (TIER == 1 && T == 1 && model == TIM_IC && ma.hand) {
+                    idx = __shfl_sync(0xffffffffu, idx, 0);
+                    if (idx < ma.hcap) {
+                        uint32_t* hs = ma.hand + idx * (uint64_t)ma.hw;
+                        for (int i = lane; i < tail; i += 32) hs[4 + i] = queue[i];
+                        if (lane == 0) {
+                            hs[0] = (uint32_t)tail;
+                            hs[1] = (uint32_t)rout.head;
+                            hs[2] = (uint32_t)rout.width;
+                            hs[3] = (uint32_t)(rout.width >> 32);
+                        }
+                    }
                 }
                 for (int i = tl; i < C::H; i += 32 * T) hash[i] = EMPTY;
                 team_sync<T>(team);
@@ -2199,6 +2247,16 @@ int tim_sample_multi(tim_ctx* owner, MultiQuery* qs, int nq, uint64_t seed) {
     ma.list2 = (uint2*)owner->ovf_list2.p;
     ma.list_cap = (uint32_t)(total + 1);
     ma.arena = (uint32_t*)owner->arena.p;
+    // pass-1 state handed to pass 2 (IC queries), in the owner's scratch
+    ma.hw = 4u + (uint32_t)cap1;
+    {
+        const uint64_t maxslots = (1ull << 30) / ((uint64_t)ma.hw * sizeof(uint32_t));
+        const uint64_t hcap =
+            std::min<uint64_t>(std::min<uint64_t>(total_ic / 8 + 4096, maxslots), total + 1);
+        TIM_TRY(tim_ensure(owner, owner->hand, (size_t)hcap * ma.hw * sizeof(uint32_t)));
+        ma.hand = (uint32_t*)owner->hand.p;
+        ma.hcap = (uint32_t)hcap;
+    }
     std::vector<QueryDesc> h_desc(nq);
     std::vector<DevScalars> h_scal(nq);
     for (int attempt = 0; attempt < 4; attempt++) {
