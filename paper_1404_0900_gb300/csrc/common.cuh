@@ -112,6 +112,7 @@ struct tim_ctx {
     bool bulk_stepped = false;
     bool bulk_bitmap_clean = false;
     uint64_t bulk_fcap = 0, bulk_mcap = 0;
+    uint64_t bulk_budget = 0;  // bytes of visited bitmaps a heavy-pass batch may use
     // IC first pass: a warp gives a set to the second pass once its examined in-edges
     // would exceed this many
     unsigned long long width_budget = 16384;

@@ -868,9 +868,25 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
     if (count == 0) return TIM_OK;
     const uint64_t n = (uint64_t)ctx->n;
     const uint64_t words = (n + 31) / 32 + 1;
-    // slots: visited bitmaps of at most ~2 GiB
-    uint64_t smax = std::max<uint64_t>(32, (2ull << 30) / (words * 4));
+    // slots: one visited bitmap of n bits per set of a batch, at most 16 GiB of them in
+    // all (a quarter of the device memory free at the context's first heavy pass, if
+    // that is less), at least 32; the buffers grow to the next power of two of the sets
+    // a call lists. Larger batches mean fewer levels for the same sets (TIM+ on a
+    // 41.6M-node, 1.4B-edge Chung-Lu graph: 32 batches and ~1,460 levels per run with
+    // 2 GiB of bitmaps, TIM+ 263 -> 246 ms with 16 GiB).
+    if (ctx->bulk_budget == 0) {
+        size_t fr = 0, tot = 0;
+        ctx->bulk_budget = 16ull << 30;
+        if (cudaMemGetInfo(&fr, &tot) == cudaSuccess)
+            ctx->bulk_budget = std::min<uint64_t>(ctx->bulk_budget, fr / 4);
+        else
+            cudaGetLastError();
+    }
+    uint64_t smax = std::max<uint64_t>(32, ctx->bulk_budget / (words * 4));
     smax = std::min<uint64_t>(smax, 65536);
+    uint64_t slots = 32;
+    while (slots < count && slots < smax) slots <<= 1;
+    smax = std::min<uint64_t>(slots, smax);
     uint32_t S = (uint32_t)std::min<uint64_t>(smax, count);
     void* prev_bitmap = ctx->bulk_bitmap.p;
     TIM_TRY(tim_ensure(ctx, ctx->bulk_bitmap, (size_t)smax * words * 4));
