@@ -41,7 +41,7 @@ PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 # exists.
 DRAM_BYTES_PER_MEMBER = {
     # profiles/sampler_dram_c3.md
-    "c3": {1: 384.8, 2: 760.1, 3: 530.7},
+    "c3": {1: 384.8, 2: 760.1, 3: 561.4},
     "c2": {1: None, 2: None, 3: None},
 }
 FALLBACK_HBM_GBS = 6800.0
