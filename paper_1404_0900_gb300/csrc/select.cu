@@ -37,10 +37,13 @@ __global__ void count_members_kernel(const uint32_t* __restrict__ pool, uint64_t
     for (uint64_t p = (quads << 2) + tid; p < members; p += stride) atomicAdd(&cnt[pool[p]], 1u);
 }
 
+// Node v's sets: node_sets[start(v) .. start(v + 1)). next[v] holds start(v) on entry
+// (next = node_off + 1, the exclusive scan written one place to the right); each member
+// takes its position with one atomic on it, so that afterwards next[v] = start(v + 1):
+// node_off[0 .. n] are the node offsets with no cursor array and no offset load.
 __global__ void scatter_sets_kernel(const uint32_t* __restrict__ pool,
                                     const uint32_t* __restrict__ pool_sid, uint64_t members,
-                                    const uint64_t* __restrict__ node_off,
-                                    uint32_t* __restrict__ cursor,
+                                    unsigned long long* __restrict__ next,
                                     uint32_t* __restrict__ node_sets) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     const uint64_t tid = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
@@ -50,20 +53,15 @@ __global__ void scatter_sets_kernel(const uint32_t* __restrict__ pool,
     for (uint64_t q = tid; q < quads; q += stride) {
         const uint4 u = __ldg(pool4 + q);
         const uint4 j = __ldg(sid4 + q);
-        const uint32_t c0 = atomicAdd(&cursor[u.x], 1u), c1 = atomicAdd(&cursor[u.y], 1u);
-        const uint32_t c2 = atomicAdd(&cursor[u.z], 1u), c3 = atomicAdd(&cursor[u.w], 1u);
-        const uint64_t o0 = __ldg(node_off + u.x), o1 = __ldg(node_off + u.y);
-        const uint64_t o2 = __ldg(node_off + u.z), o3 = __ldg(node_off + u.w);
-        node_sets[o0 + c0] = j.x;
-        node_sets[o1 + c1] = j.y;
-        node_sets[o2 + c2] = j.z;
-        node_sets[o3 + c3] = j.w;
+        const unsigned long long p0 = atomicAdd(&next[u.x], 1ull), p1 = atomicAdd(&next[u.y], 1ull);
+        const unsigned long long p2 = atomicAdd(&next[u.z], 1ull), p3 = atomicAdd(&next[u.w], 1ull);
+        node_sets[p0] = j.x;
+        node_sets[p1] = j.y;
+        node_sets[p2] = j.z;
+        node_sets[p3] = j.w;
     }
-    for (uint64_t p = (quads << 2) + tid; p < members; p += stride) {
-        const uint32_t u = pool[p];
-        const uint32_t slot = atomicAdd(&cursor[u], 1u);
-        node_sets[node_off[u] + slot] = pool_sid[p];
-    }
+    for (uint64_t p = (quads << 2) + tid; p < members; p += stride)
+        node_sets[atomicAdd(&next[pool[p]], 1ull)] = pool_sid[p];
 }
 
 __device__ __forceinline__ unsigned long long greedy_key(int cnt, uint32_t v) {
@@ -282,23 +280,24 @@ greedy_rounds_kernel(int* __restrict__ counts, uint8_t* __restrict__ chosen, uin
 int tim_build_index(tim_ctx* ctx) {
     const uint64_t n = (uint64_t)ctx->n, members = ctx->members;
     TIM_TRY(tim_ensure(ctx, ctx->counts, (n + 1) * sizeof(int)));
-    TIM_TRY(tim_ensure(ctx, ctx->node_off, (n + 1) * sizeof(uint64_t)));
-    TIM_TRY(tim_ensure(ctx, ctx->cursor, (n + 1) * sizeof(uint32_t)));
+    TIM_TRY(tim_ensure(ctx, ctx->node_off, (n + 2) * sizeof(uint64_t)));
     TIM_TRY(tim_ensure(ctx, ctx->node_sets, (members + 1) * sizeof(uint32_t)));
     CUDA_TRY(ctx, cudaMemsetAsync(ctx->counts.p, 0, (n + 1) * sizeof(int), ctx->stream));
-    CUDA_TRY(ctx, cudaMemsetAsync(ctx->cursor.p, 0, (n + 1) * sizeof(uint32_t), ctx->stream));
+    CUDA_TRY(ctx, cudaMemsetAsync(ctx->node_off.p, 0, sizeof(uint64_t), ctx->stream));
     const unsigned G = (unsigned)(ctx->num_sms * 8);
     if (members) {
         count_members_kernel<<<G, 256, 0, ctx->stream>>>((const uint32_t*)ctx->pool.p, members,
                                                          (uint32_t*)ctx->counts.p);
         LAUNCH_CHECK(ctx, "count_members_kernel");
     }
-    TIM_TRY(tim_scan_u32_to_u64(ctx, (const uint32_t*)ctx->counts.p, (uint64_t*)ctx->node_off.p, n));
+    // node_off[v + 1] = start of node v's sets (node_off[0] = 0); the scatter turns it
+    // into start(v + 1)
+    TIM_TRY(tim_scan_u32_to_u64(ctx, (const uint32_t*)ctx->counts.p,
+                                (uint64_t*)ctx->node_off.p + 1, n));
     if (members) {
         scatter_sets_kernel<<<G, 256, 0, ctx->stream>>>(
             (const uint32_t*)ctx->pool.p, (const uint32_t*)ctx->pool_sid.p, members,
-            (const uint64_t*)ctx->node_off.p, (uint32_t*)ctx->cursor.p,
-            (uint32_t*)ctx->node_sets.p);
+            (unsigned long long*)ctx->node_off.p + 1, (uint32_t*)ctx->node_sets.p);
         LAUNCH_CHECK(ctx, "scatter_sets_kernel");
     }
     return TIM_OK;
