@@ -95,12 +95,6 @@ __device__ __forceinline__ bool marked(const uint32_t* mark, uint32_t u) {
     return (__ldg(mark + (u >> 5)) >> (u & 31)) & 1u;
 }
 
-#ifdef BULK_TRACE
-// per-level record of block 0 (timing builds only): items, groups, ns of A, B, C, wait
-__device__ unsigned long long bulk_trace[1 << 16][6];
-__device__ unsigned long long bulk_trace_n;
-#endif
-
 __device__ __forceinline__ unsigned long long globaltimer_ns() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
@@ -726,9 +720,6 @@ __global__ void __launch_bounds__(256, LEVELS_MIN_BLOCKS) bulk_levels_kernel(Bul
             if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(err, 1);
             return;
         }
-#ifdef BULK_TRACE
-        unsigned long long tr0 = clerk ? globaltimer_ns() : 0ull, tr[4] = {0, 0, 0, 0};
-#endif
         // (A) group counts of this block's items and their sum
         const uint64_t per = (nl + gridDim.x - 1) / gridDim.x;
         const uint64_t ib = min((uint64_t)blockIdx.x * per, nl), ie = min(ib + per, nl);
@@ -773,17 +764,6 @@ __global__ void __launch_bounds__(256, LEVELS_MIN_BLOCKS) bulk_levels_kernel(Bul
         lap(ns_exp);
         if (!grid_barrier(a.bar, err, a.wait_limit)) return;
         lap(ns_wait);
-#ifdef BULK_TRACE
-        if (clerk) {
-            const unsigned long long k = atomicAdd(&bulk_trace_n, 1ull) & 0xFFFFull;
-            bulk_trace[k][0] = nl;
-            bulk_trace[k][1] = all;
-            bulk_trace[k][2] = t_prev - tr0;
-            bulk_trace[k][3] = __ldcg(&a.bs->m_count);
-            bulk_trace[k][4] = __ldcg(&a.bs->live);
-            bulk_trace[k][5] = level;
-        }
-#endif
         lo = hi;
         hi = __ldcg(&a.bs->f_count);
         if (__ldcg(err)) {
@@ -1070,13 +1050,3 @@ int tim_bulk_ic(tim_ctx* ctx, const SampleRequest& req, const uint32_t* list, ui
     if (live_out) *live_out = live;
     return TIM_OK;
 }
-
-#ifdef BULK_TRACE
-extern "C" int tim_debug_bulk_trace(unsigned long long* out, unsigned long long cap) {
-    unsigned long long n = 0;
-    cudaMemcpyFromSymbol(&n, bulk_trace_n, sizeof n);
-    const unsigned long long k = n < cap ? n : cap;
-    cudaMemcpyFromSymbol(out, bulk_trace, k * 6 * sizeof(unsigned long long));
-    return (int)k;
-}
-#endif
